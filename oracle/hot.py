@@ -28,8 +28,11 @@ Readings where the paper is silent (Sec. IV-A gives only the stopping rule):
   current cycle, restart when r <= 0.2 r0, or r <= 0.8 r0 and r grew since the
   previous check, or the cycle is at least 0.2 times the total iteration count.
   A restart sets the anchor and the iterate to w-bar, the cycle counter k to 0,
-  and sigma <- ||x-bar - x_r|| / ||z-bar - z_r|| where (x_r, z_r) is the
-  previous restart point (0 before the first).
+  and sigma <- sqrt(sigma * ||x-bar - x_r|| / ||z-bar - z_r||), the geometric
+  mean of the old sigma and the primal/dual movement ratio since the previous
+  restart point (x_r, z_r) (0 before the first).  The ratio alone balances the
+  two parts of the M-norm (App. A) but swings over many orders of magnitude
+  on degenerate inputs; the geometric mean damps it.
 * The iteration cap is tested at check iterations: the solve stops at the first
   check iteration whose total count reaches max_iter.
 """
@@ -121,7 +124,7 @@ def hot_solve(mu1, mu2, tol=1e-6, max_iter=100000, params=None, xs=None, ys=None
     scale = cost_scale(c_full, p.scale_cost)
     c = c_full / scale
     nb, nc = np.linalg.norm(b), np.linalg.norm(c)
-    sigma = p.sigma0 if p.sigma0 > 0 else nb / nc
+    sigma = float(p.sigma0 if p.sigma0 > 0 else nb / nc)
     N = c.size
     K = p.check_every
 
@@ -144,11 +147,13 @@ def hot_solve(mu1, mu2, tol=1e-6, max_iter=100000, params=None, xs=None, ys=None
 
         if total % K == 0:
             err, parts = kkt_residual(A, b, c, x_bar, y_bar, z_bar)
-            done = err <= tol
+            err = float(err)
+            parts = tuple(float(q) for q in parts)
+            done = bool(err <= tol)
             capped = total >= max_iter
             restart = False
             if not done and not capped and p.restart:
-                r = np.linalg.norm((x - x_bar) + sigma * (z - z_bar)) / math.sqrt(sigma)
+                r = float(np.linalg.norm((x - x_bar) + sigma * (z - z_bar))) / math.sqrt(sigma)
                 if r0 is None:
                     r0 = r
                 restart = (r <= p.restart_sufficient * r0
@@ -162,10 +167,10 @@ def hot_solve(mu1, mu2, tol=1e-6, max_iter=100000, params=None, xs=None, ys=None
                                  sigma=sigma, cost_scale=scale, x=x_bar, y=scale * y_bar, z=scale * z_bar,
                                  trace=trace)
             if restart:
-                dx = np.linalg.norm(x_bar - x_r)
-                dz = np.linalg.norm(z_bar - z_r)
+                dx = float(np.linalg.norm(x_bar - x_r))
+                dz = float(np.linalg.norm(z_bar - z_r))
                 if dx > 0.0 and dz > 0.0 and math.isfinite(dx / dz):
-                    sigma = dx / dz
+                    sigma = math.sqrt(sigma * (dx / dz))
                 x_r, z_r = x_bar.copy(), z_bar.copy()
                 x0, z0, y0 = x_bar.copy(), z_bar.copy(), y_bar.copy()
                 x, z, y = x0.copy(), z0.copy(), y0.copy()

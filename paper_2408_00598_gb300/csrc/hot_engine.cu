@@ -1,0 +1,554 @@
+// Host engine: instance set-up (Sec. II-A data of arXiv 2408.00598: b, the
+// power-of-two cost scale, norms), the batch work tables, the CUDA graph of
+// one check block (K iterations of Algorithm 2 plus the stopping/restart
+// step), and the synchronous solve entry points of the C ABI.
+#include "hot_engine.h"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+namespace hot {
+
+// ------------------------------------------------------------------ errors --
+
+static thread_local std::string g_err;
+void set_error(const std::string& msg) { g_err = msg; }
+const char* get_error() { return g_err.c_str(); }
+
+// ------------------------------------------------------------- validation --
+
+int tile_rows(int S, int fp64) {
+    if (fp64) {
+        // row-partial buffer: TR * S <= 4096
+        int tr = std::min(S, 4096 / S);
+        if (S >= 96) tr = std::min(tr, 32);
+        return std::max(tr, 1);
+    }
+    // TR * S <= 16384; large grids get several bands per slab for balance
+    switch (S) {
+        case 96: return 48;
+        case 128: return 32;
+        case 256: return 64;
+        case 512: return 32;
+        case 1024: return 16;
+        default: break;
+    }
+    return std::min(S, 16384 / S);
+}
+
+int validate_pair(const double* mu, const double* nu, int m, int n, int space, int fp64, PairHost& out) {
+    if (!mu || !nu) {
+        set_error("null histogram pointer");
+        return HOT_EINVAL;
+    }
+    if (m != n) {
+        set_error("only square grids (m == n) are supported in this version");
+        return HOT_EINVAL;
+    }
+    const int S = m;
+    const int smax = fp64 ? 512 : kMaxS;
+    if (S < 8 || S > smax || (S % 4) != 0) {
+        set_error("grid side must be a multiple of 4 in [8, " + std::to_string(smax) + "], got " + std::to_string(S));
+        return HOT_EINVAL;
+    }
+    out.S = S;
+    const size_t M = (size_t)S * S;
+    out.mu1.resize(M);
+    out.mu2.resize(M);
+    if (space == HOT_SPACE_DEVICE) {
+        cudaError_t e1 = cudaMemcpy(out.mu1.data(), mu, M * sizeof(double), cudaMemcpyDeviceToHost);
+        cudaError_t e2 = cudaMemcpy(out.mu2.data(), nu, M * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e1 != cudaSuccess || e2 != cudaSuccess) {
+            set_error("cannot read device histograms");
+            return HOT_EINVAL;
+        }
+    } else if (space == HOT_SPACE_HOST) {
+        std::memcpy(out.mu1.data(), mu, M * sizeof(double));
+        std::memcpy(out.mu2.data(), nu, M * sizeof(double));
+    } else {
+        set_error("space must be HOT_SPACE_HOST or HOT_SPACE_DEVICE");
+        return HOT_EINVAL;
+    }
+    for (int w = 0; w < 2; ++w) {
+        const std::vector<double>& v = w ? out.mu2 : out.mu1;
+        double s = 0.0;
+        for (double x : v) {
+            if (!std::isfinite(x) || x < 0.0) {
+                set_error(std::string(w ? "nu" : "mu") + " has a negative or non-finite entry");
+                return HOT_EINVAL;
+            }
+            s += x;
+        }
+        if (std::fabs(s - 1.0) > 1e-9) {
+            char buf[128];
+            std::snprintf(buf, sizeof buf, "%s must sum to 1 (got %.17g)", w ? "nu" : "mu", s);
+            set_error(buf);
+            return HOT_EINVAL;
+        }
+    }
+    return HOT_OK;
+}
+
+// --------------------------------------------------------------- instances --
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int inst_create(const PairHost& p, int fp64, double sigma0_cfg, double tol, long long max_iter, int tr_override,
+                cudaStream_t st, Inst** out) {
+    *out = nullptr;
+    std::unique_ptr<Inst> I(new Inst());
+    const int S = p.S;
+    I->S = S;
+    I->fp64 = fp64;
+    I->TR = tr_override > 0 ? tr_override : tile_rows(S, fp64);
+    const int NV = fp64 ? 2 : 4;
+    const int P = kThreads / (S / NV);
+    if (I->TR > S || (size_t)I->TR * S > (size_t)(fp64 ? 4096 : 16384) || P < 1) {
+        set_error("invalid tile rows for this grid");
+        return HOT_EINVAL;
+    }
+    I->nb = (S + I->TR - 1) / I->TR;
+    I->n_k1 = (3 * S * S - 1 + kThreads - 1) / kThreads;
+    const size_t V = 2ull * S * S * S;
+    const size_t es = fp64 ? 8 : 4;
+    I->big_bytes = 5 * align256(V * es);
+
+    // small-buffer layout
+    const size_t SS = (size_t)S * S;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off += align256(bytes);
+        return o;
+    };
+    const size_t o_ab32 = fp64 ? 0 : take(4 * SS * sizeof(float4));
+    const size_t o_ab64 = take(4 * SS * 8);
+    const size_t o_dab = take(4 * SS * 8);
+    const size_t o_ab0 = take(4 * SS * 8);      // A^T y0 pieces: y0 = 0 at the start
+    const size_t o_rs = take(2 * SS * 8);
+    const size_t o_cs = take(2 * SS * I->nb * 8);
+    const size_t o_rs0 = take(2 * SS * 8);
+    const size_t o_cs0 = take(2 * SS * I->nb * 8);
+    const size_t o_xrs = take(2 * SS * 8);
+    const size_t o_xcs = take(2 * SS * I->nb * 8);
+    const size_t o_tk = take((size_t)2 * S * I->nb * kNK * 8);
+    const size_t o_rp = take((size_t)2 * S * I->nb * 2 * 8);
+    const size_t o_vec = take(4 * (size_t)S * 8);
+    const size_t o_zero_end = off;                 // everything above starts at 0
+    const size_t o_mu1 = take(SS * 8);
+    const size_t o_mu2 = take(SS * 8);
+    const size_t o_cm = take(S * 8);
+    const size_t o_rm = take(S * 8);
+    const size_t o_k1 = take((size_t)I->n_k1 * 8);
+    const size_t o_dp = take(2 * (size_t)S * 8);
+    const size_t o_ctl = take(sizeof(HotCtl));
+    I->small_bytes = off;
+
+    cudaError_t e = cudaMallocAsync((void**)&I->big, I->big_bytes, st);
+    if (e != cudaSuccess) {
+        set_error(std::string("device allocation of the flow state failed: ") + cudaGetErrorString(e));
+        return HOT_ENOMEM;
+    }
+    e = cudaMallocAsync((void**)&I->small, I->small_bytes, st);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(I->big, st);
+        set_error(std::string("device allocation failed: ") + cudaGetErrorString(e));
+        return HOT_ENOMEM;
+    }
+    HotInst& d = I->desc;
+    d.S = S;
+    d.TR = I->TR;
+    d.nb = I->nb;
+    d.n_k1 = I->n_k1;
+    d.fp64 = fp64;
+    // power-of-two cost scale: smallest 2^E >= max c = (S-1)^2
+    const double cmax = (double)(S - 1) * (S - 1);
+    int E = 0;
+    while (std::ldexp(1.0, E) < cmax) ++E;
+    d.E = E;
+    d.h = std::ldexp(1.0, -E);
+    I->cost_scale = std::ldexp(1.0, E);
+    double c4 = 0.0;
+    for (int a = 0; a < S; ++a)
+        for (int t = 0; t < S; ++t) {
+            const double dd = (double)(a - t) * (a - t);
+            c4 += dd * dd;
+        }
+    d.norm_c = d.h * std::sqrt(2.0 * S * c4);
+    double b2 = 0.0;
+    for (double x : p.mu1) b2 += x * x;
+    for (double x : p.mu2) b2 += x * x;
+    b2 -= p.mu2[SS - 1] * p.mu2[SS - 1];
+    d.norm_b = std::sqrt(b2);
+    char* big = I->big;
+    const size_t VB = align256(V * es);
+    d.u = big;
+    d.d0 = big + VB;
+    d.d1 = big + 2 * VB;
+    d.xr = big + 3 * VB;
+    d.zr = big + 4 * VB;
+    char* sm = I->small;
+    d.ab32 = fp64 ? nullptr : (float4*)(sm + o_ab32);
+    d.ab64 = (double*)(sm + o_ab64);
+    d.dab64 = (double*)(sm + o_dab);
+    d.ab0 = (double*)(sm + o_ab0);
+    d.rs = (double*)(sm + o_rs);
+    d.cs_part = (double*)(sm + o_cs);
+    d.rs0 = (double*)(sm + o_rs0);
+    d.cs0_part = (double*)(sm + o_cs0);
+    d.xrs = (double*)(sm + o_xrs);
+    d.xcs_part = (double*)(sm + o_xcs);
+    d.tile_kkt = (double*)(sm + o_tk);
+    d.rst_part = (double*)(sm + o_rp);
+    d.vecs = (double*)(sm + o_vec);
+    d.mu1 = (double*)(sm + o_mu1);
+    d.mu2 = (double*)(sm + o_mu2);
+    d.colmu1 = (double*)(sm + o_cm);
+    d.rowmu2 = (double*)(sm + o_rm);
+    d.k1_part = (double*)(sm + o_k1);
+    d.dobj_part = (double*)(sm + o_dp);
+    d.ctl = (HotCtl*)(sm + o_ctl);
+
+    // host-side constants uploaded once
+    std::vector<double> cm(S, 0.0), rm(S, 0.0);
+    for (int i = 0; i < S; ++i)
+        for (int j = 0; j < S; ++j) {
+            cm[j] += p.mu1[(size_t)i * S + j];
+            rm[i] += p.mu2[(size_t)i * S + j];
+        }
+    HotCtl c{};
+    c.sigma = sigma0_cfg > 0.0 ? sigma0_cfg : d.norm_b / d.norm_c;
+    c.tol = tol;
+    c.r0 = -1.0;
+    c.rprev = -1.0;
+    c.max_iter = max_iter;
+    c.status = ST_RUNNING;
+    I->ctl_host = c;
+
+    cudaError_t ee = cudaMemsetAsync(sm, 0, o_zero_end, st);
+    if (ee == cudaSuccess) ee = cudaMemcpyAsync(d.mu1, p.mu1.data(), SS * 8, cudaMemcpyHostToDevice, st);
+    if (ee == cudaSuccess) ee = cudaMemcpyAsync(d.mu2, p.mu2.data(), SS * 8, cudaMemcpyHostToDevice, st);
+    if (ee == cudaSuccess) ee = cudaMemcpyAsync(d.colmu1, cm.data(), S * 8, cudaMemcpyHostToDevice, st);
+    if (ee == cudaSuccess) ee = cudaMemcpyAsync(d.rowmu2, rm.data(), S * 8, cudaMemcpyHostToDevice, st);
+    if (ee == cudaSuccess) ee = cudaMemcpyAsync(d.ctl, &I->ctl_host, sizeof(HotCtl), cudaMemcpyHostToDevice, st);
+    if (ee == cudaSuccess) {
+        launch_init(d, c.sigma, st);   // u = -sigma0 c (w0 = 0), delta and restart references 0
+        ee = cudaGetLastError();
+    }
+    // the staging vectors above are pageable: cudaMemcpyAsync from pageable
+    // memory returns after the copy is staged, so they may go out of scope.
+    if (ee != cudaSuccess) {
+        cudaFreeAsync(I->small, st);
+        cudaFreeAsync(I->big, st);
+        set_error(std::string("instance initialisation failed: ") + cudaGetErrorString(ee));
+        return HOT_ECUDA;
+    }
+    *out = I.release();
+    return HOT_OK;
+}
+
+void inst_destroy(Inst* I, cudaStream_t st) {
+    if (!I) return;
+    if (I->big) cudaFreeAsync(I->big, st);
+    if (I->small) cudaFreeAsync(I->small, st);
+    delete I;
+}
+
+// ------------------------------------------------------------------- batch --
+
+Batch::~Batch() {
+    if (graph) cudaGraphExecDestroy(graph);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    cudaFree(d_work);
+    cudaFree(d_inst);
+    cudaFree(d_pre);
+    cudaFree(d_running);
+    cudaFree(d_st);
+    cudaFreeHost(h_work);
+    cudaFreeHost(h_inst);
+    cudaFreeHost(h_pre);
+    cudaFreeHost(h_running);
+    cudaFreeHost(h_st);
+}
+
+int Batch::reserve(int n) {
+    if (n <= cap && d_work) return HOT_OK;
+    int ncap = std::max(n, std::max(16, cap * 2));
+    // the graph captured the old table pointers
+    if (graph) {
+        cudaGraphExecDestroy(graph);
+        graph = nullptr;
+    }
+    cudaFree(d_work);
+    cudaFree(d_inst);
+    cudaFree(d_pre);
+    cudaFree(d_running);
+    cudaFree(d_st);
+    cudaFreeHost(h_work);
+    cudaFreeHost(h_inst);
+    cudaFreeHost(h_pre);
+    cudaFreeHost(h_running);
+    cudaFreeHost(h_st);
+    d_work = nullptr;
+    HOT_CK(cudaMalloc(&d_work, sizeof(WorkDev)));
+    HOT_CK(cudaMalloc(&d_inst, sizeof(HotInst) * ncap));
+    HOT_CK(cudaMalloc(&d_pre, sizeof(int) * 4 * (ncap + 1)));
+    HOT_CK(cudaMalloc(&d_running, sizeof(int)));
+    HOT_CK(cudaMalloc(&d_st, sizeof(int) * ncap));
+    HOT_CK(cudaMallocHost(&h_st, sizeof(int) * ncap));
+    HOT_CK(cudaMallocHost(&h_work, sizeof(WorkDev)));
+    HOT_CK(cudaMallocHost(&h_inst, sizeof(HotInst) * ncap));
+    HOT_CK(cudaMallocHost(&h_pre, sizeof(int) * 4 * (ncap + 1)));
+    HOT_CK(cudaMallocHost(&h_running, sizeof(int) * 4));
+    cap = ncap;
+    return HOT_OK;
+}
+
+int Batch::set_instances(const std::vector<Inst*>& v, cudaStream_t st) {
+    int rc = reserve((int)v.size());
+    if (rc != HOT_OK) return rc;
+    // the pinned staging is rewritten here: wait for earlier copies out of it
+    HOT_CK(cudaStreamSynchronize(st));
+    const int n = (int)v.size();
+    int* pt = h_pre;
+    int* ps = h_pre + (cap + 1);
+    int* pv = h_pre + 2 * (cap + 1);
+    int* pk = h_pre + 3 * (cap + 1);
+    pt[0] = ps[0] = pv[0] = pk[0] = 0;
+    int running = 0;
+    for (int i = 0; i < n; ++i) {
+        h_inst[i] = v[i]->desc;
+        const int S = v[i]->S;
+        pt[i + 1] = pt[i] + 2 * S * v[i]->nb;
+        ps[i + 1] = ps[i] + 2 * S;
+        pv[i + 1] = pv[i] + 4 * S;
+        pk[i + 1] = pk[i] + v[i]->n_k1;
+        if (v[i]->ctl_host.status == ST_RUNNING) ++running;
+    }
+    h_work->ninst = n;
+    h_work->inst = d_inst;
+    h_work->pre_tile = d_pre;
+    h_work->pre_slab = d_pre + (cap + 1);
+    h_work->pre_vec = d_pre + 2 * (cap + 1);
+    h_work->pre_k1 = d_pre + 3 * (cap + 1);
+    h_work->n_running = d_running;
+    h_work->st_out = d_st;
+    for (int i = 0; i < n; ++i) h_st[i] = v[i]->ctl_host.status;
+    h_running[0] = running;
+    if (n > 0) HOT_CK(cudaMemcpyAsync(d_inst, h_inst, sizeof(HotInst) * n, cudaMemcpyHostToDevice, st));
+    HOT_CK(cudaMemcpyAsync(d_pre, h_pre, sizeof(int) * 4 * (cap + 1), cudaMemcpyHostToDevice, st));
+    HOT_CK(cudaMemcpyAsync(d_work, h_work, sizeof(WorkDev), cudaMemcpyHostToDevice, st));
+    HOT_CK(cudaMemcpyAsync(d_running, h_running, sizeof(int), cudaMemcpyHostToDevice, st));
+    if (n > 0) HOT_CK(cudaMemcpyAsync(d_st, h_st, sizeof(int) * n, cudaMemcpyHostToDevice, st));
+    ninst = n;
+    return HOT_OK;
+}
+
+int Batch::ensure_graph() {
+    if (graph) return HOT_OK;
+    if (!cap_stream) HOT_CK(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
+    ld = make_launch_dims(device);
+    HOT_CK(cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal));
+    for (int j = 0; j < K; ++j) launch_iteration(d_work, ld, fp64, j, j == K - 1, cap_stream);
+    launch_block_end(d_work, ld, fp64, K, a1, a2, a3, cap_stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cap_stream, &g);
+    if (e != cudaSuccess) {
+        set_error(std::string("graph capture failed: ") + cudaGetErrorString(e));
+        return HOT_ECUDA;
+    }
+    e = cudaGraphInstantiate(&graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        graph = nullptr;
+        set_error(std::string("graph instantiation failed: ") + cudaGetErrorString(e));
+        return HOT_ECUDA;
+    }
+    return HOT_OK;
+}
+
+int Batch::launch_block(cudaStream_t st) const {
+    HOT_CK(cudaGraphLaunch(graph, st));
+    return HOT_OK;
+}
+
+// ------------------------------------------------------------------- solve --
+
+void fill_result(const Inst* I, hot_result* r) {
+    std::memset(r, 0, sizeof(*r));
+    const HotCtl& c = I->ctl_host;
+    r->ot_value = c.pobj;
+    r->dual_value = c.dobj;
+    r->rel_kkt = c.rel_kkt;
+    r->rel_dual = c.rel_dual;
+    r->rel_comp = c.rel_comp;
+    r->rel_primal = c.rel_primal;
+    r->sigma = c.sigma;
+    r->cost_scale = I->cost_scale;
+    r->iters = c.total;
+    r->restarts = c.restarts;
+    switch (c.status) {
+        case ST_CONVERGED: r->status = HOT_OK; break;
+        case ST_CAPPED: r->status = HOT_NOT_CONVERGED; break;
+        case ST_NUMERIC: r->status = HOT_NUMERIC; break;
+        case ST_CANCELLED: r->status = HOT_ECANCELLED; break;
+        default: r->status = HOT_PENDING; break;
+    }
+    unsigned int yb = c.ymax_bits;
+    float ym;
+    std::memcpy(&ym, &yb, 4);
+    r->max_abs_dual = ym;
+    r->m = r->n = I->S;
+}
+
+int run_solve(Ctx* ctx, const std::vector<PairHost>& pairs, double tol, long long max_iter, bool keep,
+              hot_result* out, hot_kernel_times* kt) {
+    cudaStream_t st = ctx->stream;
+    const int fp64 = ctx->cfg.precision == HOT_FP64 ? 1 : 0;
+    if (!ctx->batch || ctx->batch->fp64 != fp64) {
+        ctx->batch.reset(new Batch());
+        Batch& b = *ctx->batch;
+        b.device = ctx->device;
+        b.fp64 = fp64;
+        b.K = ctx->cfg.check_every;
+        b.a1 = ctx->cfg.restart_sufficient;
+        b.a2 = ctx->cfg.restart_necessary;
+        b.a3 = ctx->cfg.restart_long;
+    }
+    Batch& B = *ctx->batch;
+    std::vector<Inst*> insts;
+    insts.reserve(pairs.size());
+    auto cleanup = [&]() {
+        for (Inst* I : insts) inst_destroy(I, st);
+    };
+    for (const PairHost& p : pairs) {
+        Inst* I = nullptr;
+        int rc = inst_create(p, fp64, ctx->cfg.sigma0, tol, max_iter, ctx->tile_override, st, &I);
+        if (rc != HOT_OK) {
+            cleanup();
+            return rc;
+        }
+        insts.push_back(I);
+    }
+    int rc = B.set_instances(insts, st);
+    if (rc == HOT_OK) rc = B.ensure_graph();      // also fixes the launch dimensions
+    if (rc != HOT_OK) {
+        cleanup();
+        return rc;
+    }
+    cudaEvent_t t0, t1, ev[2];
+    cudaEventCreate(&t0);
+    cudaEventCreate(&t1);
+    cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming);
+    const long long K = B.K;
+    const long long max_blocks = (max_iter + K - 1) / K + 2;
+    long long nb = 0;
+    int err = HOT_OK;
+    // profiled mode: direct launches with an event pair around each kernel family
+    std::vector<cudaEvent_t> pev;
+    if (kt) {
+        std::memset(kt, 0, sizeof(*kt));
+        pev.resize(3 * K + 2);
+        for (auto& e : pev) cudaEventCreate(&e);
+    }
+    cudaEventRecord(t0, st);
+    for (;;) {
+        if (!kt) {
+            if (B.launch_block(st) != HOT_OK) {
+                err = HOT_ECUDA;
+                break;
+            }
+            cudaMemcpyAsync(&B.h_running[1 + (nb & 1)], B.d_running, sizeof(int), cudaMemcpyDeviceToHost, st);
+            cudaEventRecord(ev[nb & 1], st);
+            if (nb >= 1) {
+                cudaEventSynchronize(ev[(nb - 1) & 1]);
+                if (B.h_running[1 + ((nb - 1) & 1)] <= 0) {
+                    ++nb;
+                    break;
+                }
+            }
+        } else {
+            for (int j = 0; j < K; ++j) {
+                cudaEventRecord(pev[3 * j], st);
+                launch_solve_kernels(B.d_work, B.ld, st);
+                cudaEventRecord(pev[3 * j + 1], st);
+                launch_sweep(B.d_work, B.ld, fp64, j, j == K - 1, st);
+                cudaEventRecord(pev[3 * j + 2], st);
+            }
+            launch_block_end(B.d_work, B.ld, fp64, (int)K, B.a1, B.a2, B.a3, st);
+            cudaEventRecord(pev[3 * K], st);
+            cudaMemcpyAsync(&B.h_running[1], B.d_running, sizeof(int), cudaMemcpyDeviceToHost, st);
+            if (cudaStreamSynchronize(st) != cudaSuccess) {
+                err = HOT_ECUDA;
+                break;
+            }
+            for (int j = 0; j < K; ++j) {
+                float a = 0.f, b = 0.f;
+                cudaEventElapsedTime(&a, pev[3 * j], pev[3 * j + 1]);
+                cudaEventElapsedTime(&b, pev[3 * j + 1], pev[3 * j + 2]);
+                kt->solve_ms += a;
+                kt->solve_launches += 2;
+                if (j == K - 1) {
+                    kt->sweep_check_ms += b;
+                    kt->sweep_check_launches += 1;
+                } else {
+                    kt->sweep_ms += b;
+                    kt->sweep_launches += 1;
+                }
+            }
+            float c = 0.f;
+            cudaEventElapsedTime(&c, pev[3 * K - 1], pev[3 * K]);
+            kt->block_end_ms += c;
+            kt->block_end_launches += kLaunchesBlockEnd;
+            if (B.h_running[1] <= 0) {
+                ++nb;
+                break;
+            }
+        }
+        ++nb;
+        if (nb > max_blocks) break;   // every instance hits its cap before this
+    }
+    cudaEventRecord(t1, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, t0, t1);
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    for (auto& ee : pev) cudaEventDestroy(ee);
+    if (kt) {
+        double vb = 0.0;
+        for (Inst* I : insts) vb += 2.0 * I->S * (double)I->S * I->S * (fp64 ? 24.0 : 12.0);
+        kt->sweep_bytes = vb;
+    }
+    if (e != cudaSuccess || err != HOT_OK) {
+        set_error(std::string("solve failed on the device: ") + cudaGetErrorString(e != cudaSuccess ? e : cudaGetLastError()));
+        cleanup();
+        return HOT_ECUDA;
+    }
+    const long long launches = nb * (K * kLaunchesPerIteration + kLaunchesBlockEnd);
+    for (size_t q = 0; q < insts.size(); ++q) {
+        Inst* I = insts[q];
+        cudaMemcpy(&I->ctl_host, I->desc.ctl, sizeof(HotCtl), cudaMemcpyDeviceToHost);
+        fill_result(I, &out[q]);
+        out[q].solve_ms = ms;
+        out[q].kernel_launches = launches;
+        out[q].blocks = nb;
+        if (keep) {
+            const unsigned long long id = ctx->next_id++;
+            ctx->solutions[id].inst = I;
+            out[q].solution_id = id;
+        } else {
+            inst_destroy(I, st);
+        }
+    }
+    insts.clear();
+    return HOT_OK;
+}
+
+}  // namespace hot

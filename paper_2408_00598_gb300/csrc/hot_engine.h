@@ -1,0 +1,122 @@
+// Host engine of libhot: instance memory, batch work tables, the graph-captured
+// check block, and the context object behind the C ABI.
+#pragma once
+
+#include <atomic>
+#include <condition_variable>
+#include <cstdint>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/hot.h"
+#include "hot_internal.h"
+
+namespace hot {
+
+void set_error(const std::string& msg);
+const char* get_error();
+
+#define HOT_CK(call)                                                                          \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) {                                                              \
+            ::hot::set_error(std::string(#call) + ": " + cudaGetErrorString(e_));             \
+            return e_ == cudaErrorMemoryAllocation ? HOT_ENOMEM : HOT_ECUDA;                 \
+        }                                                                                     \
+    } while (0)
+
+// One instance's device memory and descriptor.
+struct Inst {
+    int S = 0;
+    int fp64 = 0;
+    int TR = 0, nb = 0, n_k1 = 0;
+    size_t big_bytes = 0, small_bytes = 0;
+    char* big = nullptr;     // v0, d0, d1, xr, zr
+    char* small = nullptr;   // sums, vectors, mu, ctl
+    HotInst desc{};
+    double cost_scale = 1.0;
+    HotCtl ctl_host{};       // last copy of the control block
+    double t_admit_ms = 0.0; // serve loop bookkeeping
+};
+
+// Host-side constants of a histogram pair (validated).
+struct PairHost {
+    int S = 0;
+    std::vector<double> mu1, mu2;
+};
+
+int validate_pair(const double* mu, const double* nu, int m, int n, int space, int fp64, PairHost& out);
+int tile_rows(int S, int fp64);
+
+// Allocate and initialise an instance on stream `st` (inputs already validated).
+int inst_create(const PairHost& p, int fp64, double sigma0_cfg, double tol, long long max_iter, int tr_override,
+                cudaStream_t st, Inst** out);
+void inst_destroy(Inst* I, cudaStream_t st);
+
+// Device work tables plus the instantiated block graph that reads them.
+struct Batch {
+    int device = 0;
+    int cap = 0;
+    int fp64 = 0;
+    int K = 10;
+    double a1 = 0.2, a2 = 0.8, a3 = 0.2;
+    WorkDev* d_work = nullptr;
+    HotInst* d_inst = nullptr;
+    int* d_pre = nullptr;
+    int* d_running = nullptr;
+    int* d_st = nullptr;            // [cap] per-instance status after each check
+    int* h_st = nullptr;            // pinned mirror
+    WorkDev* h_work = nullptr;      // pinned
+    HotInst* h_inst = nullptr;      // pinned
+    int* h_pre = nullptr;           // pinned
+    int* h_running = nullptr;       // pinned, [4]
+    cudaGraphExec_t graph = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    LaunchDims ld{};
+    int ninst = 0;
+    ~Batch();
+    int reserve(int n);
+    int set_instances(const std::vector<Inst*>& v, cudaStream_t st);   // async H2D
+    int ensure_graph();
+    int launch_block(cudaStream_t st) const;
+};
+
+struct Solution {
+    Inst* inst = nullptr;
+};
+
+struct ServeState;
+
+struct Ctx {
+    hot_config cfg{};
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::mutex mu;                         // serialises hot_solve* / recovery / solutions
+    std::unique_ptr<Batch> batch;          // for hot_solve / hot_solve_batch
+    std::map<unsigned long long, Solution> solutions;
+    std::atomic<unsigned long long> next_id{1};
+    std::unique_ptr<ServeState> serve;
+    int tile_override = 0;                 // testing hook: force TR (0 = default)
+    Ctx();
+    ~Ctx();
+};
+
+int run_solve(Ctx* ctx, const std::vector<PairHost>& pairs, double tol, long long max_iter, bool keep,
+              hot_result* out, hot_kernel_times* kt = nullptr);
+void fill_result(const Inst* I, hot_result* r);
+int recover_plan(Ctx* ctx, Inst* I, int32_t* src, int32_t* dst, double* mass, int space, size_t cap, size_t* nnz,
+                 double* marg_l1, cudaStream_t st);
+int export_flows(Inst* I, double* x, int space, cudaStream_t st);
+
+// serve loop (hot_serve.cpp)
+void serve_shutdown(Ctx* ctx);
+
+}  // namespace hot

@@ -1,0 +1,144 @@
+// Device-side data structures shared by the HOT kernels and the host engine.
+//
+// Layout of one instance (square grid, m = n = S) in device memory.  The flow
+// vector x = [f1; f2] of the reduced model (eq. 3-4 of arXiv 2408.00598) is
+// stored as 2S "slabs" of S x S values, slab-major, row-major inside a slab:
+//   slab s <  S : f1 for column j = s;      row = k, col = i   (f1_{i,k,j})
+//   slab s >= S : f2 for row    k = s - S;  row = j, col = l   (f2_{k,j,l})
+// so element (s, r, c) sits at s*S*S + r*S + c.  In both halves the cost is
+// (r - c)^2 (eq. 4), A^T y at (s, r, c) is alpha_s[r] + beta_s[c] with
+//   f1 slab j: alpha[k] =  y1(k,j), beta[i] = y2(i,j)
+//   f2 slab k: alpha[j] = -y1(k,j), beta[l] = y3(k,l)   (y3(S-1,S-1) = 0),
+// and the row and column sums of a slab are the A x products:
+//   (A x)_1(k,j) = rowsum(f1 slab j)[k] - rowsum(f2 slab k)[j]
+//   (A x)_2(i,j) = colsum(f1 slab j)[i]
+//   (A x)_3(k,l) = colsum(f2 slab k)[l]        ((S-1,S-1) row dropped, eq. 7-8)
+// Every reduction of the method is therefore slab-local.
+//
+// The iterate is kept in the reduced form v = x + sigma z (the shadow sequence
+// of App. A): the Halpern anchor v0 and the delta d = v - v0.  The anchor is
+// stored relative to sigma times its own reduced cost, u = v0 - sigma g0 with
+// g0 = c - A^T y0 (y0 the dual of the restart point), so every stored and
+// computed per-element quantity is small where the iteration cancels:
+//   v / sigma  = g0 + (u + d) / sigma,
+//   g - v/sigma = -A^T(y - y0) - (u + d)/sigma,
+//   x-bar      = u + d + sigma A^T(y - y0).
+// The same iterate, exactly; only the rounding of FP32 storage changes.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace hot {
+
+constexpr int kThreads = 256;          // block size of the tile kernels
+constexpr int kNK = 5;                 // per-tile check partials: r^2, min^2, x^2, z^2, c.x
+constexpr int kRowSmemBytes = 16384;   // row-partial buffer of a sweep tile
+constexpr int kMaxS = 1024;
+
+enum : int {
+    ST_RUNNING = 0,
+    ST_CONVERGED = 1,
+    ST_CAPPED = 2,
+    ST_NUMERIC = 3,
+    ST_CANCELLED = 4,
+};
+
+// Per-instance control block, mutated only by the block-end kernels
+// (k_check, k_restart_sigma, k_block_end) and read by every kernel.
+struct HotCtl {
+    double sigma;          // current sigma
+    double tol;            // relative KKT tolerance
+    double r0, rprev;      // restart residuals of the current cycle (< 0: unset)
+    double rel_kkt, rel_dual, rel_comp, rel_primal;
+    double pobj, dobj;     // unscaled primal <c,x-bar> and dual <b,y-bar>
+    double dx2, dz2;       // ||x-bar - x_r||^2, ||z-bar - z_r||^2 at the last restart
+    double sigma_old;      // sigma of the check iteration that triggered the last restart
+    double res_norm;       // ||w - w-bar||_M at the last check
+    long long total;       // iterations completed before the current block
+    long long max_iter;
+    int k;                 // Halpern counter at the start of the block
+    int status;            // ST_*
+    int restarts;
+    int restart_pending;   // set at a check, consumed by the restart kernels
+    int just_finished;     // set at the check that ends the solve
+    int cancel;            // host asks the instance to stop at the next check
+    unsigned int ymax_bits;// max |alpha|, |beta| (float bits, scaled units)
+    int pad;
+};
+
+// Per-instance descriptor (read-only while a block runs).
+struct HotInst {
+    int S;                 // grid side
+    int E;                 // cost scale 2^E >= (S-1)^2; scaled cost = (r-c)^2 * 2^-E
+    int TR;                // rows per sweep tile
+    int nb;                // bands (tiles) per slab = ceil(S / TR)
+    int n_k1;              // chunks of the A x - b kernel
+    int fp64;              // 1: FP64 state, 0: FP32 anchor + delta
+    double h;              // 2^-E
+    double norm_b;         // ||b||
+    double norm_c;         // ||c|| of the scaled problem
+    void* u;               // anchor, reduced: u = v0 - sigma (c - A^T y0)   [2S][S][S]
+    void* d0;              // delta, ping             [2S][S][S]
+    void* d1;              // delta, pong             [2S][S][S]
+    void* xr;              // x-bar at the last restart (final x-bar after the solve)
+    void* zr;              // z-bar at the last restart
+    float4* ab32;          // [2S][2][S] (hi, lo, delta, 0) of alpha then beta, FP32 mode
+    double* ab64;          // [2S][2][S] alpha then beta = A^T y-bar pieces (FP64)
+    double* ab0;           // [2S][2][S] the same pieces of A^T y0 at the anchor
+    double* dab64;         // [2S][2][S] ab64 - ab0 (FP64)
+    double* rs;            // [2S][S] row sums of the delta written by the last sweep
+    double* cs_part;       // [2S][nb][S] column partial sums of the delta
+    double* rs0;           // [2S][S] row sums of u (FP64)
+    double* cs0_part;      // [2S][nb][S] column partial sums of u
+    double* xrs;           // [2S][S] row sums of x-bar (check iterations)
+    double* xcs_part;      // [2S][nb][S]
+    double* tile_kkt;      // [2S*nb][kNK]
+    double* rst_part;      // [2S*nb][2]
+    double* vecs;          // [4][S]: T1, T2, P1, P2 (slab totals and cross-slab row sums)
+    double* mu1;           // [S][S] row-major mu1(i, j)
+    double* mu2;           // [S][S] row-major mu2(k, l)
+    double* colmu1;        // [S] sum_i mu1(i, j)
+    double* rowmu2;        // [S] sum_l mu2(k, l)
+    double* k1_part;       // [n_k1] partial ||A x - b||^2
+    double* dobj_part;     // [2S] partial <b, y>
+    HotCtl* ctl;
+};
+
+// Work tables of one batch, in device memory.  pre_* are prefix sums over the
+// instances of the number of work items each kernel family handles.
+struct WorkDev {
+    int ninst;
+    int pad;
+    HotInst* inst;         // [ninst]
+    int* pre_tile;         // sweep / restart tiles: 2S * nb per instance
+    int* pre_slab;         // k_alpha: 2S per instance
+    int* pre_vec;          // k_vec: 4S per instance (one warp each)
+    int* pre_k1;           // k_kkt1: n_k1 per instance
+    int* n_running;        // instances still running
+    int* st_out;           // [ninst] status of each instance after its last check
+};
+
+// Host-side launch helpers (hot_kernels.cu).
+struct LaunchDims {
+    int grid_tile;         // persistent grids (multiples of the SM count)
+    int grid_slab;
+    int grid_vec;
+    int grid_k1;
+    int grid_inst;
+};
+
+constexpr int kLaunchesPerIteration = 3;   // k_vec, k_alpha, k_sweep
+constexpr int kLaunchesBlockEnd = 7;       // k_kkt1, k_check, 3 x k_restart, k_restart_sigma, k_block_end
+void launch_solve_kernels(const WorkDev* w, const LaunchDims& ld, cudaStream_t st);
+void launch_sweep(const WorkDev* w, const LaunchDims& ld, int fp64, int j, bool check, cudaStream_t st);
+void launch_iteration(const WorkDev* w, const LaunchDims& ld, int fp64, int j, bool check, cudaStream_t st);
+void launch_block_end(const WorkDev* w, const LaunchDims& ld, int fp64, int K, double a1, double a2, double a3,
+                      cudaStream_t st);
+LaunchDims make_launch_dims(int device);
+// u = -sigma0 c, d = 0, x_r = z_r = 0 and the FP64 sums of u for a new instance
+// (the initial point w0 = 0: v0 = 0, y0 = 0).
+void launch_init(const HotInst& I, double sigma0, cudaStream_t st);
+cudaError_t kernels_init(int device);
+
+}  // namespace hot

@@ -1,0 +1,308 @@
+// Algorithm 1 of arXiv 2408.00598 on the GPU: the transport plan from the
+// reduced-model flows, one intermediate node (k, j) per warp ("parallelise the
+// (k, j) loop", Remark after Prop. 1).
+//
+// For node (k, j), Algorithm 1's inner loops (i = 1..m, then l = 1..n, move
+// min(f1_{i,k,j}, f2_{k,j,l}) and subtract it from both) are the north-west-
+// corner coupling of the sources a_i = f1_{i,k,j} with the sinks
+// b_l = f2_{k,j,l}: with exclusive prefix sums A_i, B_l, the mass moved from i
+// to l is the overlap of [A_i, A_{i+1}) and [B_l, B_{l+1}), and mass beyond
+// min(sum a, sum b) is left unassigned exactly as the sequential loop leaves
+// it.  Each lane takes a set of sources i, finds its first sink by binary
+// search and walks forward; entries are written in (node, i, l) order.
+// Flows are clipped at 0 first (an approximate solution may have small
+// negative entries).  In the slab layout both a and b are contiguous rows:
+// a = row k of f1 slab j, b = row j of f2 slab k.
+#include "hot_engine.h"
+
+namespace hot {
+
+constexpr int kRecWarps = 8;
+
+template <typename T>
+__device__ __forceinline__ void load_node(const T* __restrict__ x, int S, int k, int j, double* a, double* b,
+                                          double* A, double* B) {
+    const int lane = threadIdx.x & 31;
+    const T* ra = x + ((size_t)j * S + k) * S;            // f1 slab j, row k
+    const T* rb = x + ((size_t)(S + k) * S + j) * S;      // f2 slab k, row j
+    for (int t = lane; t < S; t += 32) {
+        a[t] = fmax((double)ra[t], 0.0);
+        b[t] = fmax((double)rb[t], 0.0);
+    }
+    __syncwarp();
+    // exclusive prefix sums, sequential per 32-chunk with a warp scan (FP64)
+    double carryA = 0.0, carryB = 0.0;
+    for (int base = 0; base < S; base += 32) {
+        const int t = base + lane;
+        double va = t < S ? a[t] : 0.0, vb = t < S ? b[t] : 0.0;
+        double sa = va, sb = vb;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const double ya = __shfl_up_sync(0xffffffffu, sa, o);
+            const double yb = __shfl_up_sync(0xffffffffu, sb, o);
+            if (lane >= o) {
+                sa += ya;
+                sb += yb;
+            }
+        }
+        if (t < S) {
+            A[t] = carryA + sa - va;
+            B[t] = carryB + sb - vb;
+        }
+        carryA += __shfl_sync(0xffffffffu, sa, 31);
+        carryB += __shfl_sync(0xffffffffu, sb, 31);
+    }
+    if (lane == 0) {
+        A[S] = carryA;
+        B[S] = carryB;
+    }
+    __syncwarp();
+}
+
+// number of sinks overlapping source i (and optionally write them)
+__device__ __forceinline__ int node_source(int S, int i, const double* A, const double* B, const double* b,
+                                           int32_t* src, int32_t* dst, double* mass, size_t pos, int src_id,
+                                           int node_k, int node_j, int n) {
+    const double lo = A[i];
+    const double hi = fmin(A[i + 1], B[S]);
+    if (!(hi > lo)) return 0;
+    // first l with B[l+1] > lo
+    int l0 = 0, l1 = S - 1;
+    while (l0 < l1) {
+        const int mid = (l0 + l1) >> 1;
+        if (B[mid + 1] > lo) l1 = mid; else l0 = mid + 1;
+    }
+    int cnt = 0;
+    for (int l = l0; l < S && B[l] < hi; ++l) {
+        const double p = fmin(hi, B[l + 1]) - fmax(lo, B[l]);
+        if (p > 0.0 && b[l] > 0.0) {
+            if (src) {
+                src[pos + cnt] = src_id;
+                dst[pos + cnt] = node_k * n + l;
+                mass[pos + cnt] = p;
+            }
+            ++cnt;
+        }
+    }
+    return cnt;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kRecWarps * 32) k_recover(const T* __restrict__ x, int S, int count_only,
+                                                            int* __restrict__ counts,
+                                                            const long long* __restrict__ offs,
+                                                            int32_t* __restrict__ src, int32_t* __restrict__ dst,
+                                                            double* __restrict__ mass, double* __restrict__ marg1,
+                                                            double* __restrict__ marg2) {
+    extern __shared__ double sh[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nw = blockDim.x >> 5;
+    double* a = sh + (size_t)warp * (4 * S + 2);
+    double* b = a + S;
+    double* A = b + S;
+    double* B = A + S + 1;
+    const int nodes = S * S;
+    for (int node = blockIdx.x * nw + warp; node < nodes; node += gridDim.x * nw) {
+        const int k = node / S, j = node % S;    // k-major node order
+        load_node(x, S, k, j, a, b, A, B);
+        if (count_only) {
+            int c = 0;
+            for (int i = lane; i < S; i += 32)
+                c += node_source(S, i, A, B, b, nullptr, nullptr, nullptr, 0, 0, k, j, S);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+            if (lane == 0) counts[node] = c;
+            // marginals of the plan: source (i, j) gets min(a_i, max(0, Btot - A_i)),
+            // target (k, l) gets min(b_l, max(0, Atot - B_l))
+            for (int t = lane; t < S; t += 32) {
+                const double ga = fmin(a[t], fmax(0.0, B[S] - A[t]));
+                const double gb = fmin(b[t], fmax(0.0, A[S] - B[t]));
+                if (ga > 0.0) atomicAdd(&marg1[(size_t)t * S + j], ga);
+                if (gb > 0.0) atomicAdd(&marg2[(size_t)k * S + t], gb);
+            }
+        } else {
+            long long pos = offs[node];
+            for (int base = 0; base < S; base += 32) {
+                const int i = base + lane;
+                int c = 0;
+                if (i < S) c = node_source(S, i, A, B, b, nullptr, nullptr, nullptr, 0, 0, k, j, S);
+                int incl = c;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                if (i < S && c > 0)
+                    node_source(S, i, A, B, b, src, dst, mass, (size_t)(pos + incl - c), i * S + j, k, j, S);
+                pos += __shfl_sync(0xffffffffu, incl, 31);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// exclusive scan of `n` ints into long long offsets (single block, chunked)
+__global__ void k_scan(const int* __restrict__ counts, long long* __restrict__ offs, int n,
+                       unsigned long long* __restrict__ total) {
+    __shared__ long long s_tot[1024];
+    __shared__ long long s_carry;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (int base = 0; base < n; base += blockDim.x) {
+        const int t = base + threadIdx.x;
+        const long long v = t < n ? counts[t] : 0;
+        s_tot[threadIdx.x] = v;
+        __syncthreads();
+        for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+            long long y = threadIdx.x >= (unsigned)o ? s_tot[threadIdx.x - o] : 0;
+            __syncthreads();
+            s_tot[threadIdx.x] += y;
+            __syncthreads();
+        }
+        if (t < n) offs[t] = s_carry + s_tot[threadIdx.x] - v;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) s_carry += s_tot[threadIdx.x];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = (unsigned long long)s_carry;
+}
+
+__global__ void k_marg_l1(const double* __restrict__ marg, const double* __restrict__ mu, int M,
+                          double* __restrict__ out) {
+    __shared__ double s[1024];
+    double acc = 0.0;
+    for (int t = threadIdx.x; t < M; t += blockDim.x) acc += fabs(marg[t] - mu[t]);
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < (unsigned)o) s[threadIdx.x] += s[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = s[0];
+}
+
+// x-bar from the slab layout into the paper's vec order (eq. 4-6):
+// f1_{i,k,j} at i + S k + S^2 j (same as slab j, row k, col i);
+// f2_{k,j,l} at S^3 + k + S j + S^2 l (slab S+k, row j, col l).
+template <typename T>
+__global__ void k_export(const T* __restrict__ x, int S, double* __restrict__ out) {
+    const size_t SS = (size_t)S * S;
+    const size_t half = SS * S;
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < 2 * half; q += (size_t)gridDim.x * blockDim.x) {
+        if (q < half) {
+            out[q] = (double)x[q];
+        } else {
+            const size_t p = q - half;            // internal f2 index: k*SS + j*S + l
+            const size_t k = p / SS, j = (p / S) % S, l = p % S;
+            out[half + k + S * j + SS * l] = (double)x[q];
+        }
+    }
+}
+
+int export_flows(Inst* I, double* x, int space, cudaStream_t st) {
+    const int S = I->S;
+    const size_t V = 2ull * S * S * S;
+    double* dst = x;
+    double* tmp = nullptr;
+    if (space == HOT_SPACE_HOST) {
+        HOT_CK(cudaMallocAsync(&tmp, V * 8, st));
+        dst = tmp;
+    }
+    const int grid = 1024;
+    if (I->fp64) k_export<double><<<grid, 256, 0, st>>>((const double*)I->desc.xr, S, dst);
+    else k_export<float><<<grid, 256, 0, st>>>((const float*)I->desc.xr, S, dst);
+    HOT_CK(cudaGetLastError());
+    if (tmp) {
+        HOT_CK(cudaMemcpyAsync(x, tmp, V * 8, cudaMemcpyDeviceToHost, st));
+        cudaFreeAsync(tmp, st);
+    }
+    HOT_CK(cudaStreamSynchronize(st));
+    return HOT_OK;
+}
+
+int recover_plan(Ctx* ctx, Inst* I, int32_t* src, int32_t* dst, double* mass, int space, size_t cap, size_t* nnz,
+                 double* marg_l1, cudaStream_t st) {
+    (void)ctx;
+    const int S = I->S;
+    const int nodes = S * S;
+    int* counts = nullptr;
+    long long* offs = nullptr;
+    unsigned long long* dtot = nullptr;
+    double* marg = nullptr;
+    double* l1 = nullptr;
+    HOT_CK(cudaMallocAsync(&counts, sizeof(int) * nodes, st));
+    HOT_CK(cudaMallocAsync(&offs, sizeof(long long) * nodes, st));
+    HOT_CK(cudaMallocAsync(&dtot, sizeof(unsigned long long), st));
+    HOT_CK(cudaMallocAsync(&marg, sizeof(double) * 2 * nodes, st));
+    HOT_CK(cudaMallocAsync(&l1, sizeof(double) * 2, st));
+    HOT_CK(cudaMemsetAsync(marg, 0, sizeof(double) * 2 * nodes, st));
+    // warps per CTA: each holds a, b and their prefix sums (4S + 2 doubles)
+    const int nw = std::max(1, std::min(kRecWarps, (int)((200 * 1024) / ((4 * S + 2) * sizeof(double)))));
+    const size_t shm = (size_t)nw * (4 * S + 2) * sizeof(double);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_recover<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_recover<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr_set = true;
+    }
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+    const int grid = std::max(1, std::min((nodes + nw - 1) / nw, sms * 8));
+    if (I->fp64)
+        k_recover<double><<<grid, nw * 32, shm, st>>>((const double*)I->desc.xr, S, 1, counts, nullptr,
+                                                              nullptr, nullptr, nullptr, marg, marg + nodes);
+    else
+        k_recover<float><<<grid, nw * 32, shm, st>>>((const float*)I->desc.xr, S, 1, counts, nullptr,
+                                                             nullptr, nullptr, nullptr, marg, marg + nodes);
+    HOT_CK(cudaGetLastError());
+    k_scan<<<1, 1024, 0, st>>>(counts, offs, nodes, dtot);
+    unsigned long long tot = 0;
+    HOT_CK(cudaMemcpyAsync(&tot, dtot, sizeof(tot), cudaMemcpyDeviceToHost, st));
+    HOT_CK(cudaStreamSynchronize(st));
+    *nnz = (size_t)tot;
+    int rc = HOT_OK;
+    if (marg_l1) {
+        // marginals against mu1 (row-major (i, j)) and mu2 (row-major (k, l))
+        k_marg_l1<<<1, 1024, 0, st>>>(marg, I->desc.mu1, nodes, l1);
+        k_marg_l1<<<1, 1024, 0, st>>>(marg + nodes, I->desc.mu2, nodes, l1 + 1);
+        HOT_CK(cudaMemcpyAsync(marg_l1, l1, sizeof(double) * 2, cudaMemcpyDeviceToHost, st));
+    }
+    if (cap > 0 || src || dst || mass) {
+        if (cap < tot) {
+            rc = HOT_EINVAL;
+            set_error("output capacity " + std::to_string(cap) + " < plan size " + std::to_string(tot));
+        } else if (tot > 0) {
+            int32_t *ds = src, *dd = dst;
+            double* dm = mass;
+            if (space == HOT_SPACE_HOST) {
+                HOT_CK(cudaMallocAsync(&ds, sizeof(int32_t) * tot, st));
+                HOT_CK(cudaMallocAsync(&dd, sizeof(int32_t) * tot, st));
+                HOT_CK(cudaMallocAsync(&dm, sizeof(double) * tot, st));
+            }
+            if (I->fp64)
+                k_recover<double><<<grid, nw * 32, shm, st>>>((const double*)I->desc.xr, S, 0, counts, offs,
+                                                                      ds, dd, dm, nullptr, nullptr);
+            else
+                k_recover<float><<<grid, nw * 32, shm, st>>>((const float*)I->desc.xr, S, 0, counts, offs,
+                                                                     ds, dd, dm, nullptr, nullptr);
+            HOT_CK(cudaGetLastError());
+            if (space == HOT_SPACE_HOST) {
+                HOT_CK(cudaMemcpyAsync(src, ds, sizeof(int32_t) * tot, cudaMemcpyDeviceToHost, st));
+                HOT_CK(cudaMemcpyAsync(dst, dd, sizeof(int32_t) * tot, cudaMemcpyDeviceToHost, st));
+                HOT_CK(cudaMemcpyAsync(mass, dm, sizeof(double) * tot, cudaMemcpyDeviceToHost, st));
+                cudaFreeAsync(ds, st);
+                cudaFreeAsync(dd, st);
+                cudaFreeAsync(dm, st);
+            }
+        }
+    }
+    cudaFreeAsync(counts, st);
+    cudaFreeAsync(offs, st);
+    cudaFreeAsync(dtot, st);
+    cudaFreeAsync(marg, st);
+    cudaFreeAsync(l1, st);
+    HOT_CK(cudaStreamSynchronize(st));
+    return rc;
+}
+
+}  // namespace hot

@@ -1,0 +1,40 @@
+"""Shared helpers of the GPU tests: oracle reference values (stored by
+tests/golden/make_oracle_values.py, or recomputed live when the inputs on
+this machine differ from the stored hash)."""
+import hashlib
+import json
+import os
+
+import numpy as np
+
+from paper_2408_00598_gb300 import synthetic as syn
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "oracle_values.json")
+
+
+def digest(mu1, mu2):
+    h = hashlib.sha256()
+    h.update(np.ascontiguousarray(mu1).tobytes())
+    h.update(np.ascontiguousarray(mu2).tobytes())
+    return h.hexdigest()
+
+
+def oracle_case(name):
+    """(mu1, mu2, record) for a stored case; the record is recomputed by the
+    oracle when this machine's generator output differs from the stored one."""
+    with open(GOLDEN) as f:
+        rec = json.load(f)["cases"][name]
+    mu1, mu2 = syn.make_pair(rec["kind"], rec["S"], rec["seed"])
+    if digest(mu1, mu2) != rec["sha256"]:
+        from oracle import hot
+        r = hot.hot_solve(mu1, mu2, tol=rec["tol"], max_iter=rec["max_iter"])
+        rec = dict(rec, ot_value=r.ot_value, dual_value=r.dual_value, rel_kkt=r.rel_kkt, iters=r.iters,
+                   restarts=r.restarts, live=True)
+    return mu1, mu2, rec
+
+
+def case_names(prefix):
+    if not os.path.exists(GOLDEN):
+        return []
+    with open(GOLDEN) as f:
+        return sorted(k for k in json.load(f)["cases"] if k.startswith(prefix))

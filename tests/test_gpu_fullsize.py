@@ -1,0 +1,88 @@
+"""Full-size cases (256 x 256 and 512 x 512, 3.4e7 and 2.7e8 flow variables),
+checked by properties that hold at any size: textbook closed forms of the
+optimal value (integer translation, product measures), the stopping rule, and
+the marginals of the recovered plan.
+
+At the paper's stopping rule (relative KKT 1e-6 in 2-norms over 1e7..1e8
+entries) the dual objective <b, y-bar> is close to the optimum, while the
+primal <c, x-bar> can still carry a negative part of x-bar of L1 size up to
+about sigma sqrt(V) ||A^T y + z - c||; the closed forms are therefore checked
+on the dual objective at 1e-6 and on both objectives at a tighter tolerance."""
+import numpy as np
+import pytest
+
+from oracle import closed_forms
+from paper_2408_00598_gb300 import synthetic as syn
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx(lib):
+    c = lib.Context(precision="fp32")
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2408_00598_gb300 import hot
+    hot.load_library()
+    return hot
+
+
+def test_translation_256(ctx):
+    mu1, mu2, s, t = syn.make_translation(256, 3, base_kind="gauss")
+    exact = closed_forms.translation_value(s, t)
+    r = ctx.solve(mu1, mu2, tol=1e-6, max_iter=200000)
+    n, l1 = ctx.recover_plan(r, device_out=())
+    ctx.release(r)
+    assert r["status"] == 0 and r["rel_kkt"] <= 1e-6
+    assert abs(r["dual_value"] - exact) <= 1e-3 * exact
+    assert n <= 256 * 256 * (2 * 256 - 1)
+    r = ctx.solve(mu1, mu2, tol=1e-8, max_iter=400000)
+    ctx.release(r)
+    assert r["status"] == 0
+    assert abs(r["dual_value"] - exact) <= 1e-5 * exact
+    assert abs(r["ot_value"] - exact) <= 1e-3 * exact
+
+
+def test_product_measure_256(ctx):
+    rng = np.random.default_rng(4)
+    p, q, p2, q2 = (rng.uniform(0.1, 1.0, 256) for _ in range(4))
+    p, q, p2, q2 = (v / v.sum() for v in (p, q, p2, q2))
+    exact = closed_forms.product_measure_value(p, q, p2, q2)
+    r = ctx.solve(np.outer(p, q), np.outer(p2, q2), tol=1e-7, max_iter=200000)
+    ctx.release(r)
+    assert r["status"] == 0 and r["rel_kkt"] <= 1e-7
+    assert abs(r["dual_value"] - exact) <= 1e-4 * exact
+
+
+def test_white_noise_256_gap_and_plan(lib, ctx):
+    import torch
+    mu1, mu2 = syn.make_pair("white", 256, 1)
+    r = ctx.solve(mu1, mu2, tol=1e-6, max_iter=200000)
+    n, l1 = ctx.recover_plan(r, device_out=())
+    src = torch.empty(n, dtype=torch.int32, device="cuda")
+    dst = torch.empty(n, dtype=torch.int32, device="cuda")
+    mass = torch.empty(n, dtype=torch.float64, device="cuda")
+    n2, _ = ctx.recover_plan(r, device_out=(src, dst, mass))
+    ctx.release(r)
+    assert n2 == n
+    assert r["status"] == 0 and r["rel_kkt"] <= 1e-6
+    S = 256
+    m1 = torch.zeros(S * S, dtype=torch.float64, device="cuda").index_add_(0, src.long(), mass)
+    assert abs(torch.abs(m1.cpu() - torch.from_numpy(mu1.reshape(-1))).sum().item() - l1[0]) <= 1e-9
+    assert (mass > 0).all().item()
+    node = (dst.long() // S) * S + (src.long() % S)
+    assert (node[1:] >= node[:-1]).all().item()
+    assert torch.bincount(node).max().item() <= 2 * S - 1
+
+
+def test_translation_512(ctx):
+    mu1, mu2, s, t = syn.make_translation(512, 5, base_kind="shapes")
+    exact = closed_forms.translation_value(s, t)
+    r = ctx.solve(mu1, mu2, tol=1e-6, max_iter=200000)
+    ctx.release(r)
+    assert r["status"] == 0
+    assert abs(r["dual_value"] - exact) <= 1e-3 * exact

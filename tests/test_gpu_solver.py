@@ -1,0 +1,292 @@
+"""GPU parity of the HOT solver (libhot through the C ABI) against the FP64 oracle.
+
+Tolerances:
+* FP64 mode runs the same arithmetic as the oracle in a different (reduced,
+  v = x + sigma z) form and summation order; iterates agree to ~1e-12
+  relative and the restart decisions coincide.
+* FP32 bulk mode: the stated target is the oracle's OT value to 1e-6 relative
+  at the stopping rule; iterates agree to the FP32 storage precision of the
+  flows (~1e-7 relative per step, damped by the nonexpansive iteration).
+"""
+import numpy as np
+import pytest
+
+from oracle import hot as ohot
+from oracle import recover as orec
+from oracle import reduced_model as rm
+from paper_2408_00598_gb300 import synthetic as syn
+from tests.gpu_helpers import case_names, oracle_case
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2408_00598_gb300 import hot
+    hot.load_library()
+    return hot
+
+
+@pytest.fixture(scope="module")
+def ctx32(lib):
+    c = lib.Context(precision="fp32")
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def ctx64(lib):
+    c = lib.Context(precision="fp64")
+    yield c
+    c.close()
+
+
+# ------------------------------------------------------------ iterate parity --
+
+@pytest.mark.parametrize("S,kind,seed", [(8, "white", 1), (12, "gauss", 2), (16, "white", 3), (20, "shapes", 4)])
+@pytest.mark.parametrize("iters", [10, 40, 200])
+def test_fp64_iterates_match_oracle(ctx64, S, kind, seed, iters):
+    """x-bar after a fixed number of iterations (tol = 0 never stops early)."""
+    mu1, mu2 = syn.make_pair(kind, S, seed)
+    ref = ohot.hot_solve(mu1, mu2, tol=0.0, max_iter=iters)
+    r = ctx64.solve(mu1, mu2, tol=0.0, max_iter=iters)
+    x = ctx64.flows(r)
+    ctx64.release(r)
+    assert r["iters"] == ref.iters == iters
+    assert r["restarts"] == ref.restarts
+    assert abs(r["sigma"] - ref.sigma) <= 1e-9 * ref.sigma
+    scale = np.abs(ref.x).max()
+    assert np.abs(x - ref.x).max() <= 1e-10 * scale
+    assert abs(r["rel_kkt"] - ref.rel_kkt) <= 1e-6 * ref.rel_kkt
+    assert abs(r["ot_value"] - ref.ot_value) <= 1e-11 * abs(ref.ot_value) + 1e-15
+
+
+@pytest.mark.parametrize("S,kind,seed", [(16, "white", 3), (20, "shapes", 4), (24, "gauss", 5)])
+def test_fp32_iterates_track_oracle(ctx32, S, kind, seed):
+    mu1, mu2 = syn.make_pair(kind, S, seed)
+    ref = ohot.hot_solve(mu1, mu2, tol=0.0, max_iter=200)
+    r = ctx32.solve(mu1, mu2, tol=0.0, max_iter=200)
+    x = ctx32.flows(r)
+    ctx32.release(r)
+    assert r["restarts"] == ref.restarts
+    scale = np.abs(ref.x).max()
+    assert np.abs(x - ref.x).max() <= 1e-4 * scale
+    assert abs(r["ot_value"] - ref.ot_value) <= 1e-5 * abs(ref.ot_value)
+
+
+# ------------------------------------------------------- converged parity --
+
+def test_config1_fp64_16x16_against_oracle_and_exact(ctx64):
+    """16x16 white noise, FP64 throughout, relative KKT 1e-8; exact min-cost flow."""
+    mu1, mu2, rec = oracle_case("c1_white16")
+    r = ctx64.solve(mu1, mu2, tol=1e-8, max_iter=100000)
+    ctx64.release(r)
+    assert r["status"] == 0 and r["rel_kkt"] <= 1e-8
+    assert r["iters"] == rec["iters"]
+    assert abs(r["ot_value"] - rec["ot_value"]) <= 1e-9 * rec["ot_value"]
+    assert abs(r["ot_value"] - rec["exact"]) <= 1e-5 * rec["exact"]
+
+
+def test_config1_fp32_16x16(ctx32):
+    mu1, mu2, rec = oracle_case("c1_white16")
+    r = ctx32.solve(mu1, mu2, tol=1e-8, max_iter=100000)
+    ctx32.release(r)
+    assert r["status"] == 0 and r["rel_kkt"] <= 1e-8
+    assert abs(r["ot_value"] - rec["ot_value"]) <= 1e-6 * rec["ot_value"]
+    assert abs(r["ot_value"] - rec["exact"]) <= 1e-5 * rec["exact"]
+
+
+@pytest.mark.parametrize("name", case_names("c2_") + case_names("s16_"))
+def test_fp32_value_parity_at_paper_stopping_rule(ctx32, name):
+    """Relative KKT 1e-6 (eq. kkt_res): FP32 bulk value within 1e-6 of the oracle."""
+    mu1, mu2, rec = oracle_case(name)
+    r = ctx32.solve(mu1, mu2, tol=rec["tol"], max_iter=rec["max_iter"])
+    ctx32.release(r)
+    assert r["status"] == 0 and r["rel_kkt"] <= rec["tol"]
+    assert abs(r["ot_value"] - rec["ot_value"]) <= 1e-6 * abs(rec["ot_value"]), (r["iters"], rec["iters"])
+    if "exact" in rec:
+        assert abs(r["ot_value"] - rec["exact"]) <= 5e-3 * rec["exact"]
+
+
+@pytest.mark.parametrize("name", case_names("c2_"))
+def test_fp64_value_parity(ctx64, name):
+    mu1, mu2, rec = oracle_case(name)
+    r = ctx64.solve(mu1, mu2, tol=rec["tol"], max_iter=rec["max_iter"])
+    ctx64.release(r)
+    assert r["status"] == 0
+    assert r["iters"] == rec["iters"]
+    assert abs(r["ot_value"] - rec["ot_value"]) <= 1e-9 * abs(rec["ot_value"])
+
+
+# ---------------------------------------------------------- edge cases --
+
+def test_identical_histograms(ctx32):
+    """mu = nu: the value is 0; at rel-KKT 1e-8 the iterate's <c, x-bar> is
+    within the same few 1e-6 of it as the oracle's."""
+    mu1, _ = syn.make_pair("gauss", 16, 9)
+    ref = ohot.hot_solve(mu1, mu1.copy(), tol=1e-8)
+    r = ctx32.solve(mu1, mu1.copy(), tol=1e-8, max_iter=100000)
+    ctx32.release(r)
+    assert r["status"] == 0 and r["iters"] == ref.iters
+    assert abs(r["ot_value"] - ref.ot_value) <= 1e-8
+    assert abs(r["ot_value"]) <= 1e-4 and abs(r["dual_value"]) <= 1e-4
+
+
+@pytest.mark.parametrize("S", [8, 16, 32])
+def test_dirac_to_dirac(ctx32, S):
+    mu1 = np.zeros((S, S))
+    mu2 = np.zeros((S, S))
+    mu1[1, 2] = 1.0
+    mu2[S - 2, S - 1] = 1.0
+    r = ctx32.solve(mu1, mu2, tol=1e-9, max_iter=200000)
+    ctx32.release(r)
+    ref = (S - 3) ** 2 + (S - 3) ** 2
+    assert r["status"] == 0
+    assert abs(r["ot_value"] - ref) <= 1e-5 * ref
+
+
+@pytest.mark.parametrize("S", [12, 20, 28, 44])
+def test_non_power_of_two_sizes(ctx32, S):
+    mu1, mu2 = syn.make_pair("white", S, S)
+    ref = ohot.hot_solve(mu1, mu2, tol=0.0, max_iter=60)
+    r = ctx32.solve(mu1, mu2, tol=0.0, max_iter=60)
+    x = ctx32.flows(r)
+    ctx32.release(r)
+    assert r["restarts"] == ref.restarts
+    assert np.abs(x - ref.x).max() <= 1e-4 * np.abs(ref.x).max()
+
+
+def test_invalid_inputs_are_rejected(lib, ctx32):
+    good1, good2 = syn.make_pair("white", 16, 1)
+    bad = good1.copy()
+    bad[0, 0] = -1e-3
+    bad /= bad.sum()
+    nan = good1.copy()
+    nan[3, 3] = np.nan
+    cases = [(bad, good2), (good1 * 1.01, good2), (nan, good2), (good1[:, :12] / good1[:, :12].sum(), good2[:, :12]),
+             (syn.make_pair("white", 6, 1)[0], syn.make_pair("white", 6, 1)[1]),
+             (syn.make_pair("white", 10, 1)[0], syn.make_pair("white", 10, 1)[1])]
+    for a, b in cases:
+        with pytest.raises(lib.HotError) as e:
+            ctx32.solve(a, b)
+        assert e.value.status == lib.HOT_EINVAL
+    with pytest.raises(lib.HotError):
+        ctx32.solve(good1, good2, tol=-1.0)
+
+
+def test_device_inputs_match_host_inputs(lib, ctx32):
+    import torch
+    mu1, mu2 = syn.make_pair("cauchy", 32, 5)
+    r1 = ctx32.solve(mu1, mu2, tol=1e-6)
+    r2 = ctx32.solve(torch.from_numpy(mu1).cuda(), torch.from_numpy(mu2).cuda(), tol=1e-6)
+    ctx32.release(r1)
+    ctx32.release(r2)
+    assert r1["ot_value"] == r2["ot_value"] and r1["iters"] == r2["iters"]
+
+
+def test_solves_are_deterministic(ctx32):
+    mu1, mu2 = syn.make_pair("shapes", 48, 7)
+    a = ctx32.solve(mu1, mu2, tol=1e-6)
+    b = ctx32.solve(mu1, mu2, tol=1e-6)
+    ctx32.release(a)
+    ctx32.release(b)
+    assert a["ot_value"] == b["ot_value"] and a["iters"] == b["iters"] and a["rel_kkt"] == b["rel_kkt"]
+
+
+def test_flows_are_in_the_paper_vec_order(ctx32):
+    """A x-bar = b (App. C) holds for the exported flows with the oracle's A."""
+    S = 16
+    mu1, mu2 = syn.make_pair("gauss", S, 2)
+    r = ctx32.solve(mu1, mu2, tol=1e-8)
+    x = ctx32.flows(r)
+    ctx32.release(r)
+    A = rm.build_A(S, S)
+    b = rm.build_b(mu1, mu2)
+    assert np.abs(A @ x - b).max() <= 1e-7 * np.abs(b).max()
+    assert abs(rm.build_c(S, S) @ x - r["ot_value"]) <= 1e-8 * r["ot_value"]
+
+
+# ------------------------------------------------------------- recovery --
+
+def _dense_plan(entries, S):
+    P = np.zeros((S * S, S * S))
+    for i, j, k, l, p in entries:
+        P[i * S + j, k * S + l] += p
+    return P
+
+
+def test_recovery_matches_oracle_algorithm1(ctx64):
+    """Algorithm 1 on the GPU vs the literal loops on the oracle's own x-bar."""
+    S = 16
+    mu1, mu2 = syn.make_pair("white", S, 1)
+    ref = ohot.hot_solve(mu1, mu2, tol=1e-8)
+    r = ctx64.solve(mu1, mu2, tol=1e-8)
+    src, dst, mass, l1 = ctx64.recover_plan(r)
+    ctx64.release(r)
+    ent = orec.recover_from_x(ref.x, S, S)
+    Pg = np.zeros((S * S, S * S))
+    np.add.at(Pg, (src, dst), mass)
+    Po = _dense_plan(ent, S)
+    assert np.abs(Pg - Po).max() <= 1e-10
+    assert mass.min() > 0
+    # entries per node (k, j) <= m + n - 1 and ordered by node, then i, then l
+    node = (dst // S) * S + (src % S)
+    assert np.all(np.diff(node) >= 0)
+    assert np.bincount(node).max() <= 2 * S - 1
+    rs, ts = orec.plan_marginals(ent, S, S)
+    assert abs(l1[0] - np.abs(rs - mu1).sum()) <= 1e-10
+    assert abs(l1[1] - np.abs(ts - mu2).sum()) <= 1e-10
+
+
+@pytest.mark.parametrize("kind", ["white", "gauss", "shapes"])
+def test_recovered_plan_marginals_fp32(ctx32, kind):
+    """Properties of Algorithm 1 on approximate flows that hold at any size:
+    the reported L1 marginal errors are those of the returned entries; they
+    are bounded by the mass the clipping adds plus what the nodes cannot pass
+    on; the plan cost is the cost of the routed part of the clipped flows."""
+    S = 64
+    mu1, mu2 = syn.make_pair(kind, S, 3)
+    r = ctx32.solve(mu1, mu2, tol=1e-6)
+    x = ctx32.flows(r)
+    src, dst, mass, l1 = ctx32.recover_plan(r)
+    ctx32.release(r)
+    Mg1 = np.bincount(src, weights=mass, minlength=S * S).reshape(S, S)
+    Mg2 = np.bincount(dst, weights=mass, minlength=S * S).reshape(S, S)
+    assert abs(np.abs(Mg1 - mu1).sum() - l1[0]) <= 1e-9
+    assert abs(np.abs(Mg2 - mu2).sum() - l1[1]) <= 1e-9
+    f1, f2 = rm.split_x(x, S, S)
+    neg = -np.minimum(x, 0.0).sum()
+    # per node, the unassigned mass is |sum f1 - sum f2| of the clipped flows
+    node_gap = np.abs(np.maximum(f1, 0).sum(axis=0) - np.maximum(f2, 0).sum(axis=2)).sum()
+    assert l1[0] <= 2 * neg + node_gap + 1e-7
+    assert l1[1] <= 2 * neg + node_gap + 1e-7
+    cost = (((src // S) - (dst // S)) ** 2 + ((src % S) - (dst % S)) ** 2) @ mass
+    clip_cost = rm.build_c(S, S) @ np.maximum(x, 0.0)
+    assert cost <= clip_cost * (1 + 1e-9)
+    assert cost >= clip_cost - 2 * (S - 1) ** 2 * node_gap - 1e-9
+    assert mass.min() > 0
+
+
+def test_recovered_plan_marginals_tight_tolerance(ctx32):
+    """At a tight tolerance the plan's marginals match mu and nu to 1e-6 in L1."""
+    S = 32
+    mu1, mu2 = syn.make_pair("gauss", S, 3)
+    r = ctx32.solve(mu1, mu2, tol=1e-9, max_iter=200000)
+    src, dst, mass, l1 = ctx32.recover_plan(r)
+    ctx32.release(r)
+    assert r["status"] == 0
+    assert l1[0] <= 1e-6 and l1[1] <= 1e-6
+
+
+# ---------------------------------------------------------------- batch --
+
+def test_batch_equals_single_solves(lib, ctx32):
+    pairs = [syn.make_pair(k, S, s) for k, S, s in
+             [("white", 16, 1), ("gauss", 32, 2), ("shapes", 48, 3), ("cauchy", 64, 4), ("translate", 32, 5),
+              ("white", 96, 6), ("gauss", 128, 7)]]
+    out = ctx32.solve_batch([p[0] for p in pairs], [p[1] for p in pairs], tol=1e-6)
+    for (a, b), rb in zip(pairs, out):
+        rs = ctx32.solve(a, b, tol=1e-6)
+        ctx32.release(rs)
+        assert rb["status"] == 0
+        assert rb["ot_value"] == rs["ot_value"] and rb["iters"] == rs["iters"]
