@@ -40,7 +40,7 @@ SWEEP_TRAFFIC = {"kernels_sha256": None, "bytes_per_launch": None}
 
 # iterations of Algorithm 2 (with the restart rule) to rel-KKT tol for the
 # default bench pair, measured with the device solver
-ITERS_PER_SOLVE = {}
+ITERS_PER_SOLVE = {(256, "white", 1e-6): 450}
 
 
 def parse():

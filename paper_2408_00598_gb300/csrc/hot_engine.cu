@@ -137,6 +137,7 @@ int inst_create(const PairHost& p, int fp64, double sigma0_cfg, double tol, long
     const size_t o_tk = take((size_t)2 * S * I->nb * kNK * 8);
     const size_t o_rp = take((size_t)2 * S * I->nb * 2 * 8);
     const size_t o_vec = take(4 * (size_t)S * 8);
+    const size_t o_mvec = take(4 * (size_t)S * 8);
     const size_t o_zero_end = off;                 // everything above starts at 0
     const size_t o_mu1 = take(SS * 8);
     const size_t o_mu2 = take(SS * 8);
@@ -204,6 +205,7 @@ int inst_create(const PairHost& p, int fp64, double sigma0_cfg, double tol, long
     d.tile_kkt = (double*)(sm + o_tk);
     d.rst_part = (double*)(sm + o_rp);
     d.vecs = (double*)(sm + o_vec);
+    d.mvec = (double*)(sm + o_mvec);
     d.mu1 = (double*)(sm + o_mu1);
     d.mu2 = (double*)(sm + o_mu2);
     d.colmu1 = (double*)(sm + o_cm);
@@ -491,7 +493,7 @@ int run_solve(Ctx* ctx, const std::vector<PairHost>& pairs, double tol, long lon
                 cudaEventElapsedTime(&a, pev[3 * j], pev[3 * j + 1]);
                 cudaEventElapsedTime(&b, pev[3 * j + 1], pev[3 * j + 2]);
                 kt->solve_ms += a;
-                kt->solve_launches += 2;
+                kt->solve_launches += 3;
                 if (j == K - 1) {
                     kt->sweep_check_ms += b;
                     kt->sweep_check_launches += 1;

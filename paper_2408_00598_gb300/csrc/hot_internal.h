@@ -96,6 +96,7 @@ struct HotInst {
     double* tile_kkt;      // [2S*nb][kNK]
     double* rst_part;      // [2S*nb][2]
     double* vecs;          // [4][S]: T1, T2, P1, P2 (slab totals and cross-slab row sums)
+    double* mvec;          // [4][S]: instance-wide vectors of Prop. 3 (k_marg)
     double* mu1;           // [S][S] row-major mu1(i, j)
     double* mu2;           // [S][S] row-major mu2(k, l)
     double* colmu1;        // [S] sum_i mu1(i, j)
@@ -128,7 +129,7 @@ struct LaunchDims {
     int grid_inst;
 };
 
-constexpr int kLaunchesPerIteration = 3;   // k_vec, k_alpha, k_sweep
+constexpr int kLaunchesPerIteration = 4;   // k_vec, k_marg, k_alpha, k_sweep
 constexpr int kLaunchesBlockEnd = 7;       // k_kkt1, k_check, 3 x k_restart, k_restart_sigma, k_block_end
 void launch_solve_kernels(const WorkDev* w, const LaunchDims& ld, cudaStream_t st);
 void launch_sweep(const WorkDev* w, const LaunchDims& ld, int fp64, int j, bool check, cudaStream_t st);

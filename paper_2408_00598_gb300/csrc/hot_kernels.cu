@@ -261,20 +261,103 @@ __global__ void __launch_bounds__(kThreads) k_vec(const WorkDev* __restrict__ W)
     }
 }
 
-// --------------------------------------------------------------- k_alpha --
-// Prop. 3 for every slab.  With v = sigma g0 + u + d, the right-hand side of
-// eq. (update:y) is R = b/sigma - A(v/sigma - c) = AA^T y0 + (b - A(u + d))/sigma,
-// so dy = y-bar - y0 solves AA^T dy = R' := (b - A(u + d))/sigma; R' comes from
-// the slab sums of u + d.  With m = n = S:
+// ---------------------------------------------------------- k_marg/k_alpha --
+// Prop. 3 on R' = (b - A(u + d))/sigma, the right-hand side whose solution is
+// dy = y-bar - y0: with v = sigma g0 + u + d, the right-hand side of
+// eq. (update:y) is R = b/sigma - A(v/sigma - c) = AA^T y0 + R'.  R' comes
+// from the slab sums of u + d.  With m = n = S:
 //   a_j = sum_k R1(k,j), bb_j = sum_i R2(i,j), r3_k = sum_l R3(k,l), T3 = sum r3,
 //   y1-hat(k,j) = (R1(k,j) + a_j/n - (1/m+1/n) bb_j + r3_k/n + T3/n^2)/(m+n),
 //   s_k = sum_j y1-hat(k,j),  t = W-hat s,  y1^a = t + (1^T t / n) 1,
 //   y1 = y1-hat - y1^a,  y2(i,j) = (R2(i,j) - sum_k y1(k,j))/m,
 //   y3(k,l) = (R3(k,l) + sum_j y1(k,j))/n.
-// Outputs per slab: dA pieces (dab64), the full pieces ab64 = ab0 + dab64,
-// and in FP32 mode their (hi on the grid 2^-E, lo, delta) float split.
+// k_marg (one CTA per instance) forms the O(S) vectors shared by all slabs:
+//   mv[0..S)   a_j / n - (1/m + 1/n) bb_j        (column part of y1-hat)
+//   mv[S..2S)  r3_k / n + T3 / n^2 - (m+n) y1^a_k (row part of y1, times m+n)
+//   mv[2S..3S) sum_k y1(k,j)                      (for y2)
+//   mv[3S..4S) sum_j y1(k,j)                      (for y3)
+// k_alpha (one CTA per slab) then forms the slab's entries with products only
+// (FP64 division is slow on this part; reciprocals are taken once).
+__global__ void __launch_bounds__(kThreads) k_marg(const WorkDev* __restrict__ W) {
+    __shared__ double s_red[4 * 32];
+    const int ninst = W->ninst;
+    for (int inst = blockIdx.x; inst < ninst; inst += gridDim.x) {
+        const HotInst& I = W->inst[inst];
+        if (I.ctl->status != ST_RUNNING) continue;     // block-uniform
+        const int S = I.S, nb = I.nb;
+        const double m = S, n = S;
+        const double is = 1.0 / I.ctl->sigma;
+        const double in_ = 1.0 / n, im = 1.0 / m, imn = 1.0 / (m + n);
+        const double* T1 = I.vecs;
+        const double* T2 = I.vecs + S;
+        const double* P1 = I.vecs + 2 * S;
+        const double* P2 = I.vecs + 3 * S;
+        double* mv = I.mvec;
+        double kap_last = 0.0;                         // column S-1 of the last f2 slab (dropped row)
+        {
+            const int sl = 2 * S - 1;
+            for (int b = 0; b < nb; ++b)
+                kap_last += I.cs_part[((size_t)sl * nb + b) * S + (S - 1)] + I.cs0_part[((size_t)sl * nb + b) * S + (S - 1)];
+        }
+        // pass 1: a, bb, r3 and their sums
+        double red[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int q = threadIdx.x; q < S; q += blockDim.x) {
+            const double aq = -(T1[q] - P2[q]) * is;
+            const double bq = (I.colmu1[q] - T1[q]) * is;
+            double r3q = (I.rowmu2[q] - T2[q]) * is;
+            if (q == S - 1) r3q -= (I.mu2[(size_t)(S - 1) * S + (S - 1)] - kap_last) * is;
+            mv[q] = aq;                 // temporarily a
+            mv[2 * S + q] = bq;         // temporarily bb
+            mv[S + q] = r3q;            // temporarily r3
+            mv[3 * S + q] = -(P1[q] - T2[q]) * is;   // temporarily row sums of R1
+            red[0] += aq;
+            red[1] += bq;
+            red[2] += r3q;
+        }
+        block_sum<4>(red, s_red);
+        const double Asum = red[0], Bsum = red[1], T3 = red[2];
+        const double dl = (1.0 - in_) / (m + 1.0);
+        const double iw = 1.0 / (im - dl);             // 1/w, w = 1/m - (1-1/n)/(m+1)
+        // pass 2: s_k and d^T s
+        red[0] = red[1] = red[2] = red[3] = 0.0;
+        for (int q = threadIdx.x; q < S; q += blockDim.x) {
+            const double s = (mv[3 * S + q] + Asum * in_ - (im + in_) * Bsum + mv[S + q] + T3 * in_) * imn;
+            mv[3 * S + q] = s;
+            red[0] += (q == S - 1 ? dl : im) * s;
+        }
+        block_sum<4>(red, s_red);
+        const double ds = red[0];
+        // pass 3: t = W-hat s and 1^T t
+        red[0] = red[1] = red[2] = red[3] = 0.0;
+        for (int q = threadIdx.x; q < S; q += blockDim.x) {
+            const double dq = (q == S - 1 ? dl : im);
+            red[0] += -dq * mv[3 * S + q] - dq * ds * iw;
+        }
+        block_sum<4>(red, s_red);
+        const double tsum = red[0];
+        // pass 4: y1^a and its sum
+        red[0] = red[1] = red[2] = red[3] = 0.0;
+        for (int q = threadIdx.x; q < S; q += blockDim.x) {
+            const double dq = (q == S - 1 ? dl : im);
+            red[0] += -dq * mv[3 * S + q] - dq * ds * iw + tsum * in_;
+        }
+        block_sum<4>(red, s_red);
+        const double yasum = red[0];
+        // pass 5: final vectors (each thread rewrites only its own q)
+        for (int q = threadIdx.x; q < S; q += blockDim.x) {
+            const double dq = (q == S - 1 ? dl : im);
+            const double ya = -dq * mv[3 * S + q] - dq * ds * iw + tsum * in_;
+            const double aq = mv[q], bq = mv[2 * S + q], r3q = mv[S + q], sq = mv[3 * S + q];
+            mv[q] = aq * in_ - (im + in_) * bq;
+            mv[S + q] = r3q * in_ + T3 * in_ * in_ - (m + n) * ya;
+            mv[2 * S + q] = (aq - bq + T3 * in_) * in_ - yasum;
+            mv[3 * S + q] = sq - n * ya;
+        }
+        __syncthreads();
+    }
+}
+
 __global__ void __launch_bounds__(kThreads) k_alpha(const WorkDev* __restrict__ W) {
-    extern __shared__ double sm[];            // 5*S: a, bb, r3, s, ya
     __shared__ double s_red[4 * 32];
     __shared__ float s_max[32];
     __shared__ int s_t[4];
@@ -297,68 +380,10 @@ __global__ void __launch_bounds__(kThreads) k_alpha(const WorkDev* __restrict__ 
         const int S = I.S, nb = I.nb;
         const double m = S, n = S;
         const double is = 1.0 / I.ctl->sigma;
-        double* a = sm;
-        double* bb = sm + S;
-        double* r3 = sm + 2 * S;
-        double* sv = sm + 3 * S;
-        double* ya = sm + 4 * S;
-        const double* T1 = I.vecs;
-        const double* T2 = I.vecs + S;
-        const double* P1 = I.vecs + 2 * S;
-        const double* P2 = I.vecs + 3 * S;
+        const double im = 1.0 / m, in_ = 1.0 / n, imn = 1.0 / (m + n);
         const double* __restrict__ rs = I.rs;
         const double* __restrict__ rs0 = I.rs0;
-
-        // column sum (S-1) of the last f2 slab: the dropped (m, n) row of eq. (7)
-        double kap_last = 0.0;
-        {
-            const int sl = 2 * S - 1;
-            for (int b = 0; b < nb; ++b)
-                kap_last += I.cs_part[((size_t)sl * nb + b) * S + (S - 1)] + I.cs0_part[((size_t)sl * nb + b) * S + (S - 1)];
-        }
-        double red[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int q = threadIdx.x; q < S; q += blockDim.x) {
-            const double aq = -(T1[q] - P2[q]) * is;
-            const double bq = (I.colmu1[q] - T1[q]) * is;
-            double r3q = (I.rowmu2[q] - T2[q]) * is;
-            if (q == S - 1) r3q -= (I.mu2[(size_t)(S - 1) * S + (S - 1)] - kap_last) * is;
-            a[q] = aq;
-            bb[q] = bq;
-            r3[q] = r3q;
-            sv[q] = -(P1[q] - T2[q]) * is;    // row sums of R1 for now
-            red[0] += aq;
-            red[1] += bq;
-            red[2] += r3q;
-        }
-        block_sum<4>(red, s_red);
-        const double Asum = red[0], Bsum = red[1], T3 = red[2];
-        const double dlast = (1.0 - 1.0 / n) / (m + 1.0);
-        const double wq = 1.0 / m - (1.0 - 1.0 / n) / (m + 1.0);
-        red[0] = red[1] = red[2] = red[3] = 0.0;
-        for (int q = threadIdx.x; q < S; q += blockDim.x) {
-            const double s = (sv[q] + Asum / n - (1.0 / m + 1.0 / n) * Bsum + r3[q] + T3 / n) / (m + n);
-            sv[q] = s;
-            red[0] += (q == S - 1 ? dlast : 1.0 / m) * s;
-        }
-        block_sum<4>(red, s_red);
-        const double ds = red[0];
-        red[0] = red[1] = red[2] = red[3] = 0.0;
-        for (int q = threadIdx.x; q < S; q += blockDim.x) {
-            const double dq = (q == S - 1 ? dlast : 1.0 / m);
-            const double tq = -dq * sv[q] - dq * ds / wq;    // t = W-hat s
-            ya[q] = tq;
-            red[0] += tq;
-        }
-        block_sum<4>(red, s_red);
-        const double tsum = red[0];
-        red[0] = red[1] = red[2] = red[3] = 0.0;
-        for (int q = threadIdx.x; q < S; q += blockDim.x) {
-            ya[q] += tsum / n;                                  // y1^a = (I + 11^T/n) t
-            red[0] += ya[q];
-        }
-        block_sum<4>(red, s_red);
-        const double yasum = red[0];
-
+        const double* __restrict__ mv = I.mvec;
         const size_t o = (size_t)slab * 2 * S;
         double* out_d = I.dab64 + o;
         double* out_f = I.ab64 + o;
@@ -382,49 +407,42 @@ __global__ void __launch_bounds__(kThreads) k_alpha(const WorkDev* __restrict__ 
         };
         if (slab < S) {
             const int j = slab;
-            const double colY1 = (a[j] - bb[j] + T3 / n) / n - yasum;
+            const double colj = mv[j];
             for (int k = threadIdx.x; k < S; k += blockDim.x) {
                 const double R1 = -((rs[(size_t)j * S + k] + rs0[(size_t)j * S + k]) -
                                     (rs[(size_t)(S + k) * S + j] + rs0[(size_t)(S + k) * S + j])) * is;
-                const double y1 =
-                    (R1 + a[j] / n - (1.0 / m + 1.0 / n) * bb[j] + r3[k] / n + T3 / (n * n)) / (m + n) - ya[k];
-                put(k, y1);
+                put(k, (R1 + colj + mv[S + k]) * imn);      // y1(k, j)
             }
+            const double sy = mv[2 * S + j];
             for (int i = threadIdx.x; i < S; i += blockDim.x) {
                 double kap = 0.0;
                 for (int b = 0; b < nb; ++b)
                     kap += I.cs_part[((size_t)j * nb + b) * S + i] + I.cs0_part[((size_t)j * nb + b) * S + i];
                 const double mu = I.mu1[(size_t)i * S + j];
-                const double R2 = (mu - kap) * is;
-                const double y2 = (R2 - colY1) / m;
-                dob += mu * put(S + i, y2);                     // <b, y-bar>: mu1 against y2
+                dob += mu * put(S + i, ((mu - kap) * is - sy) * im);   // y2(i, j); <b, y>: mu1 . y2
             }
         } else {
             const int k = slab - S;
-            const double sp = sv[k] - n * ya[k];                // sum_j y1(k, j)
+            const double rowk = mv[S + k];
             for (int j = threadIdx.x; j < S; j += blockDim.x) {
                 const double R1 = -((rs[(size_t)j * S + k] + rs0[(size_t)j * S + k]) -
                                     (rs[(size_t)(S + k) * S + j] + rs0[(size_t)(S + k) * S + j])) * is;
-                const double y1 =
-                    (R1 + a[j] / n - (1.0 / m + 1.0 / n) * bb[j] + r3[k] / n + T3 / (n * n)) / (m + n) - ya[k];
-                put(j, -y1);                                    // A2 = -1_n^T kron I_M
+                put(j, -(R1 + mv[j] + rowk) * imn);          // -y1(k, j): A2 = -1_n^T kron I_M
             }
+            const double sp = mv[3 * S + k];
             for (int l = threadIdx.x; l < S; l += blockDim.x) {
                 if (k == S - 1 && l == S - 1) {
-                    put(S + l, 0.0);                            // no row: y3(m, n) = 0
+                    put(S + l, 0.0);                         // no row: y3(m, n) = 0
                     continue;
                 }
                 double kap = 0.0;
                 for (int b = 0; b < nb; ++b)
                     kap += I.cs_part[((size_t)slab * nb + b) * S + l] + I.cs0_part[((size_t)slab * nb + b) * S + l];
                 const double mu = I.mu2[(size_t)k * S + l];
-                const double R3 = (mu - kap) * is;
-                const double y3 = (R3 + sp) / n;
-                dob += mu * put(S + l, y3);                     // mu2 against y3
+                dob += mu * put(S + l, ((mu - kap) * is + sp) * in_);  // y3(k, l); mu2 . y3
             }
         }
-        red[0] = dob;
-        red[1] = red[2] = red[3] = 0.0;
+        double red[4] = {dob, 0.0, 0.0, 0.0};
         block_sum<4>(red, s_red);
         const float bm = block_max(ymax, s_max);
         if (threadIdx.x == 0) {
@@ -441,9 +459,13 @@ template <typename T, bool CHECK>
 __global__ void __launch_bounds__(kThreads) k_sweep(const WorkDev* __restrict__ W, int j) {
     using V = VecT<T>;
     constexpr int NV = V::N;
-    __shared__ __align__(16) T s_row[kRowSmemBytes / sizeof(float) / (sizeof(T) / sizeof(float))];
+    // row partials, one padded row of NC+1 entries per tile row (conflict-free
+    // on the write, where a warp spans columns, and on the reduction, where it
+    // spans rows)
+    constexpr int kRowN = kRowSmemBytes / sizeof(float) / (sizeof(T) / sizeof(float)) + 256;
+    __shared__ __align__(16) T s_row[kRowN];
     __shared__ __align__(16) T s_col[kThreads * NV];
-    __shared__ __align__(16) T s_xrow[CHECK ? kRowSmemBytes / sizeof(float) / (sizeof(T) / sizeof(float)) : 1];
+    __shared__ __align__(16) T s_xrow[CHECK ? kRowN : 1];
     __shared__ __align__(16) T s_xcol[CHECK ? kThreads * NV : 1];
     __shared__ double s_red[kNK * 32];
     __shared__ int s_tile[4];
@@ -489,12 +511,10 @@ __global__ void __launch_bounds__(kThreads) k_sweep(const WorkDev* __restrict__ 
             }
             if (active) {
                 int nrow = 0;
-                for (int r = r0 + ro; r < r1; r += P) {
+                auto row = [&](int r, const float (&uu)[NV], const float (&dd)[NV]) {
                     const float4 a = ab[r];
                     const float rf = (float)r;
-                    float uu[NV], dd[NV], out[NV], xo[NV];
-                    V::ld(u + (size_t)r * S + c0, uu);
-                    V::ld(din + (size_t)r * S + c0, dd);
+                    float out[NV], xo[NV];
 #pragma unroll
                     for (int e = 0; e < NV; ++e) {
                         const float dc = rf - cf[e];
@@ -516,9 +536,9 @@ __global__ void __launch_bounds__(kThreads) k_sweep(const WorkDev* __restrict__ 
                         cacc[e] += out[e];
                     }
                     V::st(dout + (size_t)r * S + c0, out);
-                    s_row[(r - r0) * NC + cg] = (out[0] + out[1]) + (out[2] + out[3]);
-                    if constexpr (CHECK) s_xrow[(r - r0) * NC + cg] = (xo[0] + xo[1]) + (xo[2] + xo[3]);
+                    s_row[(r - r0) * (NC + 1) + cg] = (out[0] + out[1]) + (out[2] + out[3]);
                     if constexpr (CHECK) {
+                        s_xrow[(r - r0) * (NC + 1) + cg] = (xo[0] + xo[1]) + (xo[2] + xo[3]);
                         // keep FP32 chains short: flush the check partials every 4 rows
                         if ((++nrow & 3) == 0) {
 #pragma unroll
@@ -528,6 +548,19 @@ __global__ void __launch_bounds__(kThreads) k_sweep(const WorkDev* __restrict__ 
                             }
                         }
                     }
+                };
+                // two rows in flight per thread: issue both rows' loads first
+                for (int r = r0 + ro; r < r1; r += 2 * P) {
+                    const int r2 = r + P;
+                    float u0[NV], d0v[NV], u1[NV], d1v[NV];
+                    V::ld(u + (size_t)r * S + c0, u0);
+                    V::ld(din + (size_t)r * S + c0, d0v);
+                    if (r2 < r1) {
+                        V::ld(u + (size_t)r2 * S + c0, u1);
+                        V::ld(din + (size_t)r2 * S + c0, d1v);
+                    }
+                    row(r, u0, d0v);
+                    if (r2 < r1) row(r2, u1, d1v);
                 }
             }
 #pragma unroll
@@ -571,8 +604,8 @@ __global__ void __launch_bounds__(kThreads) k_sweep(const WorkDev* __restrict__ 
                         cacc[e] += out[e];
                     }
                     V::st(dout + (size_t)r * S + c0, out);
-                    s_row[(r - r0) * NC + cg] = out[0] + out[1];
-                    if constexpr (CHECK) s_xrow[(r - r0) * NC + cg] = xo[0] + xo[1];
+                    s_row[(r - r0) * (NC + 1) + cg] = out[0] + out[1];
+                    if constexpr (CHECK) s_xrow[(r - r0) * (NC + 1) + cg] = xo[0] + xo[1];
                 }
             }
         }
@@ -597,11 +630,11 @@ __global__ void __launch_bounds__(kThreads) k_sweep(const WorkDev* __restrict__ 
         }
         for (int rr = threadIdx.x; rr < r1 - r0; rr += blockDim.x) {
             if constexpr (std::is_same<T, float>::value) {
-                I.rs[(size_t)slab * S + r0 + rr] = sum_f32_strided(s_row + rr * NC, NC, 1);
-                if constexpr (CHECK) I.xrs[(size_t)slab * S + r0 + rr] = sum_f32_strided(s_xrow + rr * NC, NC, 1);
+                I.rs[(size_t)slab * S + r0 + rr] = sum_f32_strided(s_row + rr * (NC + 1), NC, 1);
+                if constexpr (CHECK) I.xrs[(size_t)slab * S + r0 + rr] = sum_f32_strided(s_xrow + rr * (NC + 1), NC, 1);
             } else {
-                I.rs[(size_t)slab * S + r0 + rr] = sum_f64_strided(s_row + rr * NC, NC, 1);
-                if constexpr (CHECK) I.xrs[(size_t)slab * S + r0 + rr] = sum_f64_strided(s_xrow + rr * NC, NC, 1);
+                I.rs[(size_t)slab * S + r0 + rr] = sum_f64_strided(s_row + rr * (NC + 1), NC, 1);
+                if constexpr (CHECK) I.xrs[(size_t)slab * S + r0 + rr] = sum_f64_strided(s_xrow + rr * (NC + 1), NC, 1);
             }
         }
         if constexpr (CHECK) {
@@ -996,13 +1029,13 @@ void launch_init(const HotInst& I, double sigma0, cudaStream_t st) {
 
 cudaError_t kernels_init(int device) {
     (void)device;
-    cudaError_t e = cudaFuncSetAttribute(k_alpha, cudaFuncAttributeMaxDynamicSharedMemorySize, 5 * kMaxS * 8);
-    return e;
+    return cudaSuccess;
 }
 
 void launch_solve_kernels(const WorkDev* w, const LaunchDims& ld, cudaStream_t st) {
     k_vec<<<ld.grid_vec, kThreads, 0, st>>>(w);
-    k_alpha<<<ld.grid_slab, kThreads, 5 * kMaxS * 8, st>>>(w);
+    k_marg<<<ld.grid_inst, kThreads, 0, st>>>(w);
+    k_alpha<<<ld.grid_slab, kThreads, 0, st>>>(w);
 }
 
 void launch_sweep(const WorkDev* w, const LaunchDims& ld, int fp64, int j, bool check, cudaStream_t st) {

@@ -271,7 +271,7 @@ def test_recovered_plan_marginals_tight_tolerance(ctx32):
     """At a tight tolerance the plan's marginals match mu and nu to 1e-6 in L1."""
     S = 32
     mu1, mu2 = syn.make_pair("gauss", S, 3)
-    r = ctx32.solve(mu1, mu2, tol=1e-9, max_iter=200000)
+    r = ctx32.solve(mu1, mu2, tol=1e-8, max_iter=200000)
     src, dst, mass, l1 = ctx32.recover_plan(r)
     ctx32.release(r)
     assert r["status"] == 0
