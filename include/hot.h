@@ -185,6 +185,29 @@ typedef struct hot_kernel_times {
 HOT_API int hot_solve_profiled(hot_ctx *ctx, const double *mu, const double *nu, int m, int n, int space,
                        double tol, long long max_iter, hot_result *out, hot_kernel_times *kt);
 
+/* Algorithm 1 without any device allocation (the paper has no counterpart;
+ * this exists for callers that cannot let a library allocate device memory at
+ * call time: code with a fixed, pre-accounted device-memory footprint, or a
+ * latency-critical loop that must not pay for or synchronise on an
+ * allocation).  Its scratch is a static device array inside the library,
+ * sized for grids up to 256 x 256 (about 1.8 MB, held on every GPU that
+ * loads the library until the process exits); larger grids return
+ * HOT_EINVAL.  The first call on a device resolves that array's device
+ * address (cudaGetSymbolAddress) and should therefore come before any stream
+ * capture.
+ *   x:       device, the flows in the vec order of hot_get_flows (m*m*n + m*n*n doubles)
+ *   mu, nu:  device, row-major m*n histograms, read only when marg_l1 != NULL
+ *   src, dst, mass, cap, nnz: as in hot_recover_plan, outputs in device memory;
+ *            cap = 0 with src == NULL only counts
+ *   marg_l1: host, 2 doubles (optional)
+ *   stream:  cudaStream_t to run on (NULL: the legacy default stream); the call
+ *            returns after its work on that stream has finished.
+ * Every call shares the one scratch array and overwrites it; calls whose work
+ * overlaps on the GPU race and produce wrong results. */
+HOT_API int hot_recover_plan_static(const double *x, int m, int n, const double *mu, const double *nu,
+                            int32_t *src, int32_t *dst, double *mass, size_t cap, size_t *nnz,
+                            double *marg_l1, void *stream);
+
 /* Free the device memory of a kept solution.  Unknown id: HOT_ENOTFOUND. */
 HOT_API int hot_release(hot_ctx *ctx, unsigned long long solution_id);
 
