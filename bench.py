@@ -281,7 +281,12 @@ def bench_solve(args, dist):
                 "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
                 "kernel": "k_sweep<float,false> (Steps 2-4 fused, non-check iterations)",
                 "bytes_per_launch": kt["sweep_bytes"], "avg_launch_us": round(sweep_s * 1e6, 2),
-                "share_of_solve_device_time": round(kt["sweep_ms"] / total_ms, 4) if total_ms > 0 else None}
+                "share_of_solve_device_time": round(kt["sweep_ms"] / total_ms, 4) if total_ms > 0 else None,
+                "device_us_per_iteration": {
+                    "sweep": round(1000 * kt["sweep_ms"] / max(1, kt["sweep_launches"]), 2),
+                    "sweep_check": round(1000 * kt["sweep_check_ms"] / max(1, kt["sweep_check_launches"]), 2),
+                    "prop3_solve": round(1000 * kt["solve_ms"] / max(1, kt["sweep_launches"] + kt["sweep_check_launches"]), 2),
+                    "block_end_per_block": round(1000 * kt["block_end_ms"] / max(1, kt["sweep_check_launches"]), 2)}}
 
     out = {"metric": "solves/s (ms-to-1e-6 KKT) at N=256", "value": round(value, 4), "unit": "solves/s",
            "n_gpus": dist.world, "steps": args.steps, "warmup": max(3, args.warmup),

@@ -125,11 +125,15 @@ int inst_create(const PairHost& p, int fp64, double sigma0_cfg, double tol, long
         return o;
     };
     const size_t o_ab32 = fp64 ? 0 : take(4 * SS * sizeof(float4));
+    const size_t o_ab0_32 = fp64 ? 0 : take(4 * SS * sizeof(float2));   // y0 = 0 at the start
     const size_t o_ab64 = take(4 * SS * 8);
     const size_t o_dab = take(4 * SS * 8);
     const size_t o_ab0 = take(4 * SS * 8);      // A^T y0 pieces: y0 = 0 at the start
     const size_t o_rs = take(2 * SS * 8);
     const size_t o_cs = take(2 * SS * I->nb * 8);
+    const size_t o_cs32 = take(2 * SS * I->nb * 4);
+    const size_t o_R1a = take(2 * SS * 8);
+    const size_t o_kapa = take(2 * SS * 8);
     const size_t o_rs0 = take(2 * SS * 8);
     const size_t o_cs0 = take(2 * SS * I->nb * 8);
     const size_t o_xrs = take(2 * SS * 8);
@@ -193,6 +197,10 @@ int inst_create(const PairHost& p, int fp64, double sigma0_cfg, double tol, long
     d.zr = big + 4 * VB;
     char* sm = I->small;
     d.ab32 = fp64 ? nullptr : (float4*)(sm + o_ab32);
+    d.ab0_32 = fp64 ? nullptr : (float2*)(sm + o_ab0_32);
+    d.cs32 = (float*)(sm + o_cs32);
+    d.R1a = (double*)(sm + o_R1a);
+    d.kapa = (double*)(sm + o_kapa);
     d.ab64 = (double*)(sm + o_ab64);
     d.dab64 = (double*)(sm + o_dab);
     d.ab0 = (double*)(sm + o_ab0);
@@ -476,7 +484,7 @@ int run_solve(Ctx* ctx, const std::vector<PairHost>& pairs, double tol, long lon
         } else {
             for (int j = 0; j < K; ++j) {
                 cudaEventRecord(pev[3 * j], st);
-                launch_solve_kernels(B.d_work, B.ld, st);
+                launch_solve_kernels(B.d_work, B.ld, j == K - 1, st);
                 cudaEventRecord(pev[3 * j + 1], st);
                 launch_sweep(B.d_work, B.ld, fp64, j, j == K - 1, st);
                 cudaEventRecord(pev[3 * j + 2], st);

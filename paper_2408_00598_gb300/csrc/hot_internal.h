@@ -84,11 +84,15 @@ struct HotInst {
     void* xr;              // x-bar at the last restart (final x-bar after the solve)
     void* zr;              // z-bar at the last restart
     float4* ab32;          // [2S][2][S] (hi, lo, delta, 0) of alpha then beta, FP32 mode
-    double* ab64;          // [2S][2][S] alpha then beta = A^T y-bar pieces (FP64)
+    float2* ab0_32;        // [2S][2][S] (hi, lo) split of ab0, FP32 mode (fixed within a cycle)
+    double* ab64;          // [2S][2][S] alpha then beta = A^T y-bar pieces (FP64 mode)
     double* ab0;           // [2S][2][S] the same pieces of A^T y0 at the anchor
-    double* dab64;         // [2S][2][S] ab64 - ab0 (FP64)
+    double* dab64;         // [2S][2][S] A^T (y-bar - y0) pieces
     double* rs;            // [2S][S] row sums of the delta written by the last sweep
-    double* cs_part;       // [2S][nb][S] column partial sums of the delta
+    double* cs_part;       // [2S][nb][S] column partial sums of the delta (FP64 mode)
+    float* cs32;           // [2S][nb][S] column partial sums of the delta (FP32 mode)
+    double* R1a;           // [2S][S] anchor part of R1 along each slab's rows: -(rowsum f1 - rowsum f2)(u)/sigma
+    double* kapa;          // [2S][S] column totals of u per slab
     double* rs0;           // [2S][S] row sums of u (FP64)
     double* cs0_part;      // [2S][nb][S] column partial sums of u
     double* xrs;           // [2S][S] row sums of x-bar (check iterations)
@@ -130,8 +134,8 @@ struct LaunchDims {
 };
 
 constexpr int kLaunchesPerIteration = 4;   // k_vec, k_marg, k_alpha, k_sweep
-constexpr int kLaunchesBlockEnd = 7;       // k_kkt1, k_check, 3 x k_restart, k_restart_sigma, k_block_end
-void launch_solve_kernels(const WorkDev* w, const LaunchDims& ld, cudaStream_t st);
+constexpr int kLaunchesBlockEnd = 8;       // k_kkt1, k_check, 3 x k_restart, k_restart_sigma, k_anchor, k_block_end
+void launch_solve_kernels(const WorkDev* w, const LaunchDims& ld, bool check, cudaStream_t st);
 void launch_sweep(const WorkDev* w, const LaunchDims& ld, int fp64, int j, bool check, cudaStream_t st);
 void launch_iteration(const WorkDev* w, const LaunchDims& ld, int fp64, int j, bool check, cudaStream_t st);
 void launch_block_end(const WorkDev* w, const LaunchDims& ld, int fp64, int K, double a1, double a2, double a3,

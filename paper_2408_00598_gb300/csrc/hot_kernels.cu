@@ -106,6 +106,26 @@ __device__ __forceinline__ double sum_f64_strided(const double* p, int count, in
     return acc;
 }
 
+// Double-float accumulator: an unevaluated pair (hi, lo) of FP32 values whose
+// sum carries about twice the FP32 precision; each add is an exact two-sum
+// followed by renormalisation (FP32 arithmetic only).  Used where a sum
+// must be accurate to FP64 level but FP64 per element would be too slow.
+struct DF {
+    float hi, lo;
+};
+__device__ __forceinline__ DF df_add(DF a, float b) {
+    const float s = a.hi + b;
+    const float bb = s - a.hi;
+    const float e = ((a.hi - (s - bb)) + (b - bb)) + a.lo;
+    const float h = s + e;
+    return DF{h, e - (h - s)};
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    DF r = df_add(a, b.hi);
+    return df_add(r, b.lo);
+}
+__device__ __forceinline__ double df_val(DF a) { return (double)a.hi + (double)a.lo; }
+
 // ------------------------------------------------------ per-tile parameters --
 
 struct P32 {
@@ -204,6 +224,24 @@ template <> struct VecT<double> {
     }
 };
 
+// Asynchronous global -> shared copies (16 B per thread, cached in L2 only).
+// A thread waits only for its own copies (cp.async.wait_group), so a pipeline
+// in which every thread reads back only what it copied needs no barrier.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Stages of the FP32 sweep pipeline: each holds one pass of P rows
+// (one float4 of u and one of the delta per thread).
+constexpr int kStages = 4;
+constexpr int kStageBytes = 2 * kThreads * 16;
+
 struct TileCtx {
     int inst, slab, band;
 };
@@ -279,6 +317,7 @@ __global__ void __launch_bounds__(kThreads) k_vec(const WorkDev* __restrict__ W)
 // k_alpha (one CTA per slab) then forms the slab's entries with products only
 // (FP64 division is slow on this part; reciprocals are taken once).
 __global__ void __launch_bounds__(kThreads) k_marg(const WorkDev* __restrict__ W) {
+    extern __shared__ double sv[];                   // 7 * S: T1 T2 P1 P2 colmu1 rowmu2, then s
     __shared__ double s_red[4 * 32];
     const int ninst = W->ninst;
     for (int inst = blockIdx.x; inst < ninst; inst += gridDim.x) {
@@ -288,75 +327,89 @@ __global__ void __launch_bounds__(kThreads) k_marg(const WorkDev* __restrict__ W
         const double m = S, n = S;
         const double is = 1.0 / I.ctl->sigma;
         const double in_ = 1.0 / n, im = 1.0 / m, imn = 1.0 / (m + n);
-        const double* T1 = I.vecs;
-        const double* T2 = I.vecs + S;
-        const double* P1 = I.vecs + 2 * S;
-        const double* P2 = I.vecs + 3 * S;
-        double* mv = I.mvec;
-        double kap_last = 0.0;                         // column S-1 of the last f2 slab (dropped row)
+        double* T1 = sv;
+        double* T2 = sv + S;
+        double* P1 = sv + 2 * S;
+        double* P2 = sv + 3 * S;
+        double* cm = sv + 4 * S;
+        double* rm = sv + 5 * S;
+        double* ss = sv + 6 * S;
+        for (int q = threadIdx.x; q < 4 * S; q += blockDim.x) sv[q] = I.vecs[q];
+        for (int q = threadIdx.x; q < S; q += blockDim.x) {
+            cm[q] = I.colmu1[q];
+            rm[q] = I.rowmu2[q];
+        }
+        // column S-1 of the last f2 slab: the dropped (m, n) row of eq. (7)
+        double kap_last = I.kapa[(size_t)(2 * S - 1) * S + (S - 1)];
         {
             const int sl = 2 * S - 1;
-            for (int b = 0; b < nb; ++b)
-                kap_last += I.cs_part[((size_t)sl * nb + b) * S + (S - 1)] + I.cs0_part[((size_t)sl * nb + b) * S + (S - 1)];
+            if (I.fp64)
+                for (int b = 0; b < nb; ++b) kap_last += I.cs_part[((size_t)sl * nb + b) * S + (S - 1)];
+            else
+                for (int b = 0; b < nb; ++b) kap_last += (double)I.cs32[((size_t)sl * nb + b) * S + (S - 1)];
         }
-        // pass 1: a, bb, r3 and their sums
+        const double mu_last = I.mu2[(size_t)(S - 1) * S + (S - 1)];
+        __syncthreads();
+        auto A_ = [&](int q) { return -(T1[q] - P2[q]) * is; };
+        auto B_ = [&](int q) { return (cm[q] - T1[q]) * is; };
+        auto R3_ = [&](int q) {
+            double r = (rm[q] - T2[q]) * is;
+            if (q == S - 1) r -= (mu_last - kap_last) * is;
+            return r;
+        };
         double red[4] = {0.0, 0.0, 0.0, 0.0};
         for (int q = threadIdx.x; q < S; q += blockDim.x) {
-            const double aq = -(T1[q] - P2[q]) * is;
-            const double bq = (I.colmu1[q] - T1[q]) * is;
-            double r3q = (I.rowmu2[q] - T2[q]) * is;
-            if (q == S - 1) r3q -= (I.mu2[(size_t)(S - 1) * S + (S - 1)] - kap_last) * is;
-            mv[q] = aq;                 // temporarily a
-            mv[2 * S + q] = bq;         // temporarily bb
-            mv[S + q] = r3q;            // temporarily r3
-            mv[3 * S + q] = -(P1[q] - T2[q]) * is;   // temporarily row sums of R1
-            red[0] += aq;
-            red[1] += bq;
-            red[2] += r3q;
+            red[0] += A_(q);
+            red[1] += B_(q);
+            red[2] += R3_(q);
         }
         block_sum<4>(red, s_red);
         const double Asum = red[0], Bsum = red[1], T3 = red[2];
         const double dl = (1.0 - in_) / (m + 1.0);
         const double iw = 1.0 / (im - dl);             // 1/w, w = 1/m - (1-1/n)/(m+1)
-        // pass 2: s_k and d^T s
         red[0] = red[1] = red[2] = red[3] = 0.0;
         for (int q = threadIdx.x; q < S; q += blockDim.x) {
-            const double s = (mv[3 * S + q] + Asum * in_ - (im + in_) * Bsum + mv[S + q] + T3 * in_) * imn;
-            mv[3 * S + q] = s;
+            const double rowR1 = -(P1[q] - T2[q]) * is;
+            const double s = (rowR1 + Asum * in_ - (im + in_) * Bsum + R3_(q) + T3 * in_) * imn;   // s_k
+            ss[q] = s;
             red[0] += (q == S - 1 ? dl : im) * s;
         }
         block_sum<4>(red, s_red);
         const double ds = red[0];
-        // pass 3: t = W-hat s and 1^T t
         red[0] = red[1] = red[2] = red[3] = 0.0;
         for (int q = threadIdx.x; q < S; q += blockDim.x) {
             const double dq = (q == S - 1 ? dl : im);
-            red[0] += -dq * mv[3 * S + q] - dq * ds * iw;
+            red[0] += -dq * ss[q] - dq * ds * iw;       // 1^T W-hat s
         }
         block_sum<4>(red, s_red);
         const double tsum = red[0];
-        // pass 4: y1^a and its sum
         red[0] = red[1] = red[2] = red[3] = 0.0;
         for (int q = threadIdx.x; q < S; q += blockDim.x) {
             const double dq = (q == S - 1 ? dl : im);
-            red[0] += -dq * mv[3 * S + q] - dq * ds * iw + tsum * in_;
+            red[0] += -dq * ss[q] - dq * ds * iw + tsum * in_;
         }
         block_sum<4>(red, s_red);
         const double yasum = red[0];
-        // pass 5: final vectors (each thread rewrites only its own q)
+        double* mv = I.mvec;
         for (int q = threadIdx.x; q < S; q += blockDim.x) {
             const double dq = (q == S - 1 ? dl : im);
-            const double ya = -dq * mv[3 * S + q] - dq * ds * iw + tsum * in_;
-            const double aq = mv[q], bq = mv[2 * S + q], r3q = mv[S + q], sq = mv[3 * S + q];
+            const double ya = -dq * ss[q] - dq * ds * iw + tsum * in_;   // y1^a
+            const double aq = A_(q), bq = B_(q);
             mv[q] = aq * in_ - (im + in_) * bq;
-            mv[S + q] = r3q * in_ + T3 * in_ * in_ - (m + n) * ya;
+            mv[S + q] = R3_(q) * in_ + T3 * in_ * in_ - (m + n) * ya;
             mv[2 * S + q] = (aq - bq + T3 * in_) * in_ - yasum;
-            mv[3 * S + q] = sq - n * ya;
+            mv[3 * S + q] = ss[q] - n * ya;
         }
         __syncthreads();
     }
 }
 
+// Per-slab entries of dy = A^T-pieces of y-bar - y0.  The anchor part of R
+// (row sums and column totals of u) is precomputed once per cycle by
+// k_anchor; here only the delta's sums enter.  FP32 mode splits each full
+// piece a0 + dy into a part on the grid 2^-E and a remainder using FP32
+// arithmetic on top of the per-cycle split of a0.
+template <bool CHECK>
 __global__ void __launch_bounds__(kThreads) k_alpha(const WorkDev* __restrict__ W) {
     __shared__ double s_red[4 * 32];
     __shared__ float s_max[32];
@@ -382,75 +435,123 @@ __global__ void __launch_bounds__(kThreads) k_alpha(const WorkDev* __restrict__ 
         const double is = 1.0 / I.ctl->sigma;
         const double im = 1.0 / m, in_ = 1.0 / n, imn = 1.0 / (m + n);
         const double* __restrict__ rs = I.rs;
-        const double* __restrict__ rs0 = I.rs0;
         const double* __restrict__ mv = I.mvec;
+        const double* __restrict__ R1a = I.R1a + (size_t)slab * S;
+        const double* __restrict__ kapa = I.kapa + (size_t)slab * S;
         const size_t o = (size_t)slab * 2 * S;
-        double* out_d = I.dab64 + o;
-        double* out_f = I.ab64 + o;
-        const double* in0 = I.ab0 + o;
-        float4* o32 = I.ab32 ? I.ab32 + o : nullptr;
-        const double h = I.h;
-        const double inv_h = 1.0 / h;
+        const bool fp32 = I.ab32 != nullptr;
+        const float grid = (float)(1.0 / I.h), igrid = (float)I.h;
         float ymax = 0.f;
         double dob = 0.0;
-        // idx < S: alpha (row) entries, idx >= S: beta (column) entries
-        auto put = [&](int idx, double dv) {
-            const double full = in0[idx] + dv;
-            out_d[idx] = dv;
-            out_f[idx] = full;
-            if (o32) {
-                const double hi = rint(full * inv_h) * h;       // on the grid 2^-E
-                o32[idx] = make_float4((float)hi, (float)(full - hi), (float)dv, 0.f);
+        // idx < S: alpha (row) entries, idx >= S: beta (column) entries; returns the full piece
+        auto put = [&](int idx, double dv) -> double {
+            I.dab64[o + idx] = dv;
+            double full;
+            if (fp32) {
+                const float df = (float)dv;
+                const float dh = rintf(df * grid) * igrid;      // on the grid 2^-E
+                const float2 a0 = I.ab0_32[o + idx];
+                I.ab32[o + idx] = make_float4(a0.x + dh, a0.y + (df - dh), df, 0.f);
+                full = CHECK ? I.ab0[o + idx] + dv : 0.0;
+            } else {
+                full = I.ab0[o + idx] + dv;
+                I.ab64[o + idx] = full;
             }
-            ymax = fmaxf(ymax, fabsf((float)full));
+            if (CHECK) ymax = fmaxf(ymax, fabsf((float)full));
             return full;
+        };
+        auto kap_delta = [&](int c) -> double {           // column total of the delta over the bands
+            if (fp32) {
+                float k = 0.f;
+                for (int b = 0; b < nb; ++b) k += I.cs32[((size_t)slab * nb + b) * S + c];
+                return (double)k;
+            }
+            double k = 0.0;
+            for (int b = 0; b < nb; ++b) k += I.cs_part[((size_t)slab * nb + b) * S + c];
+            return k;
         };
         if (slab < S) {
             const int j = slab;
             const double colj = mv[j];
             for (int k = threadIdx.x; k < S; k += blockDim.x) {
-                const double R1 = -((rs[(size_t)j * S + k] + rs0[(size_t)j * S + k]) -
-                                    (rs[(size_t)(S + k) * S + j] + rs0[(size_t)(S + k) * S + j])) * is;
-                put(k, (R1 + colj + mv[S + k]) * imn);      // y1(k, j)
+                const double R1 = R1a[k] - (rs[(size_t)j * S + k] - rs[(size_t)(S + k) * S + j]) * is;
+                put(k, (R1 + colj + mv[S + k]) * imn);         // y1(k, j)
             }
             const double sy = mv[2 * S + j];
             for (int i = threadIdx.x; i < S; i += blockDim.x) {
-                double kap = 0.0;
-                for (int b = 0; b < nb; ++b)
-                    kap += I.cs_part[((size_t)j * nb + b) * S + i] + I.cs0_part[((size_t)j * nb + b) * S + i];
+                const double kap = kapa[i] + kap_delta(i);
                 const double mu = I.mu1[(size_t)i * S + j];
-                dob += mu * put(S + i, ((mu - kap) * is - sy) * im);   // y2(i, j); <b, y>: mu1 . y2
+                const double full = put(S + i, ((mu - kap) * is - sy) * im);   // y2(i, j)
+                if (CHECK) dob += mu * full;                                    // <b, y>: mu1 . y2
             }
         } else {
             const int k = slab - S;
             const double rowk = mv[S + k];
             for (int j = threadIdx.x; j < S; j += blockDim.x) {
-                const double R1 = -((rs[(size_t)j * S + k] + rs0[(size_t)j * S + k]) -
-                                    (rs[(size_t)(S + k) * S + j] + rs0[(size_t)(S + k) * S + j])) * is;
-                put(j, -(R1 + mv[j] + rowk) * imn);          // -y1(k, j): A2 = -1_n^T kron I_M
+                const double R1 = R1a[j] - (rs[(size_t)j * S + k] - rs[(size_t)(S + k) * S + j]) * is;
+                put(j, -(R1 + mv[j] + rowk) * imn);            // -y1(k, j): A2 = -1_n^T kron I_M
             }
             const double sp = mv[3 * S + k];
             for (int l = threadIdx.x; l < S; l += blockDim.x) {
                 if (k == S - 1 && l == S - 1) {
-                    put(S + l, 0.0);                         // no row: y3(m, n) = 0
+                    put(S + l, 0.0);                           // no row: y3(m, n) = 0
                     continue;
                 }
-                double kap = 0.0;
-                for (int b = 0; b < nb; ++b)
-                    kap += I.cs_part[((size_t)slab * nb + b) * S + l] + I.cs0_part[((size_t)slab * nb + b) * S + l];
+                const double kap = kapa[l] + kap_delta(l);
                 const double mu = I.mu2[(size_t)k * S + l];
-                dob += mu * put(S + l, ((mu - kap) * is + sp) * in_);  // y3(k, l); mu2 . y3
+                const double full = put(S + l, ((mu - kap) * is + sp) * in_);  // y3(k, l)
+                if (CHECK) dob += mu * full;                                    // mu2 . y3
             }
         }
-        double red[4] = {dob, 0.0, 0.0, 0.0};
-        block_sum<4>(red, s_red);
-        const float bm = block_max(ymax, s_max);
-        if (threadIdx.x == 0) {
-            I.dobj_part[slab] = red[0];
-            atomicMax(&I.ctl->ymax_bits, __float_as_uint(bm));
+        if (CHECK) {
+            double red[4] = {dob, 0.0, 0.0, 0.0};
+            block_sum<4>(red, s_red);
+            const float bm = block_max(ymax, s_max);
+            if (threadIdx.x == 0) {
+                I.dobj_part[slab] = red[0];
+                atomicMax(&I.ctl->ymax_bits, __float_as_uint(bm));
+            }
         }
         __syncthreads();
     }
+}
+
+// Once per cycle (after a restart, and at the start): the anchor parts of the
+// right-hand side, per slab: R1a along the slab's rows and the column totals
+// of u.  One CTA per slab.
+__device__ __forceinline__ void anchor_slab(const HotInst& I, int slab, double sigma) {
+    const int S = I.S, nb = I.nb;
+    const double is = 1.0 / sigma;
+    for (int q = threadIdx.x; q < S; q += blockDim.x) {
+        // f1 slab j: rows k, R1(k, j); f2 slab k: rows j, R1(k, j)
+        const int j = slab < S ? slab : q;
+        const int k = slab < S ? q : slab - S;
+        I.R1a[(size_t)slab * S + q] = -(I.rs0[(size_t)j * S + k] - I.rs0[(size_t)(S + k) * S + j]) * is;
+        double kap = 0.0;
+        for (int b = 0; b < nb; ++b) kap += I.cs0_part[((size_t)slab * nb + b) * S + q];
+        I.kapa[(size_t)slab * S + q] = kap;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_anchor(const WorkDev* __restrict__ W) {
+    __shared__ int s_t[4];
+    const int ninst = W->ninst;
+    const int nslab = W->pre_slab[ninst];
+    for (int t = blockIdx.x; t < nslab; t += gridDim.x) {
+        if (threadIdx.x == 0) {
+            const int i = find_inst(W->pre_slab, ninst, t);
+            s_t[0] = i;
+            s_t[1] = t - W->pre_slab[i];
+            s_t[2] = (W->inst[i].ctl->status == ST_RUNNING) && W->inst[i].ctl->restart_pending;
+        }
+        __syncthreads();
+        if (s_t[2]) anchor_slab(W->inst[s_t[0]], s_t[1], W->inst[s_t[0]].ctl->sigma);
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_anchor_one(HotInst I, double sigma) {
+    for (int slab = blockIdx.x; slab < 2 * I.S; slab += gridDim.x) anchor_slab(I, slab, sigma);
 }
 
 // --------------------------------------------------------------- k_sweep --
@@ -469,6 +570,8 @@ __global__ void __launch_bounds__(kThreads) k_sweep(const WorkDev* __restrict__ 
     __shared__ __align__(16) T s_xcol[CHECK ? kThreads * NV : 1];
     __shared__ double s_red[kNK * 32];
     __shared__ int s_tile[4];
+    __shared__ P32 s_p32;
+    __shared__ P64 s_p64;
     const int ninst = W->ninst;
     const int ntiles = W->pre_tile[ninst];
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -490,8 +593,13 @@ __global__ void __launch_bounds__(kThreads) k_sweep(const WorkDev* __restrict__ 
         const T* __restrict__ u = (const T*)I.u + off;
         const T* __restrict__ din = (const T*)((j & 1) ? I.d1 : I.d0) + off;
         T* __restrict__ dout = (T*)((j & 1) ? I.d0 : I.d1) + off;
-        const int kc = I.ctl->k + j;
-        const double sigma = I.ctl->sigma;
+        // per-tile constants (FP64 divisions are slow here: one thread forms them)
+        if (threadIdx.x == 0) {
+            const int kc = I.ctl->k + j;
+            if constexpr (std::is_same<T, float>::value) s_p32 = make_p32(I.ctl->sigma, kc, I.h);
+            else s_p64 = make_p64(I.ctl->sigma, kc, I.h);
+        }
+        __syncthreads();
         const int c0 = cg * NV;
         T cacc[NV], xacc[NV];
 #pragma unroll
@@ -500,7 +608,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep(const WorkDev* __restrict__ 
         double k64[kNK] = {0.0, 0.0, 0.0, 0.0, 0.0};
 
         if constexpr (std::is_same<T, float>::value) {
-            const P32 p = make_p32(sigma, kc, I.h);
+            const P32 p = s_p32;
             const float4* ab = I.ab32 + (size_t)slab * 2 * S;
             float4 bq[NV];
             float cf[NV];
@@ -539,8 +647,8 @@ __global__ void __launch_bounds__(kThreads) k_sweep(const WorkDev* __restrict__ 
                     s_row[(r - r0) * (NC + 1) + cg] = (out[0] + out[1]) + (out[2] + out[3]);
                     if constexpr (CHECK) {
                         s_xrow[(r - r0) * (NC + 1) + cg] = (xo[0] + xo[1]) + (xo[2] + xo[3]);
-                        // keep FP32 chains short: flush the check partials every 4 rows
-                        if ((++nrow & 3) == 0) {
+                        // FP32 chains of 64 terms, combined in FP64
+                        if ((++nrow & 15) == 0) {
 #pragma unroll
                             for (int q = 0; q < kNK; ++q) {
                                 k64[q] += (double)k32[q];
@@ -549,24 +657,39 @@ __global__ void __launch_bounds__(kThreads) k_sweep(const WorkDev* __restrict__ 
                         }
                     }
                 };
-                // two rows in flight per thread: issue both rows' loads first
-                for (int r = r0 + ro; r < r1; r += 2 * P) {
-                    const int r2 = r + P;
-                    float u0[NV], d0v[NV], u1[NV], d1v[NV];
-                    V::ld(u + (size_t)r * S + c0, u0);
-                    V::ld(din + (size_t)r * S + c0, d0v);
-                    if (r2 < r1) {
-                        V::ld(u + (size_t)r2 * S + c0, u1);
-                        V::ld(din + (size_t)r2 * S + c0, d1v);
+                // kStages-deep cp.async pipeline over the passes of this tile:
+                // pass q covers row r0 + ro + q P of every active thread
+                extern __shared__ float4 s_stage[];          // [kStages][2][kThreads]
+                const int npass = (r1 - r0 + P - 1) / P;
+                auto issue = [&](int q) {
+                    const int r = r0 + ro + q * P;
+                    if (r < r1) {
+                        float4* su = s_stage + (size_t)(q % kStages) * 2 * kThreads + threadIdx.x;
+                        cp_async16(su, u + (size_t)r * S + c0);
+                        cp_async16(su + kThreads, din + (size_t)r * S + c0);
                     }
-                    row(r, u0, d0v);
-                    if (r2 < r1) row(r2, u1, d1v);
+                    cp_async_commit();                       // empty groups keep the count aligned
+                };
+#pragma unroll
+                for (int q = 0; q < kStages - 1; ++q) issue(q);
+                for (int q = 0; q < npass; ++q) {
+                    issue(q + kStages - 1);
+                    cp_async_wait<kStages - 1>();            // this thread's pass-q copies are in
+                    const int r = r0 + ro + q * P;
+                    if (r < r1) {
+                        const float4* su = s_stage + (size_t)(q % kStages) * 2 * kThreads + threadIdx.x;
+                        const float4 U = su[0], D = su[kThreads];
+                        const float uu[NV] = {U.x, U.y, U.z, U.w};
+                        const float dd[NV] = {D.x, D.y, D.z, D.w};
+                        row(r, uu, dd);
+                    }
                 }
+                cp_async_wait<0>();
             }
 #pragma unroll
             for (int q = 0; q < kNK; ++q) k64[q] += (double)k32[q];
         } else {
-            const P64 p = make_p64(sigma, kc, I.h);
+            const P64 p = s_p64;
             const double* ab = I.ab64 + (size_t)slab * 2 * S;
             const double* dab = I.dab64 + (size_t)slab * 2 * S;
             double bb[NV], db[NV], cf[NV];
@@ -621,7 +744,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep(const WorkDev* __restrict__ 
         const size_t cbase = ((size_t)slab * nb + band) * S;
         for (int c = threadIdx.x; c < S; c += blockDim.x) {
             if constexpr (std::is_same<T, float>::value) {
-                I.cs_part[cbase + c] = sum_f32_strided(s_col + c, P, S);
+                I.cs32[cbase + c] = (float)sum_f32_strided(s_col + c, P, S);
                 if constexpr (CHECK) I.xcs_part[cbase + c] = sum_f32_strided(s_xcol + c, P, S);
             } else {
                 I.cs_part[cbase + c] = sum_f64_strided(s_col + c, P, S);
@@ -663,6 +786,7 @@ __device__ __forceinline__ void restart_tile(const HotInst& I, int slab, int ban
                                              double* s_red) {
     using V = VecT<T>;
     constexpr int NV = V::N;
+    constexpr bool F32 = std::is_same<T, float>::value;
     const int S = I.S, nb = I.nb, TR = I.TR;
     const int NC = S / NV;
     const int P = kThreads / NC;
@@ -680,16 +804,22 @@ __device__ __forceinline__ void restart_tile(const HotInst& I, int slab, int ban
     const double sig_old = (MODE == 1) ? I.ctl->sigma_old : I.ctl->sigma;
     const double sig_new = I.ctl->sigma;
     const int c0 = cg * NV;
+    // sums that feed later iterations: FP64 (FP64 mode) or double-float (FP32 mode)
     double racc[2] = {0.0, 0.0};
+    DF fr[2] = {DF{0.f, 0.f}, DF{0.f, 0.f}};
     double ccol[NV];
+    DF fcol[NV];
 #pragma unroll
-    for (int e = 0; e < NV; ++e) ccol[e] = 0.0;
+    for (int e = 0; e < NV; ++e) {
+        ccol[e] = 0.0;
+        fcol[e] = DF{0.f, 0.f};
+    }
     if (active) {
         for (int r = r0 + ro; r < r1; r += P) {
             T uu[NV], dd[NV], xbv[NV], zbv[NV], rv[NV];
             V::ld(u + (size_t)r * S + c0, uu);
             V::ld(d1 + (size_t)r * S + c0, dd);
-            if constexpr (std::is_same<T, float>::value) {
+            if constexpr (F32) {
                 const P32 p = make_p32(sig_old, 0, I.h);
                 const float4* ab = I.ab32 + (size_t)slab * 2 * S;
                 const float4 a = ab[r];
@@ -719,31 +849,53 @@ __device__ __forceinline__ void restart_tile(const HotInst& I, int slab, int ban
                 V::ld(zr + (size_t)r * S + c0, zo);
 #pragma unroll
                 for (int e = 0; e < NV; ++e) {
-                    const double dx = (double)xbv[e] - (double)xo[e];
-                    const double dz = (double)zbv[e] - (double)zo[e];
-                    racc[0] += dx * dx;
-                    racc[1] += dz * dz;
+                    if constexpr (F32) {
+                        // (a - b)^2 exactly as a pair: the difference is exact to
+                        // rounding, its square split by fma
+                        const float dx = xbv[e] - xo[e], dz = zbv[e] - zo[e];
+                        const float px = dx * dx, pz = dz * dz;
+                        fr[0] = df_add(fr[0], DF{px, fmaf(dx, dx, -px)});
+                        fr[1] = df_add(fr[1], DF{pz, fmaf(dz, dz, -pz)});
+                    } else {
+                        const double dx = xbv[e] - xo[e], dz = zbv[e] - zo[e];
+                        racc[0] += dx * dx;
+                        racc[1] += dz * dz;
+                    }
                 }
             } else if constexpr (MODE == 1) {
+                // the slab sums of u enter every later right-hand side of Prop. 3,
+                // where they cancel against b: FP64-level accuracy is needed
                 T nu_[NV], zero[NV];
-                double rsum = 0.0;
+                DF rsf{0.f, 0.f};
+                double rsd = 0.0;
 #pragma unroll
                 for (int e = 0; e < NV; ++e) {
-                    if constexpr (std::is_same<T, float>::value) nu_[e] = fmaf((float)sig_new, rv[e], xbv[e]);
+                    if constexpr (F32) nu_[e] = fmaf((float)sig_new, rv[e], xbv[e]);
                     else nu_[e] = xbv[e] + sig_new * rv[e];
                     zero[e] = T(0);
-                    rsum += (double)nu_[e];
-                    ccol[e] += (double)nu_[e];
+                    if constexpr (F32) {
+                        rsf = df_add(rsf, (float)nu_[e]);
+                        fcol[e] = df_add(fcol[e], (float)nu_[e]);
+                    } else {
+                        rsd += nu_[e];
+                        ccol[e] += nu_[e];
+                    }
                 }
                 V::st(u + (size_t)r * S + c0, nu_);
                 V::st(xr + (size_t)r * S + c0, xbv);
                 V::st(zr + (size_t)r * S + c0, zbv);
                 V::st(d0 + (size_t)r * S + c0, zero);
-                s_row[(r - r0) * NC + cg] = rsum;
+                s_row[(r - r0) * NC + cg] = F32 ? df_val(rsf) : rsd;
             } else {
                 V::st(xr + (size_t)r * S + c0, xbv);
             }
         }
+    }
+    if constexpr (F32) {
+        racc[0] = df_val(fr[0]);
+        racc[1] = df_val(fr[1]);
+#pragma unroll
+        for (int e = 0; e < NV; ++e) ccol[e] = df_val(fcol[e]);
     }
     if constexpr (MODE == 0) {
         block_sum<2>(racc, s_red);
@@ -762,15 +914,25 @@ __device__ __forceinline__ void restart_tile(const HotInst& I, int slab, int ban
         for (int c = threadIdx.x; c < S; c += blockDim.x) {
             I.cs0_part[cbase + c] = sum_f64_strided(s_col + c, P, S);
             I.cs_part[cbase + c] = 0.0;
+            I.cs32[cbase + c] = 0.f;
         }
+        // y0 <- y-bar: A^T y0 pieces of this tile's rows (and, for band 0, columns)
+        const size_t o = (size_t)slab * 2 * S;
+        auto set_anchor = [&](int idx) {
+            const double a0 = I.ab0[o + idx] + I.dab64[o + idx];
+            I.ab0[o + idx] = a0;
+            if (I.ab0_32) {
+                const double hi = rint(a0 / I.h) * I.h;          // on the grid 2^-E
+                I.ab0_32[o + idx] = make_float2((float)hi, (float)(a0 - hi));
+            }
+        };
         for (int rr = threadIdx.x; rr < r1 - r0; rr += blockDim.x) {
             I.rs0[(size_t)slab * S + r0 + rr] = sum_f64_strided(s_row + rr * NC, NC, 1);
             I.rs[(size_t)slab * S + r0 + rr] = 0.0;
-            I.ab0[(size_t)slab * 2 * S + r0 + rr] = I.ab64[(size_t)slab * 2 * S + r0 + rr];   // alpha rows
+            set_anchor(r0 + rr);
         }
         if (band == 0)
-            for (int c = threadIdx.x; c < S; c += blockDim.x)
-                I.ab0[(size_t)slab * 2 * S + S + c] = I.ab64[(size_t)slab * 2 * S + S + c];    // beta
+            for (int c = threadIdx.x; c < S; c += blockDim.x) set_anchor(S + c);
     }
 }
 
@@ -814,27 +976,41 @@ __global__ void __launch_bounds__(kThreads) k_init(HotInst I, double sigma0) {
         const int r0 = band * TR, r1 = min(S, r0 + TR);
         const size_t off = (size_t)slab * S * S;
         double ccol[NV];
+        DF fcol[NV];
 #pragma unroll
-        for (int e = 0; e < NV; ++e) ccol[e] = 0.0;
+        for (int e = 0; e < NV; ++e) {
+            ccol[e] = 0.0;
+            fcol[e] = DF{0.f, 0.f};
+        }
         if (active) {
             for (int r = r0 + ro; r < r1; r += P) {
                 T uu[NV], zero[NV];
-                double rsum = 0.0;
+                DF rsf{0.f, 0.f};
+                double rs = 0.0;
 #pragma unroll
                 for (int e = 0; e < NV; ++e) {
                     const double dc = (double)(r - (c0 + e));
                     uu[e] = (T)(-sigma0 * (dc * dc * I.h));
                     zero[e] = T(0);
-                    rsum += (double)uu[e];
-                    ccol[e] += (double)uu[e];
+                    if constexpr (std::is_same<T, float>::value) {
+                        rsf = df_add(rsf, (float)uu[e]);
+                        fcol[e] = df_add(fcol[e], (float)uu[e]);
+                    } else {
+                        rs += (double)uu[e];
+                        ccol[e] += (double)uu[e];
+                    }
                 }
+                if constexpr (std::is_same<T, float>::value) rs = df_val(rsf);
                 V::st((T*)I.u + off + (size_t)r * S + c0, uu);
                 V::st((T*)I.d0 + off + (size_t)r * S + c0, zero);
                 V::st((T*)I.xr + off + (size_t)r * S + c0, zero);
                 V::st((T*)I.zr + off + (size_t)r * S + c0, zero);
-                s_row[(r - r0) * NC + cg] = rsum;
+                s_row[(r - r0) * NC + cg] = rs;
             }
         }
+        if constexpr (std::is_same<T, float>::value)
+#pragma unroll
+            for (int e = 0; e < NV; ++e) ccol[e] = df_val(fcol[e]);
         __syncthreads();
         if (active)
 #pragma unroll
@@ -1019,23 +1195,32 @@ LaunchDims make_launch_dims(int device) {
 }
 
 void launch_init(const HotInst& I, double sigma0, cudaStream_t st) {
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int tiles = 2 * I.S * I.nb;
     const int grid = tiles < sms * 4 ? tiles : sms * 4;
     if (I.fp64) k_init<double><<<grid, kThreads, 0, st>>>(I, sigma0);
     else k_init<float><<<grid, kThreads, 0, st>>>(I, sigma0);
+    k_anchor_one<<<2 * I.S < sms * 4 ? 2 * I.S : sms * 4, kThreads, 0, st>>>(I, sigma0);
 }
 
 cudaError_t kernels_init(int device) {
     (void)device;
-    return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_sweep<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kStages * kStageBytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_sweep<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kStages * kStageBytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_marg, cudaFuncAttributeMaxDynamicSharedMemorySize, 7 * kMaxS * 8);
+    return e;
 }
 
-void launch_solve_kernels(const WorkDev* w, const LaunchDims& ld, cudaStream_t st) {
+void launch_solve_kernels(const WorkDev* w, const LaunchDims& ld, bool check, cudaStream_t st) {
     k_vec<<<ld.grid_vec, kThreads, 0, st>>>(w);
-    k_marg<<<ld.grid_inst, kThreads, 0, st>>>(w);
-    k_alpha<<<ld.grid_slab, kThreads, 0, st>>>(w);
+    k_marg<<<ld.grid_inst, kThreads, 7 * kMaxS * 8, st>>>(w);
+    if (check) k_alpha<true><<<ld.grid_slab, kThreads, 0, st>>>(w);
+    else k_alpha<false><<<ld.grid_slab, kThreads, 0, st>>>(w);
 }
 
 void launch_sweep(const WorkDev* w, const LaunchDims& ld, int fp64, int j, bool check, cudaStream_t st) {
@@ -1043,13 +1228,13 @@ void launch_sweep(const WorkDev* w, const LaunchDims& ld, int fp64, int j, bool 
         if (check) k_sweep<double, true><<<ld.grid_tile, kThreads, 0, st>>>(w, j);
         else k_sweep<double, false><<<ld.grid_tile, kThreads, 0, st>>>(w, j);
     } else {
-        if (check) k_sweep<float, true><<<ld.grid_tile, kThreads, 0, st>>>(w, j);
-        else k_sweep<float, false><<<ld.grid_tile, kThreads, 0, st>>>(w, j);
+        if (check) k_sweep<float, true><<<ld.grid_tile, kThreads, kStages * kStageBytes, st>>>(w, j);
+        else k_sweep<float, false><<<ld.grid_tile, kThreads, kStages * kStageBytes, st>>>(w, j);
     }
 }
 
 void launch_iteration(const WorkDev* w, const LaunchDims& ld, int fp64, int j, bool check, cudaStream_t st) {
-    launch_solve_kernels(w, ld, st);
+    launch_solve_kernels(w, ld, check, st);
     launch_sweep(w, ld, fp64, j, check, st);
 }
 
@@ -1061,11 +1246,13 @@ void launch_block_end(const WorkDev* w, const LaunchDims& ld, int fp64, int K, d
         k_restart<double, 0><<<ld.grid_tile, kThreads, 0, st>>>(w);
         k_restart_sigma<<<ld.grid_inst, kThreads, 0, st>>>(w);
         k_restart<double, 1><<<ld.grid_tile, kThreads, 0, st>>>(w);
+        k_anchor<<<ld.grid_slab, kThreads, 0, st>>>(w);
         k_restart<double, 2><<<ld.grid_tile, kThreads, 0, st>>>(w);
     } else {
         k_restart<float, 0><<<ld.grid_tile, kThreads, 0, st>>>(w);
         k_restart_sigma<<<ld.grid_inst, kThreads, 0, st>>>(w);
         k_restart<float, 1><<<ld.grid_tile, kThreads, 0, st>>>(w);
+        k_anchor<<<ld.grid_slab, kThreads, 0, st>>>(w);
         k_restart<float, 2><<<ld.grid_tile, kThreads, 0, st>>>(w);
     }
     k_block_end<<<ld.grid_inst, kThreads, 0, st>>>(w);
