@@ -20,23 +20,31 @@ const char* get_error() { return g_err.c_str(); }
 
 // ------------------------------------------------------------- validation --
 
-int tile_rows(int S, int fp64) {
+int tile_rows(int S, int fp64, int grid) {
     if (fp64) {
         // row-partial buffer: TR * S <= 4096
         int tr = std::min(S, 4096 / S);
         if (S >= 96) tr = std::min(tr, 32);
         return std::max(tr, 1);
     }
-    // TR * S <= 16384; large grids get several bands per slab for balance
-    switch (S) {
-        case 96: return 48;
-        case 128: return 32;
-        case 256: return 64;
-        case 512: return 32;
-        case 1024: return 16;
-        default: break;
+    // TR * S <= 16384 (row-partial buffer).  Among TR = S, S/2, S/4, ... with
+    // at least 4 passes per tile where possible, take the one whose tile count
+    // 2S * ceil(S/TR) spreads best over the grid's resident CTAs (the last
+    // round of a persistent grid-stride loop is the tail), larger TR on ties.
+    int best = std::min(S, 16384 / S);
+    if (grid <= 0) return best;
+    double best_imb = 1e30;
+    for (int tr = std::min(S, 16384 / S); tr >= 1; tr /= 2) {
+        if ((long long)tr * S < 4096 && tr != std::min(S, 16384 / S)) break;
+        const long long T = 2LL * S * ((S + tr - 1) / tr);
+        const long long rounds = (T + grid - 1) / grid;
+        const double imb = (double)(rounds * grid) / (double)T;
+        if (imb < best_imb * 0.99) {
+            best_imb = imb;
+            best = tr;
+        }
     }
-    return std::min(S, 16384 / S);
+    return best;
 }
 
 int validate_pair(const double* mu, const double* nu, int m, int n, int space, int fp64, PairHost& out) {
@@ -103,7 +111,7 @@ int inst_create(const PairHost& p, int fp64, double sigma0_cfg, double tol, long
     const int S = p.S;
     I->S = S;
     I->fp64 = fp64;
-    I->TR = tr_override > 0 ? tr_override : tile_rows(S, fp64);
+    I->TR = tr_override > 0 ? tr_override : tile_rows(S, fp64, sweep_grid(fp64));
     const int NV = fp64 ? 2 : 4;
     const int P = kThreads / (S / NV);
     if (I->TR > S || (size_t)I->TR * S > (size_t)(fp64 ? 4096 : 16384) || P < 1) {
@@ -142,7 +150,19 @@ int inst_create(const PairHost& p, int fp64, double sigma0_cfg, double tol, long
     const size_t o_rp = take((size_t)2 * S * I->nb * 2 * 8);
     const size_t o_vec = take(4 * (size_t)S * 8);
     const size_t o_mvec = take(4 * (size_t)S * 8);
+    const size_t F2 = fp64 ? 0 : sizeof(float2);   // double-float arrays of FP32 mode
+    const size_t o_rs2 = take(2 * SS * F2);
+    const size_t o_rs02 = take(2 * SS * F2);
+    const size_t o_R1a2 = take(2 * SS * F2);
+    const size_t o_K2 = take(2 * SS * F2);
+    const size_t o_vec2 = take(4 * (size_t)S * F2);
+    const size_t o_dab2 = take(4 * SS * F2);
     const size_t o_zero_end = off;                 // everything above starts at 0
+    const size_t o_mu1f = take(SS * F2);
+    const size_t o_mu2f = take(SS * F2);
+    const size_t o_cm2 = take(S * F2);
+    const size_t o_rm2 = take(S * F2);
+    const size_t o_p32 = take(sizeof(P32));
     const size_t o_mu1 = take(SS * 8);
     const size_t o_mu2 = take(SS * 8);
     const size_t o_cm = take(S * 8);
@@ -220,6 +240,17 @@ int inst_create(const PairHost& p, int fp64, double sigma0_cfg, double tol, long
     d.rowmu2 = (double*)(sm + o_rm);
     d.k1_part = (double*)(sm + o_k1);
     d.dobj_part = (double*)(sm + o_dp);
+    d.rs2 = fp64 ? nullptr : (float2*)(sm + o_rs2);
+    d.rs02 = fp64 ? nullptr : (float2*)(sm + o_rs02);
+    d.R1a2 = fp64 ? nullptr : (float2*)(sm + o_R1a2);
+    d.K2 = fp64 ? nullptr : (float2*)(sm + o_K2);
+    d.vec2 = fp64 ? nullptr : (float2*)(sm + o_vec2);
+    d.dab2 = fp64 ? nullptr : (float2*)(sm + o_dab2);
+    d.mu1f = fp64 ? nullptr : (float2*)(sm + o_mu1f);
+    d.mu2f = fp64 ? nullptr : (float2*)(sm + o_mu2f);
+    d.cm2 = fp64 ? nullptr : (float2*)(sm + o_cm2);
+    d.rm2 = fp64 ? nullptr : (float2*)(sm + o_rm2);
+    d.p32 = (P32*)(sm + o_p32);
     d.ctl = (HotCtl*)(sm + o_ctl);
 
     // host-side constants uploaded once
@@ -244,6 +275,24 @@ int inst_create(const PairHost& p, int fp64, double sigma0_cfg, double tol, long
     if (ee == cudaSuccess) ee = cudaMemcpyAsync(d.colmu1, cm.data(), S * 8, cudaMemcpyHostToDevice, st);
     if (ee == cudaSuccess) ee = cudaMemcpyAsync(d.rowmu2, rm.data(), S * 8, cudaMemcpyHostToDevice, st);
     if (ee == cudaSuccess) ee = cudaMemcpyAsync(d.ctl, &I->ctl_host, sizeof(HotCtl), cudaMemcpyHostToDevice, st);
+    if (!fp64) {
+        // (hi, lo) pairs of the marginals: hi = fl32(x), lo = fl32(x - hi)
+        auto pairs = [](const double* x, size_t n) {
+            std::vector<float2> v(n);
+            for (size_t q = 0; q < n; ++q) {
+                const float h = (float)x[q];
+                v[q] = make_float2(h, (float)(x[q] - (double)h));
+            }
+            return v;
+        };
+        const std::vector<float2> f1 = pairs(p.mu1.data(), SS), f2 = pairs(p.mu2.data(), SS);
+        const std::vector<float2> fc = pairs(cm.data(), S), fr = pairs(rm.data(), S);
+        if (ee == cudaSuccess) ee = cudaMemcpyAsync(d.mu1f, f1.data(), SS * F2, cudaMemcpyHostToDevice, st);
+        if (ee == cudaSuccess) ee = cudaMemcpyAsync(d.mu2f, f2.data(), SS * F2, cudaMemcpyHostToDevice, st);
+        if (ee == cudaSuccess) ee = cudaMemcpyAsync(d.cm2, fc.data(), S * F2, cudaMemcpyHostToDevice, st);
+        if (ee == cudaSuccess) ee = cudaMemcpyAsync(d.rm2, fr.data(), S * F2, cudaMemcpyHostToDevice, st);
+        // pageable sources: the copies are staged before cudaMemcpyAsync returns
+    }
     if (ee == cudaSuccess) {
         launch_init(d, c.sigma, st);   // u = -sigma0 c (w0 = 0), delta and restart references 0
         ee = cudaGetLastError();
@@ -334,7 +383,7 @@ int Batch::set_instances(const std::vector<Inst*>& v, cudaStream_t st) {
         const int S = v[i]->S;
         pt[i + 1] = pt[i] + 2 * S * v[i]->nb;
         ps[i + 1] = ps[i] + 2 * S;
-        pv[i + 1] = pv[i] + 4 * S;
+        pv[i + 1] = pv[i] + (v[i]->fp64 ? 4 * S : vec32_items(S));
         pk[i + 1] = pk[i] + v[i]->n_k1;
         if (v[i]->ctl_host.status == ST_RUNNING) ++running;
     }
@@ -360,7 +409,7 @@ int Batch::set_instances(const std::vector<Inst*>& v, cudaStream_t st) {
 int Batch::ensure_graph() {
     if (graph) return HOT_OK;
     if (!cap_stream) HOT_CK(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
-    ld = make_launch_dims(device);
+    ld = make_launch_dims(device, fp64);
     HOT_CK(cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal));
     for (int j = 0; j < K; ++j) launch_iteration(d_work, ld, fp64, j, j == K - 1, cap_stream);
     launch_block_end(d_work, ld, fp64, K, a1, a2, a3, cap_stream);
@@ -484,7 +533,7 @@ int run_solve(Ctx* ctx, const std::vector<PairHost>& pairs, double tol, long lon
         } else {
             for (int j = 0; j < K; ++j) {
                 cudaEventRecord(pev[3 * j], st);
-                launch_solve_kernels(B.d_work, B.ld, j == K - 1, st);
+                launch_solve_kernels(B.d_work, B.ld, fp64, j, j == K - 1, st);
                 cudaEventRecord(pev[3 * j + 1], st);
                 launch_sweep(B.d_work, B.ld, fp64, j, j == K - 1, st);
                 cudaEventRecord(pev[3 * j + 2], st);
@@ -501,7 +550,7 @@ int run_solve(Ctx* ctx, const std::vector<PairHost>& pairs, double tol, long lon
                 cudaEventElapsedTime(&a, pev[3 * j], pev[3 * j + 1]);
                 cudaEventElapsedTime(&b, pev[3 * j + 1], pev[3 * j + 2]);
                 kt->solve_ms += a;
-                kt->solve_launches += 3;
+                kt->solve_launches += launches_per_iteration(fp64) - 1;
                 if (j == K - 1) {
                     kt->sweep_check_ms += b;
                     kt->sweep_check_launches += 1;
@@ -541,7 +590,7 @@ int run_solve(Ctx* ctx, const std::vector<PairHost>& pairs, double tol, long lon
         cleanup();
         return HOT_ECUDA;
     }
-    const long long launches = nb * (K * kLaunchesPerIteration + kLaunchesBlockEnd);
+    const long long launches = nb * (K * launches_per_iteration(fp64) + kLaunchesBlockEnd);
     for (size_t q = 0; q < insts.size(); ++q) {
         Inst* I = insts[q];
         cudaMemcpy(&I->ctl_host, I->desc.ctl, sizeof(HotCtl), cudaMemcpyDeviceToHost);

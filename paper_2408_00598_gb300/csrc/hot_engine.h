@@ -53,7 +53,8 @@ struct PairHost {
 };
 
 int validate_pair(const double* mu, const double* nu, int m, int n, int space, int fp64, PairHost& out);
-int tile_rows(int S, int fp64);
+// rows per sweep tile; grid: resident CTAs of the sweep (0: no balancing)
+int tile_rows(int S, int fp64, int grid);
 
 // Allocate and initialise an instance on stream `st` (inputs already validated).
 int inst_create(const PairHost& p, int fp64, double sigma0_cfg, double tol, long long max_iter, int tr_override,

@@ -35,6 +35,7 @@ constexpr int kThreads = 256;          // block size of the tile kernels
 constexpr int kNK = 5;                 // per-tile check partials: r^2, min^2, x^2, z^2, c.x
 constexpr int kRowSmemBytes = 16384;   // row-partial buffer of a sweep tile
 constexpr int kMaxS = 1024;
+constexpr int kMaxTR = 128;            // FP32 tiles: TR <= S and TR * S <= kRowSmemBytes / 4
 
 enum : int {
     ST_RUNNING = 0,
@@ -65,6 +66,16 @@ struct HotCtl {
     int cancel;            // host asks the instance to stop at the next check
     unsigned int ymax_bits;// max |alpha|, |beta| (float bits, scaled units)
     int pad;
+};
+
+// Element constants of one iteration in FP32 mode (formed once per instance
+// and iteration by k_alpha32 from sigma and the Halpern counter).
+struct P32 {
+    float sih;        // 1/sigma
+    float sf;         // sigma
+    float rho, trs;   // Halpern: rho = (k+1)/(k+2), trs = 2 rho sigma
+    float h;          // 2^-E
+    float pad[3];
 };
 
 // Per-instance descriptor (read-only while a block runs).
@@ -107,6 +118,20 @@ struct HotInst {
     double* rowmu2;        // [S] sum_l mu2(k, l)
     double* k1_part;       // [n_k1] partial ||A x - b||^2
     double* dobj_part;     // [2S] partial <b, y>
+    // FP32 bulk mode only (null in FP64 mode): the per-iteration Prop. 3
+    // arithmetic runs on double-float pairs (hi, lo) of FP32 values, whose
+    // sum carries about 48 significant bits, instead of FP64
+    float2* rs2;           // [2S][S] row sums of the delta (last sweep)
+    float2* rs02;          // [2S][S] row sums of u (fixed within a cycle)
+    float2* R1a2;          // [2S][S] R1a
+    float2* K2;            // [2S][S] (mu - colsum u)/(sigma m) per slab column (/(sigma n) for f2), fixed within a cycle
+    float2* vec2;          // [4][S] T1, T2, P1, P2 of u + d
+    float2* dab2;          // [2S][2S] pieces of A^T(y-bar - y0)
+    float2* mu1f;          // [S][S] mu1 as pairs
+    float2* mu2f;          // [S][S] mu2 as pairs
+    float2* cm2;           // [S] colmu1 as pairs
+    float2* rm2;           // [S] rowmu2 as pairs
+    P32* p32;              // element constants of the current iteration
     HotCtl* ctl;
 };
 
@@ -118,7 +143,7 @@ struct WorkDev {
     HotInst* inst;         // [ninst]
     int* pre_tile;         // sweep / restart tiles: 2S * nb per instance
     int* pre_slab;         // k_alpha: 2S per instance
-    int* pre_vec;          // k_vec: 4S per instance (one warp each)
+    int* pre_vec;          // k_vec: 4S per instance (one warp each); k_vec32: vec32_items(S) CTA items
     int* pre_k1;           // k_kkt1: n_k1 per instance
     int* n_running;        // instances still running
     int* st_out;           // [ninst] status of each instance after its last check
@@ -126,21 +151,30 @@ struct WorkDev {
 
 // Host-side launch helpers (hot_kernels.cu).
 struct LaunchDims {
-    int grid_tile;         // persistent grids (multiples of the SM count)
+    // persistent grids: SM count x resident CTAs per SM of each kernel, so
+    // that every CTA of a grid-stride loop is resident from the start
+    int grid_tile;         // sweep
+    int grid_tile_chk;     // sweep of check iterations
+    int grid_rst;          // restart passes
     int grid_slab;
     int grid_vec;
     int grid_k1;
     int grid_inst;
 };
 
-constexpr int kLaunchesPerIteration = 4;   // k_vec, k_marg, k_alpha, k_sweep
+// FP64: k_vec, k_marg, k_alpha, k_sweep; FP32 bulk: k_vec32, k_alpha32, k_sweep
+inline int launches_per_iteration(int fp64) { return fp64 ? 4 : 3; }
 constexpr int kLaunchesBlockEnd = 8;       // k_kkt1, k_check, 3 x k_restart, k_restart_sigma, k_anchor, k_block_end
-void launch_solve_kernels(const WorkDev* w, const LaunchDims& ld, bool check, cudaStream_t st);
+// work items of k_vec32 per instance: T1/T2 in items of 8 outputs, P1/P2 in items of 32
+inline int vec32_items(int S) { return 2 * ((S + 7) / 8) + 2 * ((S + 31) / 32); }
+void launch_solve_kernels(const WorkDev* w, const LaunchDims& ld, int fp64, int j, bool check, cudaStream_t st);
 void launch_sweep(const WorkDev* w, const LaunchDims& ld, int fp64, int j, bool check, cudaStream_t st);
 void launch_iteration(const WorkDev* w, const LaunchDims& ld, int fp64, int j, bool check, cudaStream_t st);
 void launch_block_end(const WorkDev* w, const LaunchDims& ld, int fp64, int K, double a1, double a2, double a3,
                       cudaStream_t st);
-LaunchDims make_launch_dims(int device);
+LaunchDims make_launch_dims(int device, int fp64);
+// resident CTAs of the (non-check) sweep on the current device
+int sweep_grid(int fp64);
 // u = -sigma0 c, d = 0, x_r = z_r = 0 and the FP64 sums of u for a new instance
 // (the initial point w0 = 0: v0 = 0, y0 = 0).
 void launch_init(const HotInst& I, double sigma0, cudaStream_t st);

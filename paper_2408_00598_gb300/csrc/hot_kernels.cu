@@ -1,17 +1,20 @@
 // HOT iteration kernels for sm_103a (GB300).
 //
 // One iteration of Algorithm 2 (arXiv 2408.00598) on a batch of instances is
-// three launches:
-//   k_vec    -- slab totals and cross-slab row sums of the state (inputs of the
-//               marginals that Prop. 3 needs), one warp per output;
-//   k_alpha  -- Prop. 3: the right-hand side R of eq. (update:y) from the slab
-//               sums, its closed-form solution y-bar, and the per-slab
-//               broadcast vectors alpha/beta of A^T y-bar; one CTA per slab;
-//   k_sweep  -- Steps 2-4 fused into one streaming pass over the flow state:
-//               x-bar, z-bar = Pi_+(...), the Halpern update, and the slab row/
-//               column sums of the new state (the A v products of the next
-//               iteration); on check iterations also the KKT partial sums of
-//               eq. (kkt_res).
+// three launches in FP32 bulk mode:
+//   k_vec32   -- slab totals and cross-slab row sums of the state (inputs of
+//                the marginals that Prop. 3 needs);
+//   k_alpha32 -- Prop. 3: the right-hand side R of eq. (update:y) from the
+//                slab sums, its closed-form solution y-bar, and the per-slab
+//                broadcast vectors alpha/beta of A^T y-bar; slabs in
+//                contiguous runs per CTA;
+//   k_sweep   -- Steps 2-4 fused into one streaming pass over the flow state:
+//                x-bar, z-bar = Pi_+(...), the Halpern update, and the slab
+//                row/column sums of the new state (the A v products of the
+//                next iteration); on check iterations also the KKT partial
+//                sums of eq. (kkt_res).
+// FP64 mode runs the same solve as k_vec, k_marg (instance-wide vectors, one
+// CTA per instance) and k_alpha, in FP64.
 // A block of K iterations ends with the KKT check, the restart rule, and the
 // restart itself (new anchor), see launch_block_end.
 //
@@ -22,10 +25,13 @@
 // where z-bar = 0, i.e. on the support of the plan, where it tends to 0) is an
 // unevaluated float pair: A^T y-bar is split per slab row/column into a hi
 // part on the exact grid 2^-E of the scaled cost, so c - alpha_hi - beta_hi is
-// exact in FP32, plus an FP32 lo part.  Reductions use short FP32 chains
-// combined in FP64.
+// exact in FP32, plus an FP32 lo part.  FP64 arithmetic runs at a small
+// fraction of the FP32 rate on this part, so the per-iteration sums and the
+// Prop. 3 solve use double-float pairs (two FP32 values, about 48 bits);
+// FP64 is left to once-per-cycle work (restart, anchor sums).
 #include "hot_internal.h"
 
+#include <algorithm>
 #include <cstdint>
 #include <type_traits>
 
@@ -125,21 +131,74 @@ __device__ __forceinline__ DF df_add(DF a, DF b) {
     return df_add(r, b.lo);
 }
 __device__ __forceinline__ double df_val(DF a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ DF df_from(double x) {
+    const float h = (float)x;
+    return DF{h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ DF df_ld(float2 v) { return DF{v.x, v.y}; }
+__device__ __forceinline__ float2 df_st(DF a) { return make_float2(a.hi, a.lo); }
+__device__ __forceinline__ DF df_neg(DF a) { return DF{-a.hi, -a.lo}; }
+__device__ __forceinline__ DF df_sub(DF a, DF b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ float df_f(DF a) { return a.hi + a.lo; }
+// products: the error of hi*hi is exact by fma; the cross terms are FP32
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    const float h = p + e;
+    return DF{h, e - (h - p)};
+}
+__device__ __forceinline__ DF df_mul(DF a, float b) {
+    const float p = a.hi * b;
+    float e = fmaf(a.hi, b, -p);
+    e = fmaf(a.lo, b, e);
+    const float h = p + e;
+    return DF{h, e - (h - p)};
+}
+__device__ __forceinline__ DF df_shfl_down(DF a, int o) {
+    return DF{__shfl_down_sync(0xffffffffu, a.hi, o), __shfl_down_sync(0xffffffffu, a.lo, o)};
+}
+// warp sum in a fixed tree; the result is valid in lane 0
+__device__ __forceinline__ DF warp_sum_df(DF a) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a = df_add(a, df_shfl_down(a, o));
+    return a;
+}
+// deterministic block sum of NV pairs; every thread receives the totals
+template <int NV>
+__device__ __forceinline__ void block_sum_df(DF (&v)[NV], float2* sh) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[q] = warp_sum_df(v[q]);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) sh[q * 32 + warp] = df_st(v[q]);
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            DF x = lane < nw ? df_ld(sh[q * 32 + lane]) : DF{0.f, 0.f};
+            x = warp_sum_df(x);
+            if (lane == 0) sh[q * 32] = df_st(x);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[q] = df_ld(sh[q * 32]);
+    __syncthreads();
+}
 
 // ------------------------------------------------------ per-tile parameters --
 
-struct P32 {
-    float sih;        // 1/sigma
-    float sf;         // sigma
-    float rho, trs;   // Halpern: rho = (k+1)/(k+2), trs = 2 rho sigma
-    float h;          // 2^-E
-};
 struct P64 {
     double is, s, rho, trs, h;
 };
 
 __device__ __forceinline__ P32 make_p32(double sigma, int k, double h) {
-    P32 p;
+    P32 p{};
     p.sih = (float)(1.0 / sigma);
     p.sf = (float)sigma;
     const double rho = (k + 1.0) / (k + 2.0);
@@ -341,13 +400,7 @@ __global__ void __launch_bounds__(kThreads) k_marg(const WorkDev* __restrict__ W
         }
         // column S-1 of the last f2 slab: the dropped (m, n) row of eq. (7)
         double kap_last = I.kapa[(size_t)(2 * S - 1) * S + (S - 1)];
-        {
-            const int sl = 2 * S - 1;
-            if (I.fp64)
-                for (int b = 0; b < nb; ++b) kap_last += I.cs_part[((size_t)sl * nb + b) * S + (S - 1)];
-            else
-                for (int b = 0; b < nb; ++b) kap_last += (double)I.cs32[((size_t)sl * nb + b) * S + (S - 1)];
-        }
+        for (int b = 0; b < nb; ++b) kap_last += I.cs_part[((size_t)(2 * S - 1) * nb + b) * S + (S - 1)];
         const double mu_last = I.mu2[(size_t)(S - 1) * S + (S - 1)];
         __syncthreads();
         auto A_ = [&](int q) { return -(T1[q] - P2[q]) * is; };
@@ -439,33 +492,17 @@ __global__ void __launch_bounds__(kThreads) k_alpha(const WorkDev* __restrict__ 
         const double* __restrict__ R1a = I.R1a + (size_t)slab * S;
         const double* __restrict__ kapa = I.kapa + (size_t)slab * S;
         const size_t o = (size_t)slab * 2 * S;
-        const bool fp32 = I.ab32 != nullptr;
-        const float grid = (float)(1.0 / I.h), igrid = (float)I.h;
         float ymax = 0.f;
         double dob = 0.0;
         // idx < S: alpha (row) entries, idx >= S: beta (column) entries; returns the full piece
         auto put = [&](int idx, double dv) -> double {
             I.dab64[o + idx] = dv;
-            double full;
-            if (fp32) {
-                const float df = (float)dv;
-                const float dh = rintf(df * grid) * igrid;      // on the grid 2^-E
-                const float2 a0 = I.ab0_32[o + idx];
-                I.ab32[o + idx] = make_float4(a0.x + dh, a0.y + (df - dh), df, 0.f);
-                full = CHECK ? I.ab0[o + idx] + dv : 0.0;
-            } else {
-                full = I.ab0[o + idx] + dv;
-                I.ab64[o + idx] = full;
-            }
+            const double full = I.ab0[o + idx] + dv;
+            I.ab64[o + idx] = full;
             if (CHECK) ymax = fmaxf(ymax, fabsf((float)full));
             return full;
         };
         auto kap_delta = [&](int c) -> double {           // column total of the delta over the bands
-            if (fp32) {
-                float k = 0.f;
-                for (int b = 0; b < nb; ++b) k += I.cs32[((size_t)slab * nb + b) * S + c];
-                return (double)k;
-            }
             double k = 0.0;
             for (int b = 0; b < nb; ++b) k += I.cs_part[((size_t)slab * nb + b) * S + c];
             return k;
@@ -516,6 +553,276 @@ __global__ void __launch_bounds__(kThreads) k_alpha(const WorkDev* __restrict__ 
     }
 }
 
+// ------------------------------------------------------- k_vec32/k_alpha32 --
+// FP32 bulk mode.  The same Prop. 3 solve as k_vec/k_marg/k_alpha, with the
+// per-iteration arithmetic on double-float pairs: FP64 throughput on this
+// part is a small fraction of FP32, and pairs carry about 48 bits, far more
+// than the FP32 row and column partial sums they combine.
+//
+// k_vec32: T1, T2, P1, P2 of u + d.  A work item is one CTA: for T1/T2 (sums
+// along contiguous rows) 8 outputs, one warp each; for P1/P2 (sums down the
+// columns of the row-sum matrices) 32 outputs, one per lane, rows split over
+// the warps and combined in a fixed order.
+__global__ void __launch_bounds__(kThreads) k_vec32(const WorkDev* __restrict__ W) {
+    constexpr int kW = kThreads / 32;
+    __shared__ float2 s_p[kThreads];
+    __shared__ int s_t[3];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ninst = W->ninst;
+    const int nitems = W->pre_vec[ninst];
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        if (threadIdx.x == 0) {
+            const int i = find_inst(W->pre_vec, ninst, it);
+            s_t[0] = i;
+            s_t[1] = it - W->pre_vec[i];
+            s_t[2] = W->inst[i].ctl->status;
+        }
+        __syncthreads();
+        if (s_t[2] == ST_RUNNING) {
+            const HotInst& I = W->inst[s_t[0]];
+            const int S = I.S;
+            const int q8 = (S + 7) / 8, q32 = (S + 31) / 32;
+            const int item = s_t[1];
+            const float2* __restrict__ rs = I.rs2;
+            const float2* __restrict__ r0 = I.rs02;
+            if (item < 2 * q8) {
+                const int which = item / q8;                 // 0: T1 (f1 slab totals), 1: T2
+                const int q = (item % q8) * 8 + warp;
+                if (q < S) {                                  // warp-uniform
+                    const size_t row = (size_t)(which * S + q) * S;
+                    DF acc{0.f, 0.f};
+                    for (int t = lane; t < S; t += 32) {
+                        acc = df_add(acc, df_ld(r0[row + t]));
+                        acc = df_add(acc, df_ld(rs[row + t]));
+                    }
+                    acc = warp_sum_df(acc);
+                    if (lane == 0) I.vec2[which * S + q] = df_st(acc);
+                }
+            } else {
+                const int it2 = item - 2 * q8;
+                const int which = it2 / q32;                 // 0: P1 (over f1 slabs), 1: P2
+                const int q = (it2 % q32) * 32 + lane;
+                DF acc{0.f, 0.f};
+                if (q < S)
+                    for (int t = warp; t < S; t += kW) {
+                        const size_t idx = (size_t)(which * S + t) * S + q;
+                        acc = df_add(acc, df_ld(r0[idx]));
+                        acc = df_add(acc, df_ld(rs[idx]));
+                    }
+                s_p[threadIdx.x] = df_st(acc);
+                __syncthreads();
+                if (warp == 0 && q < S) {
+                    DF tot = df_ld(s_p[lane]);
+                    for (int w = 1; w < kW; ++w) tot = df_add(tot, df_ld(s_p[w * 32 + lane]));
+                    I.vec2[(2 + which) * S + q] = df_st(tot);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Scalars of Prop. 3 shared by a CTA (formed by thread 0).
+struct AlphaK {
+    DF is, in, im, imn, imin, iw, dl, sumd, isim, isin, fix;
+    DF cst, dsiw, tin, yasum, T3in;
+};
+
+// The instance-wide O(S) stage: from T1, T2, P1, P2 (k_vec32) the vectors
+//   mvA_q = a_q/n - (1/m + 1/n) bb_q      (column part of y1-hat)
+//   mvS_q = r3_q/n + T3/n^2 - (m+n) y1a_q (row part of y1, times m+n)
+//   sy_q  = sum_k y1(k, q)                (for y2)
+//   sp_q  = sum_j y1(q, j)                (for y3)
+// into sq[0..3][q].  With e_q = rowR1_q + r3_q and d the diagonal of W-hat,
+// every global scalar follows from four sums: sum a, sum bb, T3 = sum r3 and
+// sum d_q e_q, since s_q = (e_q + cst)/(m+n) with
+// cst = sum a/n - (1/m+1/n) sum bb + T3/n.
+__device__ void alpha32_stage(const HotInst& I, float2 (*sq)[kMaxS], float2* s_red, AlphaK& K) {
+    const int S = I.S, nb = I.nb;
+    if (threadIdx.x == 0) {
+        const double m = S, n = S;
+        const double is = 1.0 / I.ctl->sigma;
+        const double dl = (1.0 - 1.0 / n) / (m + 1.0);
+        const double iw = 1.0 / (1.0 / m - dl);       // 1/w, w = 1/m - (1-1/n)/(m+1)
+        // the dropped (m, n) row of eq. (7): column S-1 of the last f2 slab
+        float kd = 0.f;
+        for (int b = 0; b < nb; ++b) kd += I.cs32[((size_t)(2 * S - 1) * nb + b) * S + (S - 1)];
+        const double kl = I.kapa[(size_t)(2 * S - 1) * S + (S - 1)] + (double)kd;
+        const double mu_last = I.mu2[(size_t)(S - 1) * S + (S - 1)];
+        K.is = df_from(is);
+        K.in = df_from(1.0 / n);
+        K.im = df_from(1.0 / m);
+        K.imn = df_from(1.0 / (m + n));
+        K.imin = df_from(1.0 / m + 1.0 / n);
+        K.iw = df_from(iw);
+        K.dl = df_from(dl);
+        K.sumd = df_from((S - 1) / m + dl);
+        K.isim = df_from(is / m);
+        K.isin = df_from(is / n);
+        K.fix = df_from((mu_last - kl) * is);
+    }
+    __syncthreads();
+    const DF is = K.is, fix = K.fix, im = K.im, dl = K.dl;
+    const float2* __restrict__ v = I.vec2;
+    DF red[4] = {DF{0.f, 0.f}, DF{0.f, 0.f}, DF{0.f, 0.f}, DF{0.f, 0.f}};
+    for (int q = threadIdx.x; q < S; q += blockDim.x) {
+        const DF T1 = df_ld(v[q]), T2 = df_ld(v[S + q]), P1 = df_ld(v[2 * S + q]), P2 = df_ld(v[3 * S + q]);
+        const DF A = df_mul(df_sub(P2, T1), is);                     // a_q = -(T1 - P2)/sigma
+        const DF B = df_mul(df_sub(df_ld(I.cm2[q]), T1), is);         // bb_q
+        DF R3 = df_mul(df_sub(df_ld(I.rm2[q]), T2), is);              // r3_q
+        if (q == S - 1) R3 = df_sub(R3, fix);
+        const DF e = df_add(df_mul(df_sub(T2, P1), is), R3);          // rowR1_q + r3_q
+        sq[0][q] = df_st(A);
+        sq[1][q] = df_st(B);
+        sq[2][q] = df_st(R3);
+        sq[3][q] = df_st(e);
+        red[0] = df_add(red[0], A);
+        red[1] = df_add(red[1], B);
+        red[2] = df_add(red[2], R3);
+        red[3] = df_add(red[3], df_mul(e, q == S - 1 ? dl : im));
+    }
+    block_sum_df<4>(red, s_red);
+    if (threadIdx.x == 0) {
+        const DF T3 = red[2];
+        const DF cst = df_add(df_sub(df_mul(red[0], K.in), df_mul(red[1], K.imin)), df_mul(T3, K.in));
+        const DF ds = df_mul(df_add(red[3], df_mul(cst, K.sumd)), K.imn);      // sum d_q s_q
+        const DF dsiw = df_mul(ds, K.iw);
+        const DF tsum = df_neg(df_add(ds, df_mul(dsiw, K.sumd)));              // 1^T W-hat s
+        const DF tin = df_mul(tsum, K.in);
+        K.cst = cst;
+        K.dsiw = dsiw;
+        K.tin = tin;
+        K.yasum = df_add(tsum, df_mul(tin, (float)S));                         // 1^T y1a
+        K.T3in = df_mul(T3, K.in);
+    }
+    __syncthreads();
+    const DF in = K.in, imn = K.imn, imin = K.imin, cst = K.cst, dsiw = K.dsiw, tin = K.tin;
+    const DF yasum = K.yasum, T3in = K.T3in;
+    const DF T3in2 = df_mul(T3in, in);
+    const float mpn = (float)(2 * S);
+    for (int q = threadIdx.x; q < S; q += blockDim.x) {
+        const DF A = df_ld(sq[0][q]), B = df_ld(sq[1][q]), R3 = df_ld(sq[2][q]), e = df_ld(sq[3][q]);
+        const DF sk = df_mul(df_add(e, cst), imn);                             // s_q
+        const DF ya = df_add(df_neg(df_mul(df_add(sk, dsiw), q == S - 1 ? dl : im)), tin);   // y1a_q
+        sq[0][q] = df_st(df_sub(df_mul(A, in), df_mul(B, imin)));
+        sq[1][q] = df_st(df_sub(df_add(df_mul(R3, in), T3in2), df_mul(ya, mpn)));
+        sq[2][q] = df_st(df_sub(df_mul(df_add(df_sub(A, B), T3in), in), yasum));
+        sq[3][q] = df_st(df_sub(sk, df_mul(ya, (float)S)));
+    }
+    __syncthreads();
+}
+
+// k_alpha32: per slab, the entries of y-bar - y0 (pairs, kept for the
+// restart), their FP32 split for the sweep, and on check iterations <b, y>
+// and max |A^T y| pieces.  Slabs are taken in contiguous runs per CTA so that
+// the instance-wide stage is formed once per instance and CTA.
+template <bool CHECK>
+__global__ void __launch_bounds__(kThreads) k_alpha32(const WorkDev* __restrict__ W, int j) {
+    __shared__ float2 sq[4][kMaxS];
+    __shared__ float2 s_red[4 * 32];
+    __shared__ float s_max[32];
+    __shared__ AlphaK K;
+    __shared__ int s_t[4];
+    const int ninst = W->ninst;
+    const int nslab = W->pre_slab[ninst];
+    const int chunk = (nslab + gridDim.x - 1) / gridDim.x;
+    const int t0 = blockIdx.x * chunk, t1 = min(nslab, t0 + chunk);
+    int cached = -1;
+    for (int t = t0; t < t1; ++t) {
+        if (threadIdx.x == 0) {
+            const int i = find_inst(W->pre_slab, ninst, t);
+            s_t[0] = i;
+            s_t[1] = t - W->pre_slab[i];
+            s_t[2] = W->inst[i].ctl->status;
+        }
+        __syncthreads();
+        if (s_t[2] != ST_RUNNING) {
+            __syncthreads();
+            continue;
+        }
+        const HotInst& I = W->inst[s_t[0]];
+        if (s_t[0] != cached) {                          // block-uniform
+            alpha32_stage(I, sq, s_red, K);
+            cached = s_t[0];
+        }
+        const int slab = s_t[1];
+        const int S = I.S, nb = I.nb;
+        if (slab == 0 && threadIdx.x == 0) *I.p32 = make_p32(I.ctl->sigma, I.ctl->k + j, I.h);
+        const DF is = K.is, imn = K.imn;
+        const float2* __restrict__ rs = I.rs2;
+        const float2* __restrict__ R1a = I.R1a2 + (size_t)slab * S;
+        const float2* __restrict__ K2 = I.K2 + (size_t)slab * S;
+        const size_t o = (size_t)slab * 2 * S;
+        const float grid = (float)(1.0 / I.h), igrid = (float)I.h;
+        float ymax = 0.f;
+        DF dob{0.f, 0.f};
+        // idx < S: alpha (row) entries, idx >= S: beta (column) entries; returns the full piece on check iterations
+        auto put = [&](int idx, DF dv) -> DF {
+            I.dab2[o + idx] = df_st(dv);
+            const float df = df_f(dv);
+            const float dh = rintf(df * grid) * igrid;          // on the grid 2^-E
+            const float2 a0 = I.ab0_32[o + idx];
+            I.ab32[o + idx] = make_float4(a0.x + dh, a0.y + (df - dh), df, 0.f);
+            DF full{0.f, 0.f};
+            if (CHECK) {
+                full = df_add(DF{a0.x, a0.y}, dv);
+                ymax = fmaxf(ymax, fabsf(full.hi));
+            }
+            return full;
+        };
+        auto kap_delta = [&](int c) -> float {                 // column total of the delta over the bands
+            float k = 0.f;
+            for (int b = 0; b < nb; ++b) k += I.cs32[((size_t)slab * nb + b) * S + c];
+            return k;
+        };
+        if (slab < S) {
+            const int j = slab;
+            const DF colj = df_ld(sq[0][j]);
+            for (int k = threadIdx.x; k < S; k += blockDim.x) {
+                const DF dr = df_sub(df_ld(rs[(size_t)j * S + k]), df_ld(rs[(size_t)(S + k) * S + j]));
+                const DF R1 = df_sub(df_ld(R1a[k]), df_mul(dr, is));
+                put(k, df_mul(df_add(df_add(R1, colj), df_ld(sq[1][k])), imn));     // y1(k, j)
+            }
+            const DF sy_im = df_mul(df_ld(sq[2][j]), K.im);
+            const DF isim = K.isim;
+            for (int i = threadIdx.x; i < S; i += blockDim.x) {
+                const DF dv = df_sub(df_sub(df_ld(K2[i]), df_mul(isim, kap_delta(i))), sy_im);   // y2(i, j)
+                const DF full = put(S + i, dv);
+                if (CHECK) dob = df_add(dob, df_mul(df_ld(I.mu1f[(size_t)i * S + j]), full));
+            }
+        } else {
+            const int k = slab - S;
+            const DF rowk = df_ld(sq[1][k]);
+            for (int j = threadIdx.x; j < S; j += blockDim.x) {
+                const DF dr = df_sub(df_ld(rs[(size_t)j * S + k]), df_ld(rs[(size_t)(S + k) * S + j]));
+                const DF R1 = df_sub(df_ld(R1a[j]), df_mul(dr, is));
+                put(j, df_neg(df_mul(df_add(df_add(R1, df_ld(sq[0][j])), rowk), imn)));   // -y1(k, j)
+            }
+            const DF sp_in = df_mul(df_ld(sq[3][k]), K.in);
+            const DF isin = K.isin;
+            for (int l = threadIdx.x; l < S; l += blockDim.x) {
+                if (k == S - 1 && l == S - 1) {
+                    put(S + l, DF{0.f, 0.f});                   // no row: y3(m, n) = 0
+                    continue;
+                }
+                const DF dv = df_add(df_sub(df_ld(K2[l]), df_mul(isin, kap_delta(l))), sp_in);   // y3(k, l)
+                const DF full = put(S + l, dv);
+                if (CHECK) dob = df_add(dob, df_mul(df_ld(I.mu2f[(size_t)k * S + l]), full));
+            }
+        }
+        if (CHECK) {
+            DF red[1] = {dob};
+            block_sum_df<1>(red, s_red);
+            const float bm = block_max(ymax, s_max);
+            if (threadIdx.x == 0) {
+                I.dobj_part[slab] = df_val(red[0]);
+                atomicMax(&I.ctl->ymax_bits, __float_as_uint(bm));
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // Once per cycle (after a restart, and at the start): the anchor parts of the
 // right-hand side, per slab: R1a along the slab's rows and the column totals
 // of u.  One CTA per slab.
@@ -526,10 +833,22 @@ __device__ __forceinline__ void anchor_slab(const HotInst& I, int slab, double s
         // f1 slab j: rows k, R1(k, j); f2 slab k: rows j, R1(k, j)
         const int j = slab < S ? slab : q;
         const int k = slab < S ? q : slab - S;
-        I.R1a[(size_t)slab * S + q] = -(I.rs0[(size_t)j * S + k] - I.rs0[(size_t)(S + k) * S + j]) * is;
+        const double r1a = -(I.rs0[(size_t)j * S + k] - I.rs0[(size_t)(S + k) * S + j]) * is;
+        I.R1a[(size_t)slab * S + q] = r1a;
         double kap = 0.0;
         for (int b = 0; b < nb; ++b) kap += I.cs0_part[((size_t)slab * nb + b) * S + q];
         I.kapa[(size_t)slab * S + q] = kap;
+        if (!I.fp64) {
+            // pairs for the FP32-mode solve; K2 is the sigma-scaled anchor part
+            // of y2 (f1 slab j, column i) resp. y3 (f2 slab k, column l)
+            I.rs02[(size_t)slab * S + q] = df_st(df_from(I.rs0[(size_t)slab * S + q]));
+            I.R1a2[(size_t)slab * S + q] = df_st(df_from(r1a));
+            double k2;
+            if (slab < S) k2 = (I.mu1[(size_t)q * S + slab] - kap) * is / S;
+            else if (slab == 2 * S - 1 && q == S - 1) k2 = 0.0;
+            else k2 = (I.mu2[(size_t)(slab - S) * S + q] - kap) * is / S;
+            I.K2[(size_t)slab * S + q] = df_st(df_from(k2));
+        }
     }
 }
 
@@ -555,22 +874,17 @@ __global__ void __launch_bounds__(kThreads) k_anchor_one(HotInst I, double sigma
 }
 
 // --------------------------------------------------------------- k_sweep --
-// Steps 2-4 of Algorithm 2 on one tile (TR rows of one slab).
-template <typename T, bool CHECK>
-__global__ void __launch_bounds__(kThreads) k_sweep(const WorkDev* __restrict__ W, int j) {
-    using V = VecT<T>;
-    constexpr int NV = V::N;
-    // row partials, one padded row of NC+1 entries per tile row (conflict-free
-    // on the write, where a warp spans columns, and on the reduction, where it
-    // spans rows)
-    constexpr int kRowN = kRowSmemBytes / sizeof(float) / (sizeof(T) / sizeof(float)) + 256;
-    __shared__ __align__(16) T s_row[kRowN];
-    __shared__ __align__(16) T s_col[kThreads * NV];
-    __shared__ __align__(16) T s_xrow[CHECK ? kRowN : 1];
-    __shared__ __align__(16) T s_xcol[CHECK ? kThreads * NV : 1];
+// FP64 mode: Steps 2-4 of Algorithm 2 on one tile (TR rows of one slab) per
+// loop trip.
+__global__ void __launch_bounds__(kThreads, 2) k_sweep64(const WorkDev* __restrict__ W, int j, int check) {
+    constexpr int NV = 2;
+    constexpr int kRowN = kRowSmemBytes / sizeof(double) + 256;
+    __shared__ __align__(16) double s_row[kRowN];
+    __shared__ __align__(16) double s_col[kThreads * NV];
+    __shared__ __align__(16) double s_xrow[kRowN];
+    __shared__ __align__(16) double s_xcol[kThreads * NV];
     __shared__ double s_red[kNK * 32];
     __shared__ int s_tile[4];
-    __shared__ P32 s_p32;
     __shared__ P64 s_p64;
     const int ninst = W->ninst;
     const int ntiles = W->pre_tile[ninst];
@@ -590,146 +904,56 @@ __global__ void __launch_bounds__(kThreads) k_sweep(const WorkDev* __restrict__ 
         const bool active = ro < P;
         const int r0 = band * TR, r1 = min(S, r0 + TR);
         const size_t off = (size_t)slab * S * S;
-        const T* __restrict__ u = (const T*)I.u + off;
-        const T* __restrict__ din = (const T*)((j & 1) ? I.d1 : I.d0) + off;
-        T* __restrict__ dout = (T*)((j & 1) ? I.d0 : I.d1) + off;
-        // per-tile constants (FP64 divisions are slow here: one thread forms them)
-        if (threadIdx.x == 0) {
-            const int kc = I.ctl->k + j;
-            if constexpr (std::is_same<T, float>::value) s_p32 = make_p32(I.ctl->sigma, kc, I.h);
-            else s_p64 = make_p64(I.ctl->sigma, kc, I.h);
-        }
+        const double* __restrict__ u = (const double*)I.u + off;
+        const double* __restrict__ din = (const double*)((j & 1) ? I.d1 : I.d0) + off;
+        double* __restrict__ dout = (double*)((j & 1) ? I.d0 : I.d1) + off;
+        if (threadIdx.x == 0) s_p64 = make_p64(I.ctl->sigma, I.ctl->k + j, I.h);
         __syncthreads();
         const int c0 = cg * NV;
-        T cacc[NV], xacc[NV];
+        double cacc[NV], xacc[NV];
 #pragma unroll
-        for (int e = 0; e < NV; ++e) cacc[e] = xacc[e] = T(0);
-        float k32[kNK] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int e = 0; e < NV; ++e) cacc[e] = xacc[e] = 0.0;
         double k64[kNK] = {0.0, 0.0, 0.0, 0.0, 0.0};
-
-        if constexpr (std::is_same<T, float>::value) {
-            const P32 p = s_p32;
-            const float4* ab = I.ab32 + (size_t)slab * 2 * S;
-            float4 bq[NV];
-            float cf[NV];
+        const P64 p = s_p64;
+        const double* ab = I.ab64 + (size_t)slab * 2 * S;
+        const double* dab = I.dab64 + (size_t)slab * 2 * S;
+        double bb[NV], db[NV], cf[NV];
 #pragma unroll
-            for (int e = 0; e < NV; ++e) {
-                bq[e] = active ? ab[S + c0 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
-                cf[e] = (float)(c0 + e);
-            }
-            if (active) {
-                int nrow = 0;
-                auto row = [&](int r, const float (&uu)[NV], const float (&dd)[NV]) {
-                    const float4 a = ab[r];
-                    const float rf = (float)r;
-                    float out[NV], xo[NV];
+        for (int e = 0; e < NV; ++e) {
+            bb[e] = active ? ab[S + c0 + e] : 0.0;
+            db[e] = active ? dab[S + c0 + e] : 0.0;
+            cf[e] = (double)(c0 + e);
+        }
+        if (active) {
+            for (int r = r0 + ro; r < r1; r += P) {
+                const double a = ab[r], da = dab[r];
+                const double rf = (double)r;
+                double uu[NV], dd[NV], out[NV], xo[NV];
+                VecT<double>::ld(u + (size_t)r * S + c0, uu);
+                VecT<double>::ld(din + (size_t)r * S + c0, dd);
 #pragma unroll
-                    for (int e = 0; e < NV; ++e) {
-                        const float dc = rf - cf[e];
-                        const float cq = dc * dc;
-                        const E32 el = elem32(uu[e], dd[e], cq, a, bq[e], p);
-                        out[e] = fmaf(p.trs, el.r, p.rho * dd[e]);
-                        if constexpr (CHECK) {
-                            float xb, zb;
-                            xz32(el, p, xb, zb);
-                            xo[e] = xb;
-                            const float mn = fminf(xb, zb);
-                            k32[0] = fmaf(el.r, el.r, k32[0]);
-                            k32[1] = fmaf(mn, mn, k32[1]);
-                            k32[2] = fmaf(xb, xb, k32[2]);
-                            k32[3] = fmaf(zb, zb, k32[3]);
-                            k32[4] = fmaf(cq, xb, k32[4]);
-                            xacc[e] += xb;
-                        }
-                        cacc[e] += out[e];
+                for (int e = 0; e < NV; ++e) {
+                    const double dc = rf - cf[e];
+                    const double cq = dc * dc;
+                    const E64 el = elem64(uu[e], dd[e], cq, a, bb[e], da, db[e], p);
+                    out[e] = p.rho * dd[e] + p.trs * el.r;
+                    if (check) {
+                        double xb, zb;
+                        xz64(el, p, xb, zb);
+                        xo[e] = xb;
+                        const double mn = fmin(xb, zb);
+                        k64[0] += el.r * el.r;
+                        k64[1] += mn * mn;
+                        k64[2] += xb * xb;
+                        k64[3] += zb * zb;
+                        k64[4] += cq * xb;
+                        xacc[e] += xb;
                     }
-                    V::st(dout + (size_t)r * S + c0, out);
-                    s_row[(r - r0) * (NC + 1) + cg] = (out[0] + out[1]) + (out[2] + out[3]);
-                    if constexpr (CHECK) {
-                        s_xrow[(r - r0) * (NC + 1) + cg] = (xo[0] + xo[1]) + (xo[2] + xo[3]);
-                        // FP32 chains of 64 terms, combined in FP64
-                        if ((++nrow & 15) == 0) {
-#pragma unroll
-                            for (int q = 0; q < kNK; ++q) {
-                                k64[q] += (double)k32[q];
-                                k32[q] = 0.f;
-                            }
-                        }
-                    }
-                };
-                // kStages-deep cp.async pipeline over the passes of this tile:
-                // pass q covers row r0 + ro + q P of every active thread
-                extern __shared__ float4 s_stage[];          // [kStages][2][kThreads]
-                const int npass = (r1 - r0 + P - 1) / P;
-                auto issue = [&](int q) {
-                    const int r = r0 + ro + q * P;
-                    if (r < r1) {
-                        float4* su = s_stage + (size_t)(q % kStages) * 2 * kThreads + threadIdx.x;
-                        cp_async16(su, u + (size_t)r * S + c0);
-                        cp_async16(su + kThreads, din + (size_t)r * S + c0);
-                    }
-                    cp_async_commit();                       // empty groups keep the count aligned
-                };
-#pragma unroll
-                for (int q = 0; q < kStages - 1; ++q) issue(q);
-                for (int q = 0; q < npass; ++q) {
-                    issue(q + kStages - 1);
-                    cp_async_wait<kStages - 1>();            // this thread's pass-q copies are in
-                    const int r = r0 + ro + q * P;
-                    if (r < r1) {
-                        const float4* su = s_stage + (size_t)(q % kStages) * 2 * kThreads + threadIdx.x;
-                        const float4 U = su[0], D = su[kThreads];
-                        const float uu[NV] = {U.x, U.y, U.z, U.w};
-                        const float dd[NV] = {D.x, D.y, D.z, D.w};
-                        row(r, uu, dd);
-                    }
+                    cacc[e] += out[e];
                 }
-                cp_async_wait<0>();
-            }
-#pragma unroll
-            for (int q = 0; q < kNK; ++q) k64[q] += (double)k32[q];
-        } else {
-            const P64 p = s_p64;
-            const double* ab = I.ab64 + (size_t)slab * 2 * S;
-            const double* dab = I.dab64 + (size_t)slab * 2 * S;
-            double bb[NV], db[NV], cf[NV];
-#pragma unroll
-            for (int e = 0; e < NV; ++e) {
-                bb[e] = active ? ab[S + c0 + e] : 0.0;
-                db[e] = active ? dab[S + c0 + e] : 0.0;
-                cf[e] = (double)(c0 + e);
-            }
-            if (active) {
-                for (int r = r0 + ro; r < r1; r += P) {
-                    const double a = ab[r], da = dab[r];
-                    const double rf = (double)r;
-                    double uu[NV], dd[NV], out[NV], xo[NV];
-                    V::ld(u + (size_t)r * S + c0, uu);
-                    V::ld(din + (size_t)r * S + c0, dd);
-#pragma unroll
-                    for (int e = 0; e < NV; ++e) {
-                        const double dc = rf - cf[e];
-                        const double cq = dc * dc;
-                        const E64 el = elem64(uu[e], dd[e], cq, a, bb[e], da, db[e], p);
-                        out[e] = p.rho * dd[e] + p.trs * el.r;
-                        if constexpr (CHECK) {
-                            double xb, zb;
-                            xz64(el, p, xb, zb);
-                            xo[e] = xb;
-                            const double mn = fmin(xb, zb);
-                            k64[0] += el.r * el.r;
-                            k64[1] += mn * mn;
-                            k64[2] += xb * xb;
-                            k64[3] += zb * zb;
-                            k64[4] += cq * xb;
-                            xacc[e] += xb;
-                        }
-                        cacc[e] += out[e];
-                    }
-                    V::st(dout + (size_t)r * S + c0, out);
-                    s_row[(r - r0) * (NC + 1) + cg] = out[0] + out[1];
-                    if constexpr (CHECK) s_xrow[(r - r0) * (NC + 1) + cg] = xo[0] + xo[1];
-                }
+                VecT<double>::st(dout + (size_t)r * S + c0, out);
+                s_row[(r - r0) * (NC + 1) + cg] = out[0] + out[1];
+                if (check) s_xrow[(r - r0) * (NC + 1) + cg] = xo[0] + xo[1];
             }
         }
         __syncthreads();
@@ -737,30 +961,20 @@ __global__ void __launch_bounds__(kThreads) k_sweep(const WorkDev* __restrict__ 
 #pragma unroll
             for (int e = 0; e < NV; ++e) {
                 s_col[ro * S + c0 + e] = cacc[e];
-                if constexpr (CHECK) s_xcol[ro * S + c0 + e] = xacc[e];
+                if (check) s_xcol[ro * S + c0 + e] = xacc[e];
             }
         }
         __syncthreads();
         const size_t cbase = ((size_t)slab * nb + band) * S;
         for (int c = threadIdx.x; c < S; c += blockDim.x) {
-            if constexpr (std::is_same<T, float>::value) {
-                I.cs32[cbase + c] = (float)sum_f32_strided(s_col + c, P, S);
-                if constexpr (CHECK) I.xcs_part[cbase + c] = sum_f32_strided(s_xcol + c, P, S);
-            } else {
-                I.cs_part[cbase + c] = sum_f64_strided(s_col + c, P, S);
-                if constexpr (CHECK) I.xcs_part[cbase + c] = sum_f64_strided(s_xcol + c, P, S);
-            }
+            I.cs_part[cbase + c] = sum_f64_strided(s_col + c, P, S);
+            if (check) I.xcs_part[cbase + c] = sum_f64_strided(s_xcol + c, P, S);
         }
         for (int rr = threadIdx.x; rr < r1 - r0; rr += blockDim.x) {
-            if constexpr (std::is_same<T, float>::value) {
-                I.rs[(size_t)slab * S + r0 + rr] = sum_f32_strided(s_row + rr * (NC + 1), NC, 1);
-                if constexpr (CHECK) I.xrs[(size_t)slab * S + r0 + rr] = sum_f32_strided(s_xrow + rr * (NC + 1), NC, 1);
-            } else {
-                I.rs[(size_t)slab * S + r0 + rr] = sum_f64_strided(s_row + rr * (NC + 1), NC, 1);
-                if constexpr (CHECK) I.xrs[(size_t)slab * S + r0 + rr] = sum_f64_strided(s_xrow + rr * (NC + 1), NC, 1);
-            }
+            I.rs[(size_t)slab * S + r0 + rr] = sum_f64_strided(s_row + rr * (NC + 1), NC, 1);
+            if (check) I.xrs[(size_t)slab * S + r0 + rr] = sum_f64_strided(s_xrow + rr * (NC + 1), NC, 1);
         }
-        if constexpr (CHECK) {
+        if (check) {
             block_sum<kNK>(k64, s_red);
             if (threadIdx.x == 0) {
                 double* o = I.tile_kkt + ((size_t)slab * nb + band) * kNK;
@@ -770,6 +984,232 @@ __global__ void __launch_bounds__(kThreads) k_sweep(const WorkDev* __restrict__ 
         }
         __syncthreads();
     }
+}
+
+// -------------------------------------------------------------- k_sweep32 --
+// FP32 bulk mode: Steps 2-4 of Algorithm 2 as one streaming pass over the
+// flow state.  A CTA takes the tiles blockIdx.x, blockIdx.x + G, ... (TR rows
+// of one slab each) and streams their passes (P rows: every thread one float4
+// of u and one of the delta) through a kStages-deep cp.async ring that is not
+// drained between tiles, so the next tile's loads are in flight while the
+// current tile's row and column sums are reduced.  The rows' alpha pieces
+// travel in the group of each tile's first pass into a ring of their own.
+struct TileD {
+    int inst, slab, band, S, NC, P, r0, r1, npass;
+};
+
+// Every thread resolves tiles itself (no barrier); npass = 0 marks a tile of
+// an instance that is not running, or t past the end.
+__device__ __forceinline__ TileD tile_desc(const WorkDev* __restrict__ W, int t, int ntiles) {
+    TileD d{};
+    if (t >= ntiles) return d;
+    const int i = find_inst(W->pre_tile, W->ninst, t);
+    const HotInst& I = W->inst[i];
+    const int loc = t - W->pre_tile[i];
+    d.inst = i;
+    d.S = I.S;
+    d.slab = loc / I.nb;
+    d.band = loc % I.nb;
+    d.NC = I.S / 4;
+    d.P = kThreads / d.NC;
+    d.r0 = d.band * I.TR;
+    d.r1 = min(I.S, d.r0 + I.TR);
+    if (I.ctl->status == ST_RUNNING) d.npass = (d.r1 - d.r0 + d.P - 1) / d.P;
+    return d;
+}
+
+template <bool CHECK>
+__global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkDev* __restrict__ W, int j) {
+    constexpr int NV = 4;
+    constexpr int kRowN = kRowSmemBytes / sizeof(float) + 256;
+    __shared__ __align__(16) float s_row[kRowN];
+    __shared__ __align__(16) float s_col[kThreads * NV];
+    __shared__ __align__(16) float s_xrow[CHECK ? kRowN : 1];
+    __shared__ __align__(16) float s_xcol[CHECK ? kThreads * NV : 1];
+    __shared__ __align__(16) float4 s_alpha[kStages][kMaxTR];
+    __shared__ float2 s_red[kNK * 32];
+    extern __shared__ float4 s_stage[];          // [kStages][2][kThreads]
+    const int tid = threadIdx.x;
+    const int G = gridDim.x;
+    const int ntiles = W->pre_tile[W->ninst];
+
+    // issue cursor: tile it, its next pass iq, tiles started ik (alpha ring);
+    // per tile the thread's source pointers and row offset are formed once
+    struct Cur {
+        const float* u;
+        const float* d;
+        const float4* a;           // alpha pieces of the tile's rows
+        int step;                  // P rows, in floats
+        int ro, P, nr, npass;      // thread's row in a pass, rows per pass, tile rows, passes
+        int iq, it, ik;
+    } c;
+    auto set_tile = [&](int t) {
+        TileD d = tile_desc(W, t, ntiles);
+        while (t < ntiles && d.npass == 0) {
+            t += G;
+            d = tile_desc(W, t, ntiles);
+        }
+        c.it = t;
+        c.iq = 0;
+        if (t < ntiles) {
+            const HotInst& I = W->inst[d.inst];
+            const int ro = tid / d.NC, cg = tid % d.NC;
+            const size_t base = ((size_t)d.slab * d.S + d.r0) * d.S + (size_t)ro * d.S + (size_t)cg * NV;
+            c.u = (const float*)I.u + base;
+            c.d = (const float*)((j & 1) ? I.d1 : I.d0) + base;
+            c.a = I.ab32 + (size_t)d.slab * 2 * d.S + d.r0;
+            c.step = d.P * d.S;
+            c.ro = ro;
+            c.P = d.P;
+            c.nr = d.r1 - d.r0;
+            c.npass = d.npass;
+        }
+    };
+    c.ik = 0;
+    set_tile(blockIdx.x);
+    // one commit group per call: the copies of global pass n (ring slot n % kStages)
+    auto issue = [&](int n) {
+        if (c.it < ntiles) {
+            if (c.ro < c.P && c.ro + c.iq * c.P < c.nr) {
+                float4* su = s_stage + (size_t)(n % kStages) * 2 * kThreads + tid;
+                const size_t o = (size_t)c.iq * c.step;
+                cp_async16(su, c.u + o);
+                cp_async16(su + kThreads, c.d + o);
+            }
+            if (c.iq == 0 && tid < c.nr) cp_async16(&s_alpha[c.ik % kStages][tid], c.a + tid);
+            if (++c.iq == c.npass) {
+                ++c.ik;
+                set_tile(c.it + G);
+            }
+        }
+        cp_async_commit();
+    };
+#pragma unroll 1
+    for (int q = 0; q < kStages - 1; ++q) issue(q);
+
+    int n = 0;                                   // global index of the next pass to compute
+    int ct = blockIdx.x, ck = 0;
+    TileD dc = tile_desc(W, ct, ntiles);
+    while (ct < ntiles && dc.npass == 0) {
+        ct += G;
+        dc = tile_desc(W, ct, ntiles);
+    }
+    while (ct < ntiles) {
+        const HotInst& I = W->inst[dc.inst];
+        const int S = dc.S, NC = dc.NC, P = dc.P, nb = I.nb;
+        const int slab = dc.slab, band = dc.band, r0 = dc.r0, r1 = dc.r1;
+        const int cg = tid % NC, ro = tid / NC;
+        const bool active = ro < P;
+        const int c0 = cg * NV;
+        float* __restrict__ dout = (float*)((j & 1) ? I.d0 : I.d1) + (size_t)slab * S * S;
+        const float4* ab = I.ab32 + (size_t)slab * 2 * S;
+        const P32 p = *I.p32;
+        float4 bq[NV];
+        float cf[NV];
+#pragma unroll
+        for (int e = 0; e < NV; ++e) {
+            bq[e] = active ? ab[S + c0 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
+            cf[e] = (float)(c0 + e);
+        }
+        // the tile's alpha pieces came with its first pass (group n)
+        cp_async_wait<kStages - 2>();
+        __syncthreads();
+        const float4* sa = s_alpha[ck % kStages];
+        float cacc[NV], xacc[NV];
+#pragma unroll
+        for (int e = 0; e < NV; ++e) cacc[e] = xacc[e] = 0.f;
+        // KKT partials: FP32 chains of at most 64 terms per thread and tile
+        // (a tile has TR * S / 1024 <= 16 passes), summed over the CTA in pairs
+        float k32[kNK] = {0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+        for (int q = 0; q < dc.npass; ++q, ++n) {
+            issue(n + kStages - 1);
+            cp_async_wait<kStages - 1>();            // this thread's pass-n copies are in
+            const int r = r0 + ro + q * P;
+            if (active && r < r1) {
+                const float4* su = s_stage + (size_t)(n % kStages) * 2 * kThreads + tid;
+                const float4 U = su[0], D = su[kThreads];
+                const float uu[NV] = {U.x, U.y, U.z, U.w};
+                const float dd[NV] = {D.x, D.y, D.z, D.w};
+                const float4 a = sa[r - r0];
+                const float rf = (float)r;
+                float out[NV], xo[NV];
+#pragma unroll
+                for (int e = 0; e < NV; ++e) {
+                    const float dcol = rf - cf[e];
+                    const float cq = dcol * dcol;
+                    const E32 el = elem32(uu[e], dd[e], cq, a, bq[e], p);
+                    out[e] = fmaf(p.trs, el.r, p.rho * dd[e]);
+                    if constexpr (CHECK) {
+                        float xb, zb;
+                        xz32(el, p, xb, zb);
+                        xo[e] = xb;
+                        const float mn = fminf(xb, zb);
+                        k32[0] = fmaf(el.r, el.r, k32[0]);
+                        k32[1] = fmaf(mn, mn, k32[1]);
+                        k32[2] = fmaf(xb, xb, k32[2]);
+                        k32[3] = fmaf(zb, zb, k32[3]);
+                        k32[4] = fmaf(cq, xb, k32[4]);
+                        xacc[e] += xb;
+                    }
+                    cacc[e] += out[e];
+                }
+                VecT<float>::st(dout + (size_t)r * S + c0, out);
+                s_row[(r - r0) * (NC + 1) + cg] = (out[0] + out[1]) + (out[2] + out[3]);
+                if constexpr (CHECK) s_xrow[(r - r0) * (NC + 1) + cg] = (xo[0] + xo[1]) + (xo[2] + xo[3]);
+            }
+        }
+        // tile epilogue: row and column sums as double-float pairs
+        if (active) {
+#pragma unroll
+            for (int e = 0; e < NV; ++e) {
+                s_col[ro * S + c0 + e] = cacc[e];
+                if constexpr (CHECK) s_xcol[ro * S + c0 + e] = xacc[e];
+            }
+        }
+        __syncthreads();
+        const size_t cbase = ((size_t)slab * nb + band) * S;
+        for (int c = tid; c < S; c += kThreads) {
+            DF a{0.f, 0.f}, x{0.f, 0.f};
+            for (int qq = 0; qq < P; ++qq) {
+                a = df_add(a, s_col[qq * S + c]);
+                if constexpr (CHECK) x = df_add(x, s_xcol[qq * S + c]);
+            }
+            I.cs32[cbase + c] = df_f(a);
+            if constexpr (CHECK) I.xcs_part[cbase + c] = df_val(x);
+        }
+        const int warp = tid >> 5, lane = tid & 31;
+        for (int rr = warp; rr < r1 - r0; rr += kThreads / 32) {
+            DF a{0.f, 0.f}, x{0.f, 0.f};
+            for (int c = lane; c < NC; c += 32) {
+                a = df_add(a, s_row[rr * (NC + 1) + c]);
+                if constexpr (CHECK) x = df_add(x, s_xrow[rr * (NC + 1) + c]);
+            }
+            a = warp_sum_df(a);
+            if constexpr (CHECK) x = warp_sum_df(x);
+            if (lane == 0) {
+                I.rs2[(size_t)slab * S + r0 + rr] = df_st(a);
+                if constexpr (CHECK) I.xrs[(size_t)slab * S + r0 + rr] = df_val(x);
+            }
+        }
+        if constexpr (CHECK) {
+            DF kd[kNK];
+#pragma unroll
+            for (int qq = 0; qq < kNK; ++qq) kd[qq] = DF{k32[qq], 0.f};
+            block_sum_df<kNK>(kd, s_red);
+            if (tid == 0) {
+                double* o = I.tile_kkt + ((size_t)slab * nb + band) * kNK;
+#pragma unroll
+                for (int qq = 0; qq < kNK; ++qq) o[qq] = df_val(kd[qq]);
+            }
+        }
+        ++ck;
+        do {
+            ct += G;
+            dc = tile_desc(W, ct, ntiles);
+        } while (ct < ntiles && dc.npass == 0);
+    }
+    cp_async_wait<0>();
 }
 
 // ---------------------------------------------------------- restart tiles --
@@ -919,7 +1359,7 @@ __device__ __forceinline__ void restart_tile(const HotInst& I, int slab, int ban
         // y0 <- y-bar: A^T y0 pieces of this tile's rows (and, for band 0, columns)
         const size_t o = (size_t)slab * 2 * S;
         auto set_anchor = [&](int idx) {
-            const double a0 = I.ab0[o + idx] + I.dab64[o + idx];
+            const double a0 = I.ab0[o + idx] + (F32 ? df_val(df_ld(I.dab2[o + idx])) : I.dab64[o + idx]);
             I.ab0[o + idx] = a0;
             if (I.ab0_32) {
                 const double hi = rint(a0 / I.h) * I.h;          // on the grid 2^-E
@@ -928,7 +1368,8 @@ __device__ __forceinline__ void restart_tile(const HotInst& I, int slab, int ban
         };
         for (int rr = threadIdx.x; rr < r1 - r0; rr += blockDim.x) {
             I.rs0[(size_t)slab * S + r0 + rr] = sum_f64_strided(s_row + rr * NC, NC, 1);
-            I.rs[(size_t)slab * S + r0 + rr] = 0.0;
+            if (F32) I.rs2[(size_t)slab * S + r0 + rr] = make_float2(0.f, 0.f);
+            else I.rs[(size_t)slab * S + r0 + rr] = 0.0;
             set_anchor(r0 + rr);
         }
         if (band == 0)
@@ -1181,17 +1622,46 @@ __global__ void k_block_end(const WorkDev* __restrict__ W) {
 
 // ------------------------------------------------------------- launchers --
 
-LaunchDims make_launch_dims(int device) {
+// SM count x resident CTAs per SM (at most cap) of one kernel at kThreads
+template <typename F>
+static int occ_grid(F kernel, int sms, size_t dyn_smem, int cap) {
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kThreads, dyn_smem) != cudaSuccess || per < 1)
+        per = 1;
+    return sms * (per < cap ? per : cap);
+}
+
+LaunchDims make_launch_dims(int device, int fp64) {
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     if (sms <= 0) sms = 1;
     LaunchDims d;
-    d.grid_tile = sms * 4;
-    d.grid_slab = sms * 4;
-    d.grid_vec = sms * 4;
+    if (fp64) {
+        d.grid_tile = occ_grid(k_sweep64, sms, 0, 8);
+        d.grid_tile_chk = d.grid_tile;
+        d.grid_rst = std::min(occ_grid(k_restart<double, 0>, sms, 0, 8), occ_grid(k_restart<double, 1>, sms, 0, 8));
+        d.grid_slab = occ_grid(k_alpha<true>, sms, 0, 4);
+        d.grid_vec = occ_grid(k_vec, sms, 0, 4);
+    } else {
+        d.grid_tile = occ_grid(k_sweep32<false>, sms, kStages * kStageBytes, 8);
+        d.grid_tile_chk = occ_grid(k_sweep32<true>, sms, kStages * kStageBytes, 8);
+        d.grid_rst = std::min(occ_grid(k_restart<float, 0>, sms, 0, 8), occ_grid(k_restart<float, 1>, sms, 0, 8));
+        d.grid_slab = occ_grid(k_alpha32<true>, sms, 0, 4);
+        d.grid_vec = occ_grid(k_vec32, sms, 0, 4);
+    }
     d.grid_k1 = sms * 2;
     d.grid_inst = sms * 2;
     return d;
+}
+
+int sweep_grid(int fp64) {
+    static int cache[2][64];                 // per precision and device ordinal; 0 = not yet queried
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return 0;
+    int& c = cache[fp64 ? 1 : 0][dev];
+    if (c == 0) c = make_launch_dims(dev, fp64).grid_tile;
+    return c;
 }
 
 void launch_init(const HotInst& I, double sigma0, cudaStream_t st) {
@@ -1207,34 +1677,39 @@ void launch_init(const HotInst& I, double sigma0, cudaStream_t st) {
 
 cudaError_t kernels_init(int device) {
     (void)device;
-    cudaError_t e = cudaFuncSetAttribute(k_sweep<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_sweep32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          kStages * kStageBytes);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_sweep<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(k_sweep32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  kStages * kStageBytes);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_marg, cudaFuncAttributeMaxDynamicSharedMemorySize, 7 * kMaxS * 8);
     return e;
 }
 
-void launch_solve_kernels(const WorkDev* w, const LaunchDims& ld, bool check, cudaStream_t st) {
-    k_vec<<<ld.grid_vec, kThreads, 0, st>>>(w);
-    k_marg<<<ld.grid_inst, kThreads, 7 * kMaxS * 8, st>>>(w);
-    if (check) k_alpha<true><<<ld.grid_slab, kThreads, 0, st>>>(w);
-    else k_alpha<false><<<ld.grid_slab, kThreads, 0, st>>>(w);
+void launch_solve_kernels(const WorkDev* w, const LaunchDims& ld, int fp64, int j, bool check, cudaStream_t st) {
+    if (fp64) {
+        k_vec<<<ld.grid_vec, kThreads, 0, st>>>(w);
+        k_marg<<<ld.grid_inst, kThreads, 7 * kMaxS * 8, st>>>(w);
+        if (check) k_alpha<true><<<ld.grid_slab, kThreads, 0, st>>>(w);
+        else k_alpha<false><<<ld.grid_slab, kThreads, 0, st>>>(w);
+    } else {
+        k_vec32<<<ld.grid_vec, kThreads, 0, st>>>(w);
+        if (check) k_alpha32<true><<<ld.grid_slab, kThreads, 0, st>>>(w, j);
+        else k_alpha32<false><<<ld.grid_slab, kThreads, 0, st>>>(w, j);
+    }
 }
 
 void launch_sweep(const WorkDev* w, const LaunchDims& ld, int fp64, int j, bool check, cudaStream_t st) {
     if (fp64) {
-        if (check) k_sweep<double, true><<<ld.grid_tile, kThreads, 0, st>>>(w, j);
-        else k_sweep<double, false><<<ld.grid_tile, kThreads, 0, st>>>(w, j);
+        k_sweep64<<<check ? ld.grid_tile_chk : ld.grid_tile, kThreads, 0, st>>>(w, j, check ? 1 : 0);
     } else {
-        if (check) k_sweep<float, true><<<ld.grid_tile, kThreads, kStages * kStageBytes, st>>>(w, j);
-        else k_sweep<float, false><<<ld.grid_tile, kThreads, kStages * kStageBytes, st>>>(w, j);
+        if (check) k_sweep32<true><<<ld.grid_tile_chk, kThreads, kStages * kStageBytes, st>>>(w, j);
+        else k_sweep32<false><<<ld.grid_tile, kThreads, kStages * kStageBytes, st>>>(w, j);
     }
 }
 
 void launch_iteration(const WorkDev* w, const LaunchDims& ld, int fp64, int j, bool check, cudaStream_t st) {
-    launch_solve_kernels(w, ld, check, st);
+    launch_solve_kernels(w, ld, fp64, j, check, st);
     launch_sweep(w, ld, fp64, j, check, st);
 }
 
@@ -1243,17 +1718,17 @@ void launch_block_end(const WorkDev* w, const LaunchDims& ld, int fp64, int K, d
     k_kkt1<<<ld.grid_k1, kThreads, 0, st>>>(w);
     k_check<<<ld.grid_inst, kThreads, 0, st>>>(w, K, a1, a2, a3);
     if (fp64) {
-        k_restart<double, 0><<<ld.grid_tile, kThreads, 0, st>>>(w);
+        k_restart<double, 0><<<ld.grid_rst, kThreads, 0, st>>>(w);
         k_restart_sigma<<<ld.grid_inst, kThreads, 0, st>>>(w);
-        k_restart<double, 1><<<ld.grid_tile, kThreads, 0, st>>>(w);
+        k_restart<double, 1><<<ld.grid_rst, kThreads, 0, st>>>(w);
         k_anchor<<<ld.grid_slab, kThreads, 0, st>>>(w);
-        k_restart<double, 2><<<ld.grid_tile, kThreads, 0, st>>>(w);
+        k_restart<double, 2><<<ld.grid_rst, kThreads, 0, st>>>(w);
     } else {
-        k_restart<float, 0><<<ld.grid_tile, kThreads, 0, st>>>(w);
+        k_restart<float, 0><<<ld.grid_rst, kThreads, 0, st>>>(w);
         k_restart_sigma<<<ld.grid_inst, kThreads, 0, st>>>(w);
-        k_restart<float, 1><<<ld.grid_tile, kThreads, 0, st>>>(w);
+        k_restart<float, 1><<<ld.grid_rst, kThreads, 0, st>>>(w);
         k_anchor<<<ld.grid_slab, kThreads, 0, st>>>(w);
-        k_restart<float, 2><<<ld.grid_tile, kThreads, 0, st>>>(w);
+        k_restart<float, 2><<<ld.grid_rst, kThreads, 0, st>>>(w);
     }
     k_block_end<<<ld.grid_inst, kThreads, 0, st>>>(w);
 }

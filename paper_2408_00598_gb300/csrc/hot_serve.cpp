@@ -55,7 +55,8 @@ struct ServeState {
 static size_t inst_bytes_estimate(int S, int fp64) {
     const size_t V = 2ull * S * S * S;
     const size_t big = 5 * (V * (fp64 ? 8 : 4) + 256);
-    const size_t nb = (S + tile_rows(S, fp64) - 1) / tile_rows(S, fp64);
+    const int tr = tile_rows(S, fp64, sweep_grid(fp64));
+    const size_t nb = (S + tr - 1) / tr;
     const size_t small = (size_t)S * S * (8 * 4 + 8 * 4 + 8 * 6 * nb + 8 * 2 + 16) + 1024 * 64;
     return big + small;
 }
