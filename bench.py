@@ -34,12 +34,15 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the FP32 sweep
-# (k_sweep<float,false>) on the 256^3 x 2 state, and the hash of the kernel
+# (k_sweep32<false>) on the 256^3 x 2 state, and the hash of the kernel
 # source it was taken on (traffic is reported only while the source matches).
 SWEEP_TRAFFIC = {"kernels_sha256": None, "bytes_per_launch": None}
 
-# iterations of Algorithm 2 (with the restart rule) to rel-KKT tol for the
-# default bench pair, measured with the device solver
+# iterations of Algorithm 2 (with the restart rule) that the FP64 oracle takes
+# to rel-KKT tol on the default bench pair (synthetic.make_pair("white", 256,
+# 1000)): oracle.hot.hot_solve(mu1, mu2, tol=1e-6) -> 450 iterations, 12
+# restarts, rel-KKT 9.1177e-7, 1269 s on one x86 core.  Used to extrapolate
+# the oracle's per-iteration time to a full solve.
 ITERS_PER_SOLVE = {(256, "white", 1e-6): 450}
 
 
@@ -279,7 +282,7 @@ def bench_solve(args, dist):
     total_ms = kt["sweep_ms"] + kt["sweep_check_ms"] + kt["solve_ms"] + kt["block_end_ms"]
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
-                "kernel": "k_sweep<float,false> (Steps 2-4 fused, non-check iterations)",
+                "kernel": "k_sweep32<false> (Steps 2-4 fused, non-check iterations)",
                 "bytes_per_launch": kt["sweep_bytes"], "avg_launch_us": round(sweep_s * 1e6, 2),
                 "share_of_solve_device_time": round(kt["sweep_ms"] / total_ms, 4) if total_ms > 0 else None,
                 "device_us_per_iteration": {
@@ -304,7 +307,7 @@ def bench_solve(args, dist):
            "roofline": roofline, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
            "clocks": clocks}
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
-        per_solve, desc = oracle_sample(mu1, mu2, iters)
+        per_solve, desc = oracle_sample(mu1, mu2, ITERS_PER_SOLVE.get((S, args.kind, args.tol), iters))
         out["cpu_baseline"] = {"value": round(1.0 / per_solve, 8), "unit": "solves/s", "cores": cpu_threads(),
                                "kind": "oracle", "sample": desc}
     ctx.close()
@@ -318,10 +321,9 @@ def bench_reference(args, dist):
         return None
     S = args.size
     mu1, mu2 = syn.make_pair(args.kind, S, 1000)
-    # iterations a solve of this pair takes: a property of the method on this
-    # input (the oracle and the device path follow the same trajectory);
-    # running the oracle to convergence at S = 256 would take about half an
-    # hour, so the measured count is a documented constant
+    # iterations the oracle takes to converge on this pair (one full oracle
+    # solve at S = 256 takes about 20 minutes, so the count is a documented
+    # constant measured with the oracle itself)
     iters = ITERS_PER_SOLVE.get((S, args.kind, args.tol), 1100)
     times = []
     desc = ""

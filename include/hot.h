@@ -68,6 +68,18 @@ extern "C" {
 #define HOT_SPACE_HOST    0
 #define HOT_SPACE_DEVICE  1
 
+/* Iteration (Step 4 of Algorithm 2).  HOT_METHOD_GADMM is the generalized
+   ADMM the paper compares against (Sec. IV-A): Step 4 replaced by
+   w^{k+1} = (1 - rho) w^k + rho w-bar^k; the restart rule and sigma update
+   apply unchanged. */
+#define HOT_METHOD_HALPERN 0
+#define HOT_METHOD_GADMM   1
+/* Stopping rule: the relative KKT residual eq. (kkt_res), or the absolute one
+   of Table VI (the same three terms without their normalisers).  Both are
+   measured on the scaled problem and both are reported. */
+#define HOT_STOP_RELATIVE  0
+#define HOT_STOP_ABSOLUTE  1
+
 typedef struct hot_ctx hot_ctx;
 
 /* ---- configuration (hot_config_default fills the defaults) -------------- */
@@ -85,7 +97,10 @@ typedef struct hot_config {
     int    max_queue;           /* queued requests before hot_submit returns HOT_EBUSY (0: 65536) */
     const char *autotune_cache; /* file caching tuned tile shapes; NULL: defaults, no file  */
     int    keep_batch_solutions;/* 1: hot_solve_batch keeps every final iterate (solution_id) */
-    int    reserved[7];
+    int    method;              /* HOT_METHOD_HALPERN (Algorithm 2, default) or HOT_METHOD_GADMM */
+    double relaxation;          /* rho of HOT_METHOD_GADMM, in (0, 2)                   (1.7) */
+    int    stop_rule;           /* HOT_STOP_RELATIVE (eq. kkt_res, default) or HOT_STOP_ABSOLUTE */
+    int    reserved[3];
 } hot_config;
 
 /* ---- result of one solve ------------------------------------------------ */
@@ -108,6 +123,7 @@ typedef struct hot_result {
     int    m, n;
     long long kernel_launches;  /* device kernels this call launched (early-exiting ones included) */
     long long blocks;           /* check blocks (K iterations each) launched                      */
+    double abs_kkt;             /* absolute KKT residual (Table VI) on the scaled problem          */
 } hot_result;
 
 /* Fill `cfg` with the defaults listed above.  Never fails. */

@@ -35,6 +35,17 @@ Readings where the paper is silent (Sec. IV-A gives only the stopping rule):
   on degenerate inputs; the geometric mean damps it.
 * The iteration cap is tested at check iterations: the solve stops at the first
   check iteration whose total count reaches max_iter.
+
+Variants (Sec. IV-A and App. D):
+
+* method="gadmm": the generalized ADMM the paper compares against, Algorithm 2
+  with Step 4 replaced by w^{k+1} = (1 - rho) w^k + rho w-bar^k (rho = 1.7;
+  rho = 1 is plain ADMM, w^{k+1} = w-bar^k).  Reading: the restart rule and
+  the sigma update above apply unchanged (a restart sets the iterate to w-bar).
+* stop="absolute": the absolute KKT residual of Table VI, the three terms of
+  eq. (kkt_res) without their normalisers, max{||A^T y + z - c||,
+  ||min(x, z)||, ||Ax - b||}.  Reading: measured, like the relative one, on the
+  scaled problem that is solved.
 """
 from dataclasses import dataclass, field
 import math
@@ -54,6 +65,9 @@ class HotParams:
     restart_necessary: float = 0.8
     restart_long: float = 0.2
     scale_cost: bool = True
+    method: str = "hot"            # "hot" (Halpern Step 4) or "gadmm" (generalized ADMM)
+    relax: float = 1.7             # rho of the generalized ADMM
+    stop: str = "relative"         # "relative" (eq. kkt_res) or "absolute" (Table VI)
 
 
 @dataclass
@@ -62,6 +76,7 @@ class HotResult:
     dual_value: float              # <b, y-bar> (unscaled)
     rel_kkt: float
     parts: tuple                   # (dual, complementarity, primal) terms of eq. (kkt_res)
+    abs_kkt: float                 # max of the same three terms without normalisers
     iters: int
     restarts: int
     converged: bool
@@ -81,6 +96,11 @@ def kkt_residual(A, b, c, x, y, z):
     comp = np.linalg.norm(np.minimum(x, z)) / (1.0 + np.linalg.norm(x) + np.linalg.norm(z))
     primal = np.linalg.norm(A @ x - b) / (1.0 + np.linalg.norm(b))
     return max(dual, comp, primal), (dual, comp, primal)
+
+
+def kkt_absolute(A, b, c, x, y, z):
+    """Absolute KKT residual (Table VI): max{||A^T y + z - c||, ||min(x, z)||, ||Ax - b||}."""
+    return max(np.linalg.norm(A.T @ y + z - c), np.linalg.norm(np.minimum(x, z)), np.linalg.norm(A @ x - b))
 
 
 def kkt_mapping(A, b, c, x, y, z):
@@ -149,7 +169,8 @@ def hot_solve(mu1, mu2, tol=1e-6, max_iter=100000, params=None, xs=None, ys=None
             err, parts = kkt_residual(A, b, c, x_bar, y_bar, z_bar)
             err = float(err)
             parts = tuple(float(q) for q in parts)
-            done = bool(err <= tol)
+            aerr = float(kkt_absolute(A, b, c, x_bar, y_bar, z_bar))
+            done = bool((aerr if p.stop == "absolute" else err) <= tol)
             capped = total >= max_iter
             restart = False
             if not done and not capped and p.restart:
@@ -163,7 +184,8 @@ def hot_solve(mu1, mu2, tol=1e-6, max_iter=100000, params=None, xs=None, ys=None
             trace.append((total, err, restart, sigma))
             if done or capped:
                 return HotResult(ot_value=scale * float(c @ x_bar), dual_value=scale * float(b @ y_bar),
-                                 rel_kkt=err, parts=parts, iters=total, restarts=restarts, converged=done,
+                                 rel_kkt=err, parts=parts, abs_kkt=aerr, iters=total, restarts=restarts,
+                                 converged=done,
                                  sigma=sigma, cost_scale=scale, x=x_bar, y=scale * y_bar, z=scale * z_bar,
                                  trace=trace)
             if restart:
@@ -180,10 +202,17 @@ def hot_solve(mu1, mu2, tol=1e-6, max_iter=100000, params=None, xs=None, ys=None
                 restarts += 1
                 continue
 
-        # Step 4 (Halpern, step size 1/(k+2))
-        x = x0 / (k + 2) + (k + 1) / (k + 2) * (2.0 * x_bar - x)
-        z = z0 / (k + 2) + (k + 1) / (k + 2) * (2.0 * z_bar - z)
-        y = y0 / (k + 2) + (k + 1) / (k + 2) * (2.0 * y_bar - y)
+        if p.method == "gadmm":
+            # Step 4 of the generalized ADMM: w^{k+1} = (1 - rho) w^k + rho w-bar^k
+            rho = p.relax
+            x = (1.0 - rho) * x + rho * x_bar
+            z = (1.0 - rho) * z + rho * z_bar
+            y = (1.0 - rho) * y + rho * y_bar
+        else:
+            # Step 4 (Halpern, step size 1/(k+2))
+            x = x0 / (k + 2) + (k + 1) / (k + 2) * (2.0 * x_bar - x)
+            z = z0 / (k + 2) + (k + 1) / (k + 2) * (2.0 * z_bar - z)
+            y = y0 / (k + 2) + (k + 1) / (k + 2) * (2.0 * y_bar - y)
         k += 1
 
 

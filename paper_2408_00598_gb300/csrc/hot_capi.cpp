@@ -51,6 +51,9 @@ void hot_config_default(hot_config* cfg) {
     cfg->max_batch = 1024;
     cfg->max_queue = 65536;
     cfg->autotune_cache = nullptr;
+    cfg->method = HOT_METHOD_HALPERN;
+    cfg->relaxation = 1.7;
+    cfg->stop_rule = HOT_STOP_RELATIVE;
 }
 
 const char* hot_status_string(int status) {
@@ -95,6 +98,18 @@ int hot_create(hot_ctx** out, const hot_config* cfg) {
     }
     if (!(c.restart_sufficient > 0 && c.restart_necessary > 0 && c.restart_long > 0)) {
         set_error("restart thresholds must be positive");
+        return HOT_EINVAL;
+    }
+    if (c.method != HOT_METHOD_HALPERN && c.method != HOT_METHOD_GADMM) {
+        set_error("method must be HOT_METHOD_HALPERN or HOT_METHOD_GADMM");
+        return HOT_EINVAL;
+    }
+    if (c.method == HOT_METHOD_GADMM && !(c.relaxation > 0.0 && c.relaxation < 2.0)) {
+        set_error("relaxation must be in (0, 2)");
+        return HOT_EINVAL;
+    }
+    if (c.stop_rule != HOT_STOP_RELATIVE && c.stop_rule != HOT_STOP_ABSOLUTE) {
+        set_error("stop_rule must be HOT_STOP_RELATIVE or HOT_STOP_ABSOLUTE");
         return HOT_EINVAL;
     }
     int ndev = 0;

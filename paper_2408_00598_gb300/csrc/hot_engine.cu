@@ -27,24 +27,14 @@ int tile_rows(int S, int fp64, int grid) {
         if (S >= 96) tr = std::min(tr, 32);
         return std::max(tr, 1);
     }
-    // TR * S <= 16384 (row-partial buffer).  Among TR = S, S/2, S/4, ... with
-    // at least 4 passes per tile where possible, take the one whose tile count
-    // 2S * ceil(S/TR) spreads best over the grid's resident CTAs (the last
-    // round of a persistent grid-stride loop is the tail), larger TR on ties.
-    int best = std::min(S, 16384 / S);
-    if (grid <= 0) return best;
-    double best_imb = 1e30;
-    for (int tr = std::min(S, 16384 / S); tr >= 1; tr /= 2) {
-        if ((long long)tr * S < 4096 && tr != std::min(S, 16384 / S)) break;
-        const long long T = 2LL * S * ((S + tr - 1) / tr);
-        const long long rounds = (T + grid - 1) / grid;
-        const double imb = (double)(rounds * grid) / (double)T;
-        if (imb < best_imb * 0.99) {
-            best_imb = imb;
-            best = tr;
-        }
-    }
-    return best;
+    // TR * S <= 16384 (row-partial buffer).  Tiles as tall as that allows
+    // (the per-tile set-up and reductions cost more than a ragged last round
+    // of the persistent grid), halved while a slab-set this small leaves the
+    // grid's CTAs under two tiles each and a tile keeps at least 4 passes
+    int tr = std::min(S, 16384 / S);
+    if (grid > 0)
+        while (2LL * S * ((S + tr - 1) / tr) < 2LL * grid && (long long)(tr / 2) * S >= 4096) tr /= 2;
+    return tr;
 }
 
 int validate_pair(const double* mu, const double* nu, int m, int n, int space, int fp64, PairHost& out) {
@@ -104,7 +94,7 @@ int validate_pair(const double* mu, const double* nu, int m, int n, int space, i
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-int inst_create(const PairHost& p, int fp64, double sigma0_cfg, double tol, long long max_iter, int tr_override,
+int inst_create(const PairHost& p, int fp64, const hot_config& cfg, double tol, long long max_iter, int tr_override,
                 cudaStream_t st, Inst** out) {
     *out = nullptr;
     std::unique_ptr<Inst> I(new Inst());
@@ -153,7 +143,6 @@ int inst_create(const PairHost& p, int fp64, double sigma0_cfg, double tol, long
     const size_t F2 = fp64 ? 0 : sizeof(float2);   // double-float arrays of FP32 mode
     const size_t o_rs2 = take(2 * SS * F2);
     const size_t o_rs02 = take(2 * SS * F2);
-    const size_t o_R1a2 = take(2 * SS * F2);
     const size_t o_K2 = take(2 * SS * F2);
     const size_t o_vec2 = take(4 * (size_t)S * F2);
     const size_t o_dab2 = take(4 * SS * F2);
@@ -163,6 +152,7 @@ int inst_create(const PairHost& p, int fp64, double sigma0_cfg, double tol, long
     const size_t o_cm2 = take(S * F2);
     const size_t o_rm2 = take(S * F2);
     const size_t o_p32 = take(sizeof(P32));
+    const size_t o_cyc = take(sizeof(CycleK));
     const size_t o_mu1 = take(SS * 8);
     const size_t o_mu2 = take(SS * 8);
     const size_t o_cm = take(S * 8);
@@ -189,6 +179,9 @@ int inst_create(const PairHost& p, int fp64, double sigma0_cfg, double tol, long
     d.nb = I->nb;
     d.n_k1 = I->n_k1;
     d.fp64 = fp64;
+    d.gadmm = cfg.method == HOT_METHOD_GADMM ? 1 : 0;
+    d.stop_abs = cfg.stop_rule == HOT_STOP_ABSOLUTE ? 1 : 0;
+    d.relax = cfg.relaxation;
     // power-of-two cost scale: smallest 2^E >= max c = (S-1)^2
     const double cmax = (double)(S - 1) * (S - 1);
     int E = 0;
@@ -242,7 +235,6 @@ int inst_create(const PairHost& p, int fp64, double sigma0_cfg, double tol, long
     d.dobj_part = (double*)(sm + o_dp);
     d.rs2 = fp64 ? nullptr : (float2*)(sm + o_rs2);
     d.rs02 = fp64 ? nullptr : (float2*)(sm + o_rs02);
-    d.R1a2 = fp64 ? nullptr : (float2*)(sm + o_R1a2);
     d.K2 = fp64 ? nullptr : (float2*)(sm + o_K2);
     d.vec2 = fp64 ? nullptr : (float2*)(sm + o_vec2);
     d.dab2 = fp64 ? nullptr : (float2*)(sm + o_dab2);
@@ -251,6 +243,7 @@ int inst_create(const PairHost& p, int fp64, double sigma0_cfg, double tol, long
     d.cm2 = fp64 ? nullptr : (float2*)(sm + o_cm2);
     d.rm2 = fp64 ? nullptr : (float2*)(sm + o_rm2);
     d.p32 = (P32*)(sm + o_p32);
+    d.cyc = (CycleK*)(sm + o_cyc);
     d.ctl = (HotCtl*)(sm + o_ctl);
 
     // host-side constants uploaded once
@@ -261,7 +254,7 @@ int inst_create(const PairHost& p, int fp64, double sigma0_cfg, double tol, long
             rm[i] += p.mu2[(size_t)i * S + j];
         }
     HotCtl c{};
-    c.sigma = sigma0_cfg > 0.0 ? sigma0_cfg : d.norm_b / d.norm_c;
+    c.sigma = cfg.sigma0 > 0.0 ? cfg.sigma0 : d.norm_b / d.norm_c;
     c.tol = tol;
     c.r0 = -1.0;
     c.rprev = -1.0;
@@ -445,6 +438,7 @@ void fill_result(const Inst* I, hot_result* r) {
     r->rel_dual = c.rel_dual;
     r->rel_comp = c.rel_comp;
     r->rel_primal = c.rel_primal;
+    r->abs_kkt = c.abs_kkt;
     r->sigma = c.sigma;
     r->cost_scale = I->cost_scale;
     r->iters = c.total;
@@ -485,7 +479,7 @@ int run_solve(Ctx* ctx, const std::vector<PairHost>& pairs, double tol, long lon
     };
     for (const PairHost& p : pairs) {
         Inst* I = nullptr;
-        int rc = inst_create(p, fp64, ctx->cfg.sigma0, tol, max_iter, ctx->tile_override, st, &I);
+        int rc = inst_create(p, fp64, ctx->cfg, tol, max_iter, ctx->tile_override, st, &I);
         if (rc != HOT_OK) {
             cleanup();
             return rc;

@@ -57,7 +57,7 @@ int validate_pair(const double* mu, const double* nu, int m, int n, int space, i
 int tile_rows(int S, int fp64, int grid);
 
 // Allocate and initialise an instance on stream `st` (inputs already validated).
-int inst_create(const PairHost& p, int fp64, double sigma0_cfg, double tol, long long max_iter, int tr_override,
+int inst_create(const PairHost& p, int fp64, const hot_config& cfg, double tol, long long max_iter, int tr_override,
                 cudaStream_t st, Inst** out);
 void inst_destroy(Inst* I, cudaStream_t st);
 

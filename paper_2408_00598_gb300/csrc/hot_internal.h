@@ -52,6 +52,7 @@ struct HotCtl {
     double tol;            // relative KKT tolerance
     double r0, rprev;      // restart residuals of the current cycle (< 0: unset)
     double rel_kkt, rel_dual, rel_comp, rel_primal;
+    double abs_kkt;        // max of the three KKT terms without normalisers
     double pobj, dobj;     // unscaled primal <c,x-bar> and dual <b,y-bar>
     double dx2, dz2;       // ||x-bar - x_r||^2, ||z-bar - z_r||^2 at the last restart
     double sigma_old;      // sigma of the check iteration that triggered the last restart
@@ -78,6 +79,15 @@ struct P32 {
     float pad[3];
 };
 
+// Prop. 3 constants that change only with sigma, i.e. once per cycle, as
+// double-float pairs (FP32 mode): 1/sigma, 1/n, 1/m, 1/(m+n), 1/m + 1/n,
+// 1/w, the last diagonal entry dl of W-hat, the sum of its diagonal,
+// 1/(sigma m), 1/(sigma n), and mu2(m,n) minus the anchor's column total
+// there (the dropped row of eq. 7).  Written by k_anchor, read by k_alpha32.
+struct CycleK {
+    float2 is, in, im, imn, imin, iw, dl, sumd, isim, isin, mk, pad;
+};
+
 // Per-instance descriptor (read-only while a block runs).
 struct HotInst {
     int S;                 // grid side
@@ -86,6 +96,9 @@ struct HotInst {
     int nb;                // bands (tiles) per slab = ceil(S / TR)
     int n_k1;              // chunks of the A x - b kernel
     int fp64;              // 1: FP64 state, 0: FP32 anchor + delta
+    int gadmm;             // 1: Step 4 of the generalized ADMM instead of Halpern's
+    int stop_abs;          // 1: stop on the absolute KKT residual
+    double relax;          // rho of the generalized ADMM
     double h;              // 2^-E
     double norm_b;         // ||b||
     double norm_c;         // ||c|| of the scaled problem
@@ -121,9 +134,8 @@ struct HotInst {
     // FP32 bulk mode only (null in FP64 mode): the per-iteration Prop. 3
     // arithmetic runs on double-float pairs (hi, lo) of FP32 values, whose
     // sum carries about 48 significant bits, instead of FP64
-    float2* rs2;           // [2S][S] row sums of the delta (last sweep)
+    float2* rs2;           // [2S][S] row sums of u + d (last sweep; = rs02 after a restart)
     float2* rs02;          // [2S][S] row sums of u (fixed within a cycle)
-    float2* R1a2;          // [2S][S] R1a
     float2* K2;            // [2S][S] (mu - colsum u)/(sigma m) per slab column (/(sigma n) for f2), fixed within a cycle
     float2* vec2;          // [4][S] T1, T2, P1, P2 of u + d
     float2* dab2;          // [2S][2S] pieces of A^T(y-bar - y0)
@@ -132,6 +144,7 @@ struct HotInst {
     float2* cm2;           // [S] colmu1 as pairs
     float2* rm2;           // [S] rowmu2 as pairs
     P32* p32;              // element constants of the current iteration
+    struct CycleK* cyc;    // Prop. 3 constants of the current cycle
     HotCtl* ctl;
 };
 

@@ -197,22 +197,26 @@ struct P64 {
     double is, s, rho, trs, h;
 };
 
-__device__ __forceinline__ P32 make_p32(double sigma, int k, double h) {
+// Step 4 on the delta d = v - v0 of v = x + sigma z, with v-bar - v = sigma r:
+//   Halpern (Algorithm 2): d' = rho_k d + 2 rho_k sigma r, rho_k = (k+1)/(k+2);
+//   generalized ADMM:      d' = d + rho sigma r          (w' = (1-rho) w + rho w-bar).
+// Both are d' = rho d + trs r.
+__device__ __forceinline__ P32 make_p32(double sigma, int k, double h, int gadmm = 0, double relax = 1.0) {
     P32 p{};
     p.sih = (float)(1.0 / sigma);
     p.sf = (float)sigma;
-    const double rho = (k + 1.0) / (k + 2.0);
+    const double rho = gadmm ? 1.0 : (k + 1.0) / (k + 2.0);
     p.rho = (float)rho;
-    p.trs = (float)(2.0 * rho * sigma);
+    p.trs = (float)(gadmm ? relax * sigma : 2.0 * rho * sigma);
     p.h = (float)h;
     return p;
 }
-__device__ __forceinline__ P64 make_p64(double sigma, int k, double h) {
+__device__ __forceinline__ P64 make_p64(double sigma, int k, double h, int gadmm = 0, double relax = 1.0) {
     P64 p;
     p.is = 1.0 / sigma;
     p.s = sigma;
-    p.rho = (k + 1.0) / (k + 2.0);
-    p.trs = 2.0 * p.rho * sigma;
+    p.rho = gadmm ? 1.0 : (k + 1.0) / (k + 2.0);
+    p.trs = gadmm ? relax * sigma : 2.0 * p.rho * sigma;
     p.h = h;
     return p;
 }
@@ -300,6 +304,10 @@ __device__ __forceinline__ void cp_async_wait() {
 // (one float4 of u and one of the delta per thread).
 constexpr int kStages = 4;
 constexpr int kStageBytes = 2 * kThreads * 16;
+// k_sweep32 dynamic shared memory: the pass ring, plus on check iterations
+// the x-bar row partials, column partials and per-warp row pairs
+constexpr int kSweepSmem = kStages * kStageBytes;
+constexpr int kSweepSmemChk = kSweepSmem + (kRowSmemBytes + 256 * 4) + kThreads * 4 * 4 + (kThreads / 32) * kMaxTR * 8;
 
 struct TileCtx {
     int inst, slab, band;
@@ -583,18 +591,14 @@ __global__ void __launch_bounds__(kThreads) k_vec32(const WorkDev* __restrict__ 
             const int S = I.S;
             const int q8 = (S + 7) / 8, q32 = (S + 31) / 32;
             const int item = s_t[1];
-            const float2* __restrict__ rs = I.rs2;
-            const float2* __restrict__ r0 = I.rs02;
+            const float2* __restrict__ rs = I.rs2;           // row sums of u + d
             if (item < 2 * q8) {
                 const int which = item / q8;                 // 0: T1 (f1 slab totals), 1: T2
                 const int q = (item % q8) * 8 + warp;
                 if (q < S) {                                  // warp-uniform
                     const size_t row = (size_t)(which * S + q) * S;
                     DF acc{0.f, 0.f};
-                    for (int t = lane; t < S; t += 32) {
-                        acc = df_add(acc, df_ld(r0[row + t]));
-                        acc = df_add(acc, df_ld(rs[row + t]));
-                    }
+                    for (int t = lane; t < S; t += 32) acc = df_add(acc, df_ld(rs[row + t]));
                     acc = warp_sum_df(acc);
                     if (lane == 0) I.vec2[which * S + q] = df_st(acc);
                 }
@@ -604,11 +608,7 @@ __global__ void __launch_bounds__(kThreads) k_vec32(const WorkDev* __restrict__ 
                 const int q = (it2 % q32) * 32 + lane;
                 DF acc{0.f, 0.f};
                 if (q < S)
-                    for (int t = warp; t < S; t += kW) {
-                        const size_t idx = (size_t)(which * S + t) * S + q;
-                        acc = df_add(acc, df_ld(r0[idx]));
-                        acc = df_add(acc, df_ld(rs[idx]));
-                    }
+                    for (int t = warp; t < S; t += kW) acc = df_add(acc, df_ld(rs[(size_t)(which * S + t) * S + q]));
                 s_p[threadIdx.x] = df_st(acc);
                 __syncthreads();
                 if (warp == 0 && q < S) {
@@ -640,26 +640,21 @@ struct AlphaK {
 __device__ void alpha32_stage(const HotInst& I, float2 (*sq)[kMaxS], float2* s_red, AlphaK& K) {
     const int S = I.S, nb = I.nb;
     if (threadIdx.x == 0) {
-        const double m = S, n = S;
-        const double is = 1.0 / I.ctl->sigma;
-        const double dl = (1.0 - 1.0 / n) / (m + 1.0);
-        const double iw = 1.0 / (1.0 / m - dl);       // 1/w, w = 1/m - (1-1/n)/(m+1)
+        const CycleK& C = *I.cyc;
+        K.is = df_ld(C.is);
+        K.in = df_ld(C.in);
+        K.im = df_ld(C.im);
+        K.imn = df_ld(C.imn);
+        K.imin = df_ld(C.imin);
+        K.iw = df_ld(C.iw);
+        K.dl = df_ld(C.dl);
+        K.sumd = df_ld(C.sumd);
+        K.isim = df_ld(C.isim);
+        K.isin = df_ld(C.isin);
         // the dropped (m, n) row of eq. (7): column S-1 of the last f2 slab
         float kd = 0.f;
         for (int b = 0; b < nb; ++b) kd += I.cs32[((size_t)(2 * S - 1) * nb + b) * S + (S - 1)];
-        const double kl = I.kapa[(size_t)(2 * S - 1) * S + (S - 1)] + (double)kd;
-        const double mu_last = I.mu2[(size_t)(S - 1) * S + (S - 1)];
-        K.is = df_from(is);
-        K.in = df_from(1.0 / n);
-        K.im = df_from(1.0 / m);
-        K.imn = df_from(1.0 / (m + n));
-        K.imin = df_from(1.0 / m + 1.0 / n);
-        K.iw = df_from(iw);
-        K.dl = df_from(dl);
-        K.sumd = df_from((S - 1) / m + dl);
-        K.isim = df_from(is / m);
-        K.isin = df_from(is / n);
-        K.fix = df_from((mu_last - kl) * is);
+        K.fix = df_mul(df_add(df_ld(C.mk), -kd), K.is);
     }
     __syncthreads();
     const DF is = K.is, fix = K.fix, im = K.im, dl = K.dl;
@@ -747,10 +742,9 @@ __global__ void __launch_bounds__(kThreads) k_alpha32(const WorkDev* __restrict_
         }
         const int slab = s_t[1];
         const int S = I.S, nb = I.nb;
-        if (slab == 0 && threadIdx.x == 0) *I.p32 = make_p32(I.ctl->sigma, I.ctl->k + j, I.h);
+        if (slab == 0 && threadIdx.x == 0) *I.p32 = make_p32(I.ctl->sigma, I.ctl->k + j, I.h, I.gadmm, I.relax);
         const DF is = K.is, imn = K.imn;
-        const float2* __restrict__ rs = I.rs2;
-        const float2* __restrict__ R1a = I.R1a2 + (size_t)slab * S;
+        const float2* __restrict__ rs = I.rs2;             // row sums of u + d
         const float2* __restrict__ K2 = I.K2 + (size_t)slab * S;
         const size_t o = (size_t)slab * 2 * S;
         const float grid = (float)(1.0 / I.h), igrid = (float)I.h;
@@ -779,8 +773,8 @@ __global__ void __launch_bounds__(kThreads) k_alpha32(const WorkDev* __restrict_
             const int j = slab;
             const DF colj = df_ld(sq[0][j]);
             for (int k = threadIdx.x; k < S; k += blockDim.x) {
-                const DF dr = df_sub(df_ld(rs[(size_t)j * S + k]), df_ld(rs[(size_t)(S + k) * S + j]));
-                const DF R1 = df_sub(df_ld(R1a[k]), df_mul(dr, is));
+                // R1(k, j) = -(rowsum f1 slab j - rowsum f2 slab k)/sigma
+                const DF R1 = df_mul(df_sub(df_ld(rs[(size_t)(S + k) * S + j]), df_ld(rs[(size_t)j * S + k])), is);
                 put(k, df_mul(df_add(df_add(R1, colj), df_ld(sq[1][k])), imn));     // y1(k, j)
             }
             const DF sy_im = df_mul(df_ld(sq[2][j]), K.im);
@@ -794,8 +788,7 @@ __global__ void __launch_bounds__(kThreads) k_alpha32(const WorkDev* __restrict_
             const int k = slab - S;
             const DF rowk = df_ld(sq[1][k]);
             for (int j = threadIdx.x; j < S; j += blockDim.x) {
-                const DF dr = df_sub(df_ld(rs[(size_t)j * S + k]), df_ld(rs[(size_t)(S + k) * S + j]));
-                const DF R1 = df_sub(df_ld(R1a[j]), df_mul(dr, is));
+                const DF R1 = df_mul(df_sub(df_ld(rs[(size_t)(S + k) * S + j]), df_ld(rs[(size_t)j * S + k])), is);
                 put(j, df_neg(df_mul(df_add(df_add(R1, df_ld(sq[0][j])), rowk), imn)));   // -y1(k, j)
             }
             const DF sp_in = df_mul(df_ld(sq[3][k]), K.in);
@@ -829,20 +822,38 @@ __global__ void __launch_bounds__(kThreads) k_alpha32(const WorkDev* __restrict_
 __device__ __forceinline__ void anchor_slab(const HotInst& I, int slab, double sigma) {
     const int S = I.S, nb = I.nb;
     const double is = 1.0 / sigma;
+    if (!I.fp64 && slab == 0 && threadIdx.x == 0) {
+        const double m = S, n = S;
+        const double dl = (1.0 - 1.0 / n) / (m + 1.0);
+        CycleK& K = *I.cyc;
+        K.is = df_st(df_from(is));
+        K.in = df_st(df_from(1.0 / n));
+        K.im = df_st(df_from(1.0 / m));
+        K.imn = df_st(df_from(1.0 / (m + n)));
+        K.imin = df_st(df_from(1.0 / m + 1.0 / n));
+        K.iw = df_st(df_from(1.0 / (1.0 / m - dl)));       // 1/w, w = 1/m - (1-1/n)/(m+1)
+        K.dl = df_st(df_from(dl));
+        K.sumd = df_st(df_from((S - 1) / m + dl));
+        K.isim = df_st(df_from(is / m));
+        K.isin = df_st(df_from(is / n));
+    }
     for (int q = threadIdx.x; q < S; q += blockDim.x) {
         // f1 slab j: rows k, R1(k, j); f2 slab k: rows j, R1(k, j)
         const int j = slab < S ? slab : q;
         const int k = slab < S ? q : slab - S;
-        const double r1a = -(I.rs0[(size_t)j * S + k] - I.rs0[(size_t)(S + k) * S + j]) * is;
-        I.R1a[(size_t)slab * S + q] = r1a;
+        I.R1a[(size_t)slab * S + q] = -(I.rs0[(size_t)j * S + k] - I.rs0[(size_t)(S + k) * S + j]) * is;
         double kap = 0.0;
         for (int b = 0; b < nb; ++b) kap += I.cs0_part[((size_t)slab * nb + b) * S + q];
         I.kapa[(size_t)slab * S + q] = kap;
         if (!I.fp64) {
-            // pairs for the FP32-mode solve; K2 is the sigma-scaled anchor part
+            // pairs for the FP32-mode solve: the row sums of u (also those of
+            // u + d, d = 0 at the anchor); K2 is the sigma-scaled anchor part
             // of y2 (f1 slab j, column i) resp. y3 (f2 slab k, column l)
-            I.rs02[(size_t)slab * S + q] = df_st(df_from(I.rs0[(size_t)slab * S + q]));
-            I.R1a2[(size_t)slab * S + q] = df_st(df_from(r1a));
+            const float2 r0 = df_st(df_from(I.rs0[(size_t)slab * S + q]));
+            I.rs02[(size_t)slab * S + q] = r0;
+            I.rs2[(size_t)slab * S + q] = r0;
+            if (slab == 2 * S - 1 && q == S - 1)
+                I.cyc->mk = df_st(df_from(I.mu2[(size_t)(S - 1) * S + (S - 1)] - kap));
             double k2;
             if (slab < S) k2 = (I.mu1[(size_t)q * S + slab] - kap) * is / S;
             else if (slab == 2 * S - 1 && q == S - 1) k2 = 0.0;
@@ -856,6 +867,12 @@ __global__ void __launch_bounds__(kThreads) k_anchor(const WorkDev* __restrict__
     __shared__ int s_t[4];
     const int ninst = W->ninst;
     const int nslab = W->pre_slab[ninst];
+    int any = 0;
+    for (int i = threadIdx.x; i < ninst; i += blockDim.x) {
+        const HotCtl* C = W->inst[i].ctl;
+        any |= (C->status == ST_RUNNING && C->restart_pending != 0);
+    }
+    if (!__syncthreads_or(any)) return;
     for (int t = blockIdx.x; t < nslab; t += gridDim.x) {
         if (threadIdx.x == 0) {
             const int i = find_inst(W->pre_slab, ninst, t);
@@ -907,7 +924,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep64(const WorkDev* __restri
         const double* __restrict__ u = (const double*)I.u + off;
         const double* __restrict__ din = (const double*)((j & 1) ? I.d1 : I.d0) + off;
         double* __restrict__ dout = (double*)((j & 1) ? I.d0 : I.d1) + off;
-        if (threadIdx.x == 0) s_p64 = make_p64(I.ctl->sigma, I.ctl->k + j, I.h);
+        if (threadIdx.x == 0) s_p64 = make_p64(I.ctl->sigma, I.ctl->k + j, I.h, I.gadmm, I.relax);
         __syncthreads();
         const int c0 = cg * NV;
         double cacc[NV], xacc[NV];
@@ -993,13 +1010,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep64(const WorkDev* __restri
 // of u and one of the delta) through a kStages-deep cp.async ring that is not
 // drained between tiles, so the next tile's loads are in flight while the
 // current tile's row and column sums are reduced.  The rows' alpha pieces
-// travel in the group of each tile's first pass into a ring of their own.
+// travel in the group of each tile's first pass into a ring of their own, and
+// thread 0 leaves each tile's descriptor in a third ring for the compute side.
+//
+// The scaled cost is separable, h (r - c)^2 = h r^2 + h c^2 - 2 h r c, so the
+// grid part of the reduced cost is Gh = (A_r + B_c) - 2 h r c with
+// A_r = h r^2 - alpha_hi (per row) and B_c = h c^2 - beta_hi (per column):
+// every term is an integer multiple of 2^-E, so Gh is exact in FP32 as before.
 struct TileD {
     int inst, slab, band, S, NC, P, r0, r1, npass;
 };
 
-// Every thread resolves tiles itself (no barrier); npass = 0 marks a tile of
-// an instance that is not running, or t past the end.
+// Resolve tile t; npass = 0 marks a tile of an instance that is not running,
+// or t past the end.
 __device__ __forceinline__ TileD tile_desc(const WorkDev* __restrict__ W, int t, int ntiles) {
     TileD d{};
     if (t >= ntiles) return d;
@@ -1009,7 +1032,7 @@ __device__ __forceinline__ TileD tile_desc(const WorkDev* __restrict__ W, int t,
     d.inst = i;
     d.S = I.S;
     d.slab = loc / I.nb;
-    d.band = loc % I.nb;
+    d.band = loc - d.slab * I.nb;
     d.NC = I.S / 4;
     d.P = kThreads / d.NC;
     d.r0 = d.band * I.TR;
@@ -1021,27 +1044,34 @@ __device__ __forceinline__ TileD tile_desc(const WorkDev* __restrict__ W, int t,
 template <bool CHECK>
 __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkDev* __restrict__ W, int j) {
     constexpr int NV = 4;
+    constexpr int kW = kThreads / 32;
     constexpr int kRowN = kRowSmemBytes / sizeof(float) + 256;
     __shared__ __align__(16) float s_row[kRowN];
     __shared__ __align__(16) float s_col[kThreads * NV];
-    __shared__ __align__(16) float s_xrow[CHECK ? kRowN : 1];
-    __shared__ __align__(16) float s_xcol[CHECK ? kThreads * NV : 1];
     __shared__ __align__(16) float4 s_alpha[kStages][kMaxTR];
+    __shared__ __align__(16) float2 s_rdf[kW][kMaxTR];            // per-warp row partial pairs
+    __shared__ TileD s_td[kStages];
     __shared__ float2 s_red[kNK * 32];
-    extern __shared__ float4 s_stage[];          // [kStages][2][kThreads]
+    // dynamic: the pass ring [kStages][2][kThreads] float4, then (check
+    // iterations) the x-bar row and column partials
+    extern __shared__ float4 s_stage[];
+    float* s_xrow = reinterpret_cast<float*>(s_stage + kStages * 2 * kThreads);
+    float* s_xcol = s_xrow + kRowN;
+    float2 (*s_xdf)[kMaxTR] = reinterpret_cast<float2 (*)[kMaxTR]>(s_xcol + kThreads * NV);
     const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
     const int G = gridDim.x;
     const int ntiles = W->pre_tile[W->ninst];
 
-    // issue cursor: tile it, its next pass iq, tiles started ik (alpha ring);
-    // per tile the thread's source pointers and row offset are formed once
+    // ---- issue side: every thread walks the same tile sequence
     struct Cur {
-        const float* u;
-        const float* d;
+        const float* u;            // this thread's source of the next pass (u)
+        const float* d;            // and of the delta
         const float4* a;           // alpha pieces of the tile's rows
         int step;                  // P rows, in floats
-        int ro, P, nr, npass;      // thread's row in a pass, rows per pass, tile rows, passes
-        int iq, it, ik;
+        int row;                   // this thread's row (relative) in the next pass
+        int P, nr, left, it, ik;   // rows/pass, tile rows, passes left, tile, tiles started
+        bool first;                // next pass is the tile's first (carries the alpha pieces)
     } c;
     auto set_tile = [&](int t) {
         TileD d = tile_desc(W, t, ntiles);
@@ -1050,19 +1080,20 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkD
             d = tile_desc(W, t, ntiles);
         }
         c.it = t;
-        c.iq = 0;
         if (t < ntiles) {
             const HotInst& I = W->inst[d.inst];
-            const int ro = tid / d.NC, cg = tid % d.NC;
-            const size_t base = ((size_t)d.slab * d.S + d.r0) * d.S + (size_t)ro * d.S + (size_t)cg * NV;
+            const int ro = tid / d.NC, cg = tid - ro * d.NC;
+            const size_t base = ((size_t)d.slab * d.S + d.r0 + ro) * d.S + (size_t)cg * NV;
             c.u = (const float*)I.u + base;
             c.d = (const float*)((j & 1) ? I.d1 : I.d0) + base;
             c.a = I.ab32 + (size_t)d.slab * 2 * d.S + d.r0;
             c.step = d.P * d.S;
-            c.ro = ro;
+            c.row = ro < d.P ? ro : kMaxS;           // threads past P rows copy nothing
             c.P = d.P;
             c.nr = d.r1 - d.r0;
-            c.npass = d.npass;
+            c.left = d.npass;
+            c.first = true;
+            if (tid == 0) s_td[c.ik % kStages] = d;
         }
     };
     c.ik = 0;
@@ -1070,14 +1101,19 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkD
     // one commit group per call: the copies of global pass n (ring slot n % kStages)
     auto issue = [&](int n) {
         if (c.it < ntiles) {
-            if (c.ro < c.P && c.ro + c.iq * c.P < c.nr) {
+            if (c.row < c.nr) {
                 float4* su = s_stage + (size_t)(n % kStages) * 2 * kThreads + tid;
-                const size_t o = (size_t)c.iq * c.step;
-                cp_async16(su, c.u + o);
-                cp_async16(su + kThreads, c.d + o);
+                cp_async16(su, c.u);
+                cp_async16(su + kThreads, c.d);
             }
-            if (c.iq == 0 && tid < c.nr) cp_async16(&s_alpha[c.ik % kStages][tid], c.a + tid);
-            if (++c.iq == c.npass) {
+            if (c.first) {
+                if (tid < c.nr) cp_async16(&s_alpha[c.ik % kStages][tid], c.a + tid);
+                c.first = false;
+            }
+            c.u += c.step;
+            c.d += c.step;
+            c.row += c.P;
+            if (--c.left == 0) {
                 ++c.ik;
                 set_tile(c.it + G);
             }
@@ -1087,127 +1123,167 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkD
 #pragma unroll 1
     for (int q = 0; q < kStages - 1; ++q) issue(q);
 
-    int n = 0;                                   // global index of the next pass to compute
-    int ct = blockIdx.x, ck = 0;
-    TileD dc = tile_desc(W, ct, ntiles);
-    while (ct < ntiles && dc.npass == 0) {
-        ct += G;
-        dc = tile_desc(W, ct, ntiles);
-    }
-    while (ct < ntiles) {
-        const HotInst& I = W->inst[dc.inst];
-        const int S = dc.S, NC = dc.NC, P = dc.P, nb = I.nb;
-        const int slab = dc.slab, band = dc.band, r0 = dc.r0, r1 = dc.r1;
-        const int cg = tid % NC, ro = tid / NC;
-        const bool active = ro < P;
-        const int c0 = cg * NV;
-        float* __restrict__ dout = (float*)((j & 1) ? I.d0 : I.d1) + (size_t)slab * S * S;
-        const float4* ab = I.ab32 + (size_t)slab * 2 * S;
-        const P32 p = *I.p32;
-        float4 bq[NV];
-        float cf[NV];
+    // ---- compute side
+    // per column of this thread: B_c = h c^2 - beta_hi (exact), beta_lo,
+    // dbeta, c; loaded for the next tile during the current tile's epilogue
+    float4 bq[NV];
+    P32 p;
+    auto load_cols = [&](const TileD& d) {
+        const HotInst& I = W->inst[d.inst];
+        const int ro = tid / d.NC, c0 = (tid - ro * d.NC) * NV;
+        p = *I.p32;
+        const float4* ab = I.ab32 + (size_t)d.slab * 2 * d.S + d.S;
 #pragma unroll
-        for (int e = 0; e < NV; ++e) {
-            bq[e] = active ? ab[S + c0 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
-            cf[e] = (float)(c0 + e);
-        }
-        // the tile's alpha pieces came with its first pass (group n)
+        for (int e = 0; e < NV; ++e)
+            bq[e] = ro < d.P ? ab[c0 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
+    };
+    bool have = false;                           // bq, p hold the current tile's values
+    int n = 0;                                   // global index of the next pass to compute
+    for (int ck = 0;; ++ck) {
+        // the tile's alpha pieces and its descriptor: group n (its first pass)
+        // and thread 0's store, both complete before this barrier
         cp_async_wait<kStages - 2>();
         __syncthreads();
+        // the issue side has started every tile this CTA still has (it runs ahead)
+        if (c.it >= ntiles && ck >= c.ik) break;
+        const TileD dc = s_td[ck % kStages];
+        if (!have) load_cols(dc);
+        const HotInst& I = W->inst[dc.inst];
+        const int S = dc.S, NC = dc.NC, P = dc.P, nb = I.nb;
+        const int slab = dc.slab, band = dc.band, r0 = dc.r0, nr = dc.r1 - dc.r0;
+        const int ro = tid / NC, cg = tid - ro * NC;
+        const bool active = ro < P;
+        const int c0 = cg * NV;
+        const float h = p.h;
+#pragma unroll
+        for (int e = 0; e < NV; ++e) {
+            const float cf = (float)(c0 + e);
+            bq[e] = make_float4(fmaf(cf * cf, h, -bq[e].x), bq[e].y, bq[e].z, cf);
+        }
         const float4* sa = s_alpha[ck % kStages];
+        float* __restrict__ dout = (float*)((j & 1) ? I.d0 : I.d1) + ((size_t)slab * S + r0 + ro) * S + c0;
+        const int ostep = P * S;
+        float* srow = s_row + ro * (NC + 1) + cg;
+        float* sxrow = s_xrow + (CHECK ? ro * (NC + 1) + cg : 0);
+        const int rstep = P * (NC + 1);
         float cacc[NV], xacc[NV];
 #pragma unroll
         for (int e = 0; e < NV; ++e) cacc[e] = xacc[e] = 0.f;
         // KKT partials: FP32 chains of at most 64 terms per thread and tile
         // (a tile has TR * S / 1024 <= 16 passes), summed over the CTA in pairs
         float k32[kNK] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        int rr = ro;                              // this thread's row, relative to r0
 #pragma unroll 1
         for (int q = 0; q < dc.npass; ++q, ++n) {
             issue(n + kStages - 1);
-            cp_async_wait<kStages - 1>();            // this thread's pass-n copies are in
-            const int r = r0 + ro + q * P;
-            if (active && r < r1) {
+            cp_async_wait<kStages - 1>();         // this thread's pass-n copies are in
+            if (active && rr < nr) {
                 const float4* su = s_stage + (size_t)(n % kStages) * 2 * kThreads + tid;
                 const float4 U = su[0], D = su[kThreads];
                 const float uu[NV] = {U.x, U.y, U.z, U.w};
                 const float dd[NV] = {D.x, D.y, D.z, D.w};
-                const float4 a = sa[r - r0];
-                const float rf = (float)r;
+                const float4 a = sa[rr];
+                const float rf = (float)(r0 + rr);
+                const float Ar = fmaf(rf * rf, h, -a.x);      // h r^2 - alpha_hi (exact)
+                const float m2hr = -2.f * h * rf;             // exact
                 float out[NV], xo[NV];
 #pragma unroll
                 for (int e = 0; e < NV; ++e) {
-                    const float dcol = rf - cf[e];
-                    const float cq = dcol * dcol;
-                    const E32 el = elem32(uu[e], dd[e], cq, a, bq[e], p);
-                    out[e] = fmaf(p.trs, el.r, p.rho * dd[e]);
+                    const float4 b = bq[e];
+                    const float Gh = fmaf(m2hr, b.w, Ar + b.x);   // h (r-c)^2 - alpha_hi - beta_hi
+                    const float Gl = -(a.y + b.y);
+                    const float Dv = a.z + b.z;                  // A^T (y-bar - y0)
+                    const float s = uu[e] + dd[e];
+                    const float w = fmaf(-s, p.sih, -Dv);        // g - v/sigma
+                    const float mg = -(Gh + Gl);                 // -g
+                    const float r = fmaxf(w, mg);                // z-bar - g
+                    out[e] = fmaf(p.trs, r, p.rho * dd[e]);
                     if constexpr (CHECK) {
-                        float xb, zb;
-                        xz32(el, p, xb, zb);
+                        const float zb = (w > mg) ? ((Gh + Gl) + w) : 0.f;
+                        const float xb = fmaf(p.sf, Dv, s);
+                        const float dcol = rf - b.w;
                         xo[e] = xb;
                         const float mn = fminf(xb, zb);
-                        k32[0] = fmaf(el.r, el.r, k32[0]);
+                        k32[0] = fmaf(r, r, k32[0]);
                         k32[1] = fmaf(mn, mn, k32[1]);
                         k32[2] = fmaf(xb, xb, k32[2]);
                         k32[3] = fmaf(zb, zb, k32[3]);
-                        k32[4] = fmaf(cq, xb, k32[4]);
+                        k32[4] = fmaf(dcol * dcol, xb, k32[4]);
                         xacc[e] += xb;
                     }
                     cacc[e] += out[e];
                 }
-                VecT<float>::st(dout + (size_t)r * S + c0, out);
-                s_row[(r - r0) * (NC + 1) + cg] = (out[0] + out[1]) + (out[2] + out[3]);
-                if constexpr (CHECK) s_xrow[(r - r0) * (NC + 1) + cg] = (xo[0] + xo[1]) + (xo[2] + xo[3]);
+                *reinterpret_cast<float4*>(dout) = make_float4(out[0], out[1], out[2], out[3]);
+                *srow = (out[0] + out[1]) + (out[2] + out[3]);
+                if constexpr (CHECK) *sxrow = (xo[0] + xo[1]) + (xo[2] + xo[3]);
             }
+            dout += ostep;
+            srow += rstep;
+            if constexpr (CHECK) sxrow += rstep;
+            rr += P;
         }
-        // tile epilogue: row and column sums as double-float pairs
+        // ---- tile epilogue: column and row sums as double-float pairs
         if (active) {
-#pragma unroll
-            for (int e = 0; e < NV; ++e) {
-                s_col[ro * S + c0 + e] = cacc[e];
-                if constexpr (CHECK) s_xcol[ro * S + c0 + e] = xacc[e];
-            }
+            *reinterpret_cast<float4*>(&s_col[ro * S + c0]) = make_float4(cacc[0], cacc[1], cacc[2], cacc[3]);
+            if constexpr (CHECK)
+                *reinterpret_cast<float4*>(&s_xcol[ro * S + c0]) = make_float4(xacc[0], xacc[1], xacc[2], xacc[3]);
         }
         __syncthreads();
+        // the next tile's column values (thread 0 stored its descriptor while
+        // issuing its first pass, before this barrier); the loads complete
+        // under the reductions below
+        have = !(c.it >= ntiles && ck + 1 >= c.ik);
+        if (have) load_cols(s_td[(ck + 1) % kStages]);
         const size_t cbase = ((size_t)slab * nb + band) * S;
-        for (int c = tid; c < S; c += kThreads) {
+        for (int cc = tid; cc < S; cc += kThreads) {
             DF a{0.f, 0.f}, x{0.f, 0.f};
             for (int qq = 0; qq < P; ++qq) {
-                a = df_add(a, s_col[qq * S + c]);
-                if constexpr (CHECK) x = df_add(x, s_xcol[qq * S + c]);
+                a = df_add(a, s_col[qq * S + cc]);
+                if constexpr (CHECK) x = df_add(x, s_xcol[qq * S + cc]);
             }
-            I.cs32[cbase + c] = df_f(a);
-            if constexpr (CHECK) I.xcs_part[cbase + c] = df_val(x);
+            I.cs32[cbase + cc] = df_f(a);
+            if constexpr (CHECK) I.xcs_part[cbase + cc] = df_val(x);
         }
-        const int warp = tid >> 5, lane = tid & 31;
-        for (int rr = warp; rr < r1 - r0; rr += kThreads / 32) {
-            DF a{0.f, 0.f}, x{0.f, 0.f};
-            for (int c = lane; c < NC; c += 32) {
-                a = df_add(a, s_row[rr * (NC + 1) + c]);
-                if constexpr (CHECK) x = df_add(x, s_xrow[rr * (NC + 1) + c]);
-            }
-            a = warp_sum_df(a);
-            if constexpr (CHECK) x = warp_sum_df(x);
-            if (lane == 0) {
-                I.rs2[(size_t)slab * S + r0 + rr] = df_st(a);
-                if constexpr (CHECK) I.xrs[(size_t)slab * S + r0 + rr] = df_val(x);
+        // rows: warp w sums partials [w NC/8, (w+1) NC/8) of rows lane, lane + 32, ...
+        // (row stride NC + 1 keeps the lanes on distinct banks), then the 8
+        // pairs of each row are combined in warp order
+        {
+            const int w0 = (warp * NC) / kW, w1 = ((warp + 1) * NC) / kW;
+            for (int r = lane; r < nr; r += 32) {
+                DF a{0.f, 0.f}, x{0.f, 0.f};
+                for (int cc = w0; cc < w1; ++cc) {
+                    a = df_add(a, s_row[r * (NC + 1) + cc]);
+                    if constexpr (CHECK) x = df_add(x, s_xrow[r * (NC + 1) + cc]);
+                }
+                s_rdf[warp][r] = df_st(a);
+                if constexpr (CHECK) s_xdf[warp][r] = df_st(x);
             }
         }
         if constexpr (CHECK) {
             DF kd[kNK];
 #pragma unroll
             for (int qq = 0; qq < kNK; ++qq) kd[qq] = DF{k32[qq], 0.f};
-            block_sum_df<kNK>(kd, s_red);
+            block_sum_df<kNK>(kd, s_red);        // its barriers also publish s_rdf
             if (tid == 0) {
                 double* o = I.tile_kkt + ((size_t)slab * nb + band) * kNK;
 #pragma unroll
                 for (int qq = 0; qq < kNK; ++qq) o[qq] = df_val(kd[qq]);
             }
+        } else {
+            __syncthreads();
         }
-        ++ck;
-        do {
-            ct += G;
-            dc = tile_desc(W, ct, ntiles);
-        } while (ct < ntiles && dc.npass == 0);
+        for (int r = tid; r < nr; r += kThreads) {
+            DF a = df_ld(s_rdf[0][r]), x{0.f, 0.f};
+            if constexpr (CHECK) x = df_ld(s_xdf[0][r]);
+#pragma unroll
+            for (int w = 1; w < kW; ++w) {
+                a = df_add(a, df_ld(s_rdf[w][r]));
+                if constexpr (CHECK) x = df_add(x, df_ld(s_xdf[w][r]));
+            }
+            a = df_add(a, df_ld(I.rs02[(size_t)slab * S + r0 + r]));      // + row sum of u
+            I.rs2[(size_t)slab * S + r0 + r] = df_st(a);
+            if constexpr (CHECK) I.xrs[(size_t)slab * S + r0 + r] = df_val(x);
+        }
     }
     cp_async_wait<0>();
 }
@@ -1368,8 +1444,7 @@ __device__ __forceinline__ void restart_tile(const HotInst& I, int slab, int ban
         };
         for (int rr = threadIdx.x; rr < r1 - r0; rr += blockDim.x) {
             I.rs0[(size_t)slab * S + r0 + rr] = sum_f64_strided(s_row + rr * NC, NC, 1);
-            if (F32) I.rs2[(size_t)slab * S + r0 + rr] = make_float2(0.f, 0.f);
-            else I.rs[(size_t)slab * S + r0 + rr] = 0.0;
+            if (!F32) I.rs[(size_t)slab * S + r0 + rr] = 0.0;      // FP32: k_anchor resets rs2
             set_anchor(r0 + rr);
         }
         if (band == 0)
@@ -1385,6 +1460,13 @@ __global__ void __launch_bounds__(kThreads) k_restart(const WorkDev* __restrict_
     __shared__ int s_tile[4];
     const int ninst = W->ninst;
     const int ntiles = W->pre_tile[ninst];
+    // most blocks end without a restart: leave at once unless some instance needs this pass
+    int any = 0;
+    for (int i = threadIdx.x; i < ninst; i += blockDim.x) {
+        const HotCtl* C = W->inst[i].ctl;
+        any |= (MODE == 2) ? (C->just_finished != 0) : (C->status == ST_RUNNING && C->restart_pending != 0);
+    }
+    if (!__syncthreads_or(any)) return;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         TileCtx tc;
         resolve_tile(W, t, tc, s_tile);
@@ -1538,6 +1620,8 @@ __global__ void __launch_bounds__(kThreads) k_check(const WorkDev* __restrict__ 
             const double rel_comp = sqrt(mn2) / (1.0 + sqrt(x2) + sqrt(z2));
             const double rel_primal = sqrt(ax2) / (1.0 + I.norm_b);
             const double rel = fmax(rel_dual, fmax(rel_comp, rel_primal));
+            const double absk = fmax(sqrt(r2), fmax(sqrt(mn2), sqrt(ax2)));      // Table VI
+            C->abs_kkt = absk;
             C->rel_dual = rel_dual;
             C->rel_comp = rel_comp;
             C->rel_primal = rel_primal;
@@ -1554,7 +1638,7 @@ __global__ void __launch_bounds__(kThreads) k_check(const WorkDev* __restrict__ 
             } else if (C->cancel) {
                 C->status = ST_CANCELLED;
                 fin = 1;
-            } else if (rel <= C->tol) {
+            } else if ((I.stop_abs ? absk : rel) <= C->tol) {
                 C->status = ST_CONVERGED;
                 fin = 1;
             } else if (total >= C->max_iter) {
@@ -1643,8 +1727,8 @@ LaunchDims make_launch_dims(int device, int fp64) {
         d.grid_slab = occ_grid(k_alpha<true>, sms, 0, 4);
         d.grid_vec = occ_grid(k_vec, sms, 0, 4);
     } else {
-        d.grid_tile = occ_grid(k_sweep32<false>, sms, kStages * kStageBytes, 8);
-        d.grid_tile_chk = occ_grid(k_sweep32<true>, sms, kStages * kStageBytes, 8);
+        d.grid_tile = occ_grid(k_sweep32<false>, sms, kSweepSmem, 8);
+        d.grid_tile_chk = occ_grid(k_sweep32<true>, sms, kSweepSmemChk, 8);
         d.grid_rst = std::min(occ_grid(k_restart<float, 0>, sms, 0, 8), occ_grid(k_restart<float, 1>, sms, 0, 8));
         d.grid_slab = occ_grid(k_alpha32<true>, sms, 0, 4);
         d.grid_vec = occ_grid(k_vec32, sms, 0, 4);
@@ -1677,11 +1761,9 @@ void launch_init(const HotInst& I, double sigma0, cudaStream_t st) {
 
 cudaError_t kernels_init(int device) {
     (void)device;
-    cudaError_t e = cudaFuncSetAttribute(k_sweep32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kStages * kStageBytes);
+    cudaError_t e = cudaFuncSetAttribute(k_sweep32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSweepSmem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_sweep32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kStages * kStageBytes);
+        e = cudaFuncSetAttribute(k_sweep32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSweepSmemChk);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_marg, cudaFuncAttributeMaxDynamicSharedMemorySize, 7 * kMaxS * 8);
     return e;
 }
@@ -1703,8 +1785,8 @@ void launch_sweep(const WorkDev* w, const LaunchDims& ld, int fp64, int j, bool 
     if (fp64) {
         k_sweep64<<<check ? ld.grid_tile_chk : ld.grid_tile, kThreads, 0, st>>>(w, j, check ? 1 : 0);
     } else {
-        if (check) k_sweep32<true><<<ld.grid_tile_chk, kThreads, kStages * kStageBytes, st>>>(w, j);
-        else k_sweep32<false><<<ld.grid_tile, kThreads, kStages * kStageBytes, st>>>(w, j);
+        if (check) k_sweep32<true><<<ld.grid_tile_chk, kThreads, kSweepSmemChk, st>>>(w, j);
+        else k_sweep32<false><<<ld.grid_tile, kThreads, kSweepSmem, st>>>(w, j);
     }
 }
 

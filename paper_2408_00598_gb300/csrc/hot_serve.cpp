@@ -131,7 +131,7 @@ static void serve_loop(Ctx* ctx) {
         for (Req* r : admit) {
             Inst* I = nullptr;
             r->t_admit = Clock::now();
-            const int rc = inst_create(r->pair, fp64, ctx->cfg.sigma0, r->tol, r->max_iter, 0, s->st, &I);
+            const int rc = inst_create(r->pair, fp64, ctx->cfg, r->tol, r->max_iter, 0, s->st, &I);
             std::lock_guard<std::mutex> g(s->mu);
             if (rc != HOT_OK) {
                 s->in_use -= std::min(s->in_use, r->bytes);

@@ -33,6 +33,10 @@ HOT_FP32_BULK = 0
 HOT_FP64 = 1
 HOT_SPACE_HOST = 0
 HOT_SPACE_DEVICE = 1
+HOT_METHOD_HALPERN = 0
+HOT_METHOD_GADMM = 1
+HOT_STOP_RELATIVE = 0
+HOT_STOP_ABSOLUTE = 1
 
 
 class HotError(RuntimeError):
@@ -52,7 +56,8 @@ class hot_config(ctypes.Structure):
                 ("restart_sufficient", ctypes.c_double), ("restart_necessary", ctypes.c_double),
                 ("restart_long", ctypes.c_double), ("mem_budget", ctypes.c_size_t), ("max_batch", ctypes.c_int),
                 ("max_queue", ctypes.c_int), ("autotune_cache", ctypes.c_char_p),
-                ("keep_batch_solutions", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+                ("keep_batch_solutions", ctypes.c_int), ("method", ctypes.c_int), ("relaxation", ctypes.c_double),
+                ("stop_rule", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 class hot_result(ctypes.Structure):
@@ -62,7 +67,7 @@ class hot_result(ctypes.Structure):
                 ("queue_ms", ctypes.c_double), ("iters", ctypes.c_longlong), ("restarts", ctypes.c_int),
                 ("status", ctypes.c_int), ("solution_id", ctypes.c_ulonglong), ("max_abs_dual", ctypes.c_float),
                 ("m", ctypes.c_int), ("n", ctypes.c_int), ("kernel_launches", ctypes.c_longlong),
-                ("blocks", ctypes.c_longlong)]
+                ("blocks", ctypes.c_longlong), ("abs_kkt", ctypes.c_double)]
 
     def to_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
@@ -352,12 +357,18 @@ def hot_serve_stats_get(ctx):
 
 
 class Context:
-    """Owns one hot_ctx.  ``precision``: "fp32" (FP32 bulk) or "fp64"."""
+    """Owns one hot_ctx.  ``precision``: "fp32" (FP32 bulk) or "fp64";
+    ``method``: "hot" (Algorithm 2) or "gadmm" (generalized ADMM, ``relaxation``
+    rho); ``stop``: "relative" (eq. kkt_res) or "absolute" (Table VI)."""
 
-    def __init__(self, device=0, precision="fp32", stream=None, **kw):
+    def __init__(self, device=0, precision="fp32", stream=None, method="hot", stop="relative", **kw):
         cfg = hot_config_default()
         cfg.device = device
         cfg.precision = HOT_FP64 if precision == "fp64" else HOT_FP32_BULK
+        if method not in ("hot", "gadmm") or stop not in ("relative", "absolute"):
+            raise ValueError("method must be 'hot' or 'gadmm', stop 'relative' or 'absolute'")
+        cfg.method = HOT_METHOD_GADMM if method == "gadmm" else HOT_METHOD_HALPERN
+        cfg.stop_rule = HOT_STOP_ABSOLUTE if stop == "absolute" else HOT_STOP_RELATIVE
         if stream is not None:
             cfg.stream = ctypes.c_void_p(stream)
         for k, v in kw.items():
