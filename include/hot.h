@@ -224,6 +224,26 @@ HOT_API int hot_recover_plan_static(const double *x, int m, int n, const double 
                             int32_t *src, int32_t *dst, double *mass, size_t cap, size_t *nnz,
                             double *marg_l1, void *stream);
 
+/* Barycentric projection of a transport plan, the colour-transfer use of a
+ * plan (Sec. IV-B, App. G): for every source bin s,
+ *     out[s] = sum_t pi(s, t) y[t] / sum_t pi(s, t),   weight[s] = sum_t pi(s, t),
+ * over the entries (src[e], dst[e], mass[e]) of a plan such as the output of
+ * hot_recover_plan (source bins are row-major m x n indices of mu, target
+ * bins those of nu).  A source with no mass gets out = 0 and weight = 0.
+ *   src, dst, mass: device, nnz entries (int32, int32, double)
+ *   y:       device, ndst x D doubles, row-major (a D-vector per target bin, 1 <= D <= 8)
+ *   out:     device, nsrc x D doubles, row-major (written)
+ *   weight:  device, nsrc doubles (written)
+ *   stream:  cudaStream_t to run on (NULL: the legacy default stream); the call
+ *            returns after its work on that stream has finished.
+ * Entries whose bin index is out of range are skipped and make the call
+ * return HOT_EINVAL (the other entries are still applied).  Sums are FP64
+ * atomic adds in unspecified order: reproducible to rounding, not bit for bit.
+ * Allocates 4 bytes of device memory for the error count. */
+HOT_API int hot_barycentric_map(const int32_t *src, const int32_t *dst, const double *mass, size_t nnz,
+                                const double *y, int ndst, int D, double *out, double *weight, int nsrc,
+                                void *stream);
+
 /* Free the device memory of a kept solution.  Unknown id: HOT_ENOTFOUND. */
 HOT_API int hot_release(hot_ctx *ctx, unsigned long long solution_id);
 

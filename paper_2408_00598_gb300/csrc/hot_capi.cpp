@@ -332,4 +332,11 @@ int hot_serve_stats_get(hot_ctx* ctx, hot_serve_stats* out) {
     HOT_GUARD_END
 }
 
+int hot_barycentric_map(const int32_t* src, const int32_t* dst, const double* mass, size_t nnz, const double* y,
+                        int ndst, int D, double* out, double* weight, int nsrc, void* stream) {
+    HOT_GUARD_BEGIN
+    return hot::barycentric_map(src, dst, mass, nnz, y, ndst, D, out, weight, nsrc, (cudaStream_t)stream);
+    HOT_GUARD_END
+}
+
 }  // extern "C"

@@ -57,6 +57,10 @@ int validate_pair(const double* mu, const double* nu, int m, int n, int space, i
 int tile_rows(int S, int fp64, int grid);
 
 // Allocate and initialise an instance on stream `st` (inputs already validated).
+// Barycentric projection of a plan (hot_consumers.cu).
+int barycentric_map(const int* src, const int* dst, const double* mass, size_t nnz, const double* y, int ndst,
+                    int D, double* out, double* weight, int nsrc, cudaStream_t st);
+
 int inst_create(const PairHost& p, int fp64, const hot_config& cfg, double tol, long long max_iter, int tr_override,
                 cudaStream_t st, Inst** out);
 void inst_destroy(Inst* I, cudaStream_t st);

@@ -134,6 +134,7 @@ def load_library(path=None):
         "hot_cancel": (i, [vp, ull]),
         "hot_forget": (i, [vp, ull]),
         "hot_serve_stats_get": (i, [vp, P(hot_serve_stats)]),
+        "hot_barycentric_map": (i, [vp, vp, vp, sz, vp, i, i, vp, vp, i, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -167,6 +168,30 @@ def hot_config_default():
     load_library().hot_config_default(ctypes.byref(cfg))
     return cfg
 
+
+
+def hot_barycentric_map(src, dst, mass, y, nsrc, out=None, weight=None, stream=None):
+    """Barycentric projection of a plan (device tensors): out[s] = sum pi y[t] / sum pi,
+    weight[s] = sum pi.  src/dst int32, mass float64 (nnz each), y float64 (ndst, D)."""
+    import torch
+    lib = load_library()
+    if not (src.is_cuda and dst.is_cuda and mass.is_cuda and y.is_cuda):
+        raise HotError(HOT_EINVAL, "hot_barycentric_map takes device tensors")
+    if src.dtype != torch.int32 or dst.dtype != torch.int32 or mass.dtype != torch.float64 or y.dtype != torch.float64:
+        raise HotError(HOT_EINVAL, "src/dst must be int32 and mass/y float64")
+    y2 = y.reshape(y.shape[0], -1).contiguous()
+    D = y2.shape[1]
+    if out is None:
+        out = torch.empty((nsrc, D), dtype=torch.float64, device=y.device)
+    if weight is None:
+        weight = torch.empty(nsrc, dtype=torch.float64, device=y.device)
+    s, t, m = src.contiguous(), dst.contiguous(), mass.contiguous()
+    rc = lib.hot_barycentric_map(s.data_ptr(), t.data_ptr(), m.data_ptr(), s.numel(), y2.data_ptr(), y2.shape[0], D,
+                                 out.data_ptr(), weight.data_ptr(), nsrc,
+                                 ctypes.c_void_p(stream if stream is not None else torch.cuda.current_stream().cuda_stream))
+    if rc != HOT_OK:
+        raise _err(lib, None, rc)
+    return out, weight
 
 def hot_create(cfg=None):
     lib = load_library()

@@ -1,0 +1,79 @@
+"""GPU parity of the plan consumer hot_barycentric_map (the colour-transfer
+use of a plan, Sec. IV-B / App. G) against the oracle, and the whole chain
+solve -> Algorithm 1 -> barycentric map on a translated pair, whose image of
+every source bin is the bin moved by the translation (closed form)."""
+import numpy as np
+import pytest
+
+from oracle import consumers
+from paper_2408_00598_gb300 import synthetic as syn
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hot():
+    from paper_2408_00598_gb300 import hot
+    hot.load_library()
+    return hot
+
+
+@pytest.mark.parametrize("nnz,nsrc,ndst,D", [(0, 5, 3, 2), (1, 1, 1, 1), (5000, 300, 200, 3), (200000, 4096, 4096, 8)])
+def test_barycentric_map_matches_oracle(hot, nnz, nsrc, ndst, D):
+    import torch
+    rng = np.random.default_rng(nnz + D)
+    src = rng.integers(0, nsrc, nnz).astype(np.int32)
+    src[: min(nnz, nsrc // 3)] = 0                       # one heavy row, and rows with no entry
+    dst = rng.integers(0, ndst, nnz).astype(np.int32)
+    mass = rng.uniform(0.0, 1.0, nnz)
+    y = rng.standard_normal((ndst, D))
+    ref, wref = consumers.barycentric_map(src, dst, mass, y, nsrc)
+    out, w = hot.hot_barycentric_map(torch.from_numpy(src).cuda(), torch.from_numpy(dst).cuda(),
+                                     torch.from_numpy(mass).cuda(), torch.from_numpy(y).cuda(), nsrc)
+    np.testing.assert_allclose(w.cpu().numpy(), wref, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=1e-11, atol=1e-11)
+
+
+def test_out_of_range_bins_are_reported(hot):
+    import torch
+    src = torch.tensor([0, 7], dtype=torch.int32, device="cuda")
+    dst = torch.tensor([0, 0], dtype=torch.int32, device="cuda")
+    mass = torch.tensor([1.0, 1.0], dtype=torch.float64, device="cuda")
+    y = torch.ones((1, 2), dtype=torch.float64, device="cuda")
+    with pytest.raises(hot.HotError) as e:
+        hot.hot_barycentric_map(src, dst, mass, y, 4)
+    assert e.value.status == hot.HOT_EINVAL
+
+
+@pytest.mark.parametrize("S,precision,tol", [(32, "fp64", 1e-10), (64, "fp32", 1e-8)])
+def test_translation_chain(hot, S, precision, tol):
+    """Solve, recover the plan on the device, map the bins' own coordinates:
+    every source bin with mass lands on itself plus (s, t); synthetic points
+    drawn from mu1 move by (s, t) on average."""
+    import torch
+    mu1, mu2, s, t = syn.make_translation(S, 6)
+    with hot.Context(precision=precision) as ctx:
+        r = ctx.solve(mu1, mu2, tol=tol, max_iter=300000)
+        n, _ = ctx.recover_plan(r, device_out=())
+        src = torch.empty(n, dtype=torch.int32, device="cuda")
+        dst = torch.empty(n, dtype=torch.int32, device="cuda")
+        mass = torch.empty(n, dtype=torch.float64, device="cuda")
+        ctx.recover_plan(r, device_out=(src, dst, mass))
+        ctx.release(r)
+    assert r["status"] == 0
+    xy = torch.from_numpy(consumers.grid_coordinates(S, S)).cuda()
+    out, w = hot.hot_barycentric_map(src, dst, mass, xy, S * S)
+    out, w = out.cpu().numpy(), w.cpu().numpy()
+    xyh = consumers.grid_coordinates(S, S)
+    shift = np.array([s, t], dtype=float)
+    dev = np.abs(out - xyh - shift).max(axis=1)
+    # mass-weighted mean deviation, and the worst bin among those with 1 % of
+    # the largest bin's mass (an approximate plan spreads tiny rows the most)
+    assert (w * dev).sum() / w.sum() <= (1e-6 if precision == "fp64" else 1e-3)
+    big = mu1.ravel() > 1e-2 * mu1.max()
+    assert dev[big].max() <= (1e-4 if precision == "fp64" else 2e-2)
+    # a synthetic point set: 10^5 points drawn from mu1's bins, moved by T
+    rng = np.random.default_rng(1)
+    pts = rng.choice(S * S, 100000, p=mu1.ravel() / mu1.sum())
+    moved = out[pts] - xyh[pts]
+    assert np.abs(moved.mean(axis=0) - shift).max() <= 1e-3
