@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=512)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--duration", type=float, default=60.0)
+    ap.add_argument("--compare-fp64", action="store_true",
+                    help="batch mode: also solve the same pairs one by one in FP64 mode (the plain GPU form)")
     return ap.parse_args()
 
 
@@ -368,6 +370,25 @@ def bench_batch(args, dist):
     t = dist.max(time.perf_counter() - t0)
     iters = sum(o["iters"] for o in out)
     vol = sum(2 * b[1] ** 3 for b in batch)
+    extra = {}
+    if args.compare_fp64:
+        # the plain FP64 single-instance form on the same pairs, one solve at a time
+        ctx64 = hot.Context(device=dist.local_rank, precision="fp64", stream=stream.cuda_stream)
+        r64 = [ctx64.solve(mus[0], nus[0], tol=args.tol)]          # warm-up
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        r64 = [ctx64.solve(a, b, tol=args.tol) for a, b in zip(mus, nus)]
+        torch.cuda.synchronize()
+        t64 = time.perf_counter() - t1
+        for r in r64:
+            ctx64.release(r)
+        ctx64.close()
+        rel = [abs(a["dual_value"] - b["dual_value"]) / abs(b["dual_value"]) for a, b in zip(out, r64)]
+        relp = [abs(a["ot_value"] - b["ot_value"]) / abs(b["ot_value"]) for a, b in zip(out, r64)]
+        extra = {"fp64_sequential": {"solves_per_s": round(args.batch / t64, 2), "seconds": round(t64, 2),
+                                     "converged": sum(1 for r in r64 if r["status"] == 0)},
+                 "fp32_batch_vs_fp64": {"max_rel_dual": max(rel), "median_rel_dual": statistics.median(rel),
+                                        "max_rel_ot": max(relp), "median_rel_ot": statistics.median(relp)}}
     return {"metric": "batched solves/s (512 pairs, S in {32..128})", "value": round(dist.world * args.batch *
                                                                                      args.steps / t, 2),
             "unit": "solves/s", "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup,
@@ -375,7 +396,7 @@ def bench_batch(args, dist):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "batch of %d pairs" % args.batch, "tol": args.tol},
             "instance_iterations": iters, "converged": sum(1 for o in out if o["status"] == 0),
-            "blocks": out[0]["blocks"], "flow_variables": vol}
+            "blocks": out[0]["blocks"], "flow_variables": vol, **extra}
 
 
 def bench_serve(args, dist):

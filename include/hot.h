@@ -95,7 +95,7 @@ typedef struct hot_config {
     size_t mem_budget;          /* bytes of device memory the serve loop may hold; 0: 80 % of free */
     int    max_batch;           /* instances resident at once in the serve loop (0: 1024)   */
     int    max_queue;           /* queued requests before hot_submit returns HOT_EBUSY (0: 65536) */
-    const char *autotune_cache; /* file caching tuned tile shapes; NULL: defaults, no file  */
+    const char *autotune_cache; /* file of tuned tile shapes (hot_autotune); NULL: no file   */
     int    keep_batch_solutions;/* 1: hot_solve_batch keeps every final iterate (solution_id) */
     int    method;              /* HOT_METHOD_HALPERN (Algorithm 2, default) or HOT_METHOD_GADMM */
     double relaxation;          /* rho of HOT_METHOD_GADMM, in (0, 2)                   (1.7) */
@@ -243,6 +243,26 @@ HOT_API int hot_recover_plan_static(const double *x, int m, int n, const double 
 HOT_API int hot_barycentric_map(const int32_t *src, const int32_t *dst, const double *mass, size_t nnz,
                                 const double *y, int ndst, int D, double *out, double *weight, int nsrc,
                                 void *stream);
+
+/* Tile-shape autotuner.  The sweep tiles every S x S slab into bands of TR
+ * rows; this times each candidate TR on a synthetic S x S instance on the
+ * context's device (a fixed number of iterations, no early stop) and keeps
+ * the fastest for every later instance of that size on this context,
+ * including the serve loop.  With cfg.autotune_cache set, hot_create loads
+ * the entries for this device from that file and hot_autotune appends its
+ * result (text, one entry per line: device name, fp32|fp64, S, TR,
+ * microseconds per iteration; the last entry for a key wins).
+ *   tile_rows, us_per_iter: host, optional (NULL: not written)
+ * Allocates and frees the device memory of one instance per candidate;
+ * serialised with hot_solve on the same context.  HOT_EINVAL for grid sides
+ * the solver does not take, or when the cache file cannot be written. */
+HOT_API int hot_autotune(hot_ctx *ctx, int S, int *tile_rows, double *us_per_iter);
+
+/* The entry of an autotune cache file for (device name as written there,
+ * precision HOT_FP32_BULK or HOT_FP64, S): host only, needs no GPU.
+ * HOT_ENOTFOUND when the file or the entry is missing. */
+HOT_API int hot_autotune_cache_lookup(const char *path, const char *device, int precision, int S, int *tile_rows,
+                                      double *us_per_iter);
 
 /* Free the device memory of a kept solution.  Unknown id: HOT_ENOTFOUND. */
 HOT_API int hot_release(hot_ctx *ctx, unsigned long long solution_id);

@@ -32,7 +32,12 @@ Readings where the paper is silent (Sec. IV-A gives only the stopping rule):
   mean of the old sigma and the primal/dual movement ratio since the previous
   restart point (x_r, z_r) (0 before the first).  The ratio alone balances the
   two parts of the M-norm (App. A) but swings over many orders of magnitude
-  on degenerate inputs; the geometric mean damps it.
+  on degenerate inputs; the geometric mean damps it.  The new sigma is then
+  rounded to the geometric grid 2^(j/16): sigma is a free parameter, so a
+  4 % grid leaves the iteration counts unchanged on the synthetic classes,
+  while two runs whose norms differ only by rounding (an FP32 and an FP64
+  implementation) pick the same sigma instead of drifting apart by the
+  rounding error at every restart.
 * The iteration cap is tested at check iterations: the solve stops at the first
   check iteration whose total count reaches max_iter.
 
@@ -65,6 +70,7 @@ class HotParams:
     restart_necessary: float = 0.8
     restart_long: float = 0.2
     scale_cost: bool = True
+    sigma_steps: int = 16          # sigma rounded to 2^(j / sigma_steps) at restarts (0: not rounded)
     method: str = "hot"            # "hot" (Halpern Step 4) or "gadmm" (generalized ADMM)
     relax: float = 1.7             # rho of the generalized ADMM
     stop: str = "relative"         # "relative" (eq. kkt_res) or "absolute" (Table VI)
@@ -193,6 +199,9 @@ def hot_solve(mu1, mu2, tol=1e-6, max_iter=100000, params=None, xs=None, ys=None
                 dz = float(np.linalg.norm(z_bar - z_r))
                 if dx > 0.0 and dz > 0.0 and math.isfinite(dx / dz):
                     sigma = math.sqrt(sigma * (dx / dz))
+                    if p.sigma_steps > 0:
+                        q = p.sigma_steps
+                        sigma = 2.0 ** (round(math.log2(sigma) * q) / q)
                 x_r, z_r = x_bar.copy(), z_bar.copy()
                 x0, z0, y0 = x_bar.copy(), z_bar.copy(), y_bar.copy()
                 x, z, y = x0.copy(), z0.copy(), y0.copy()

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libhot.so")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["hot_kernels.cu", "hot_engine.cu", "hot_recover.cu", "hot_serve.cpp", "hot_capi.cpp", "hot_noalloc.cu",
-           "hot_consumers.cu"]
+           "hot_consumers.cu", "hot_autotune.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2,-fvisibility=hidden",
          "-I" + os.path.join(ROOT, "include")]

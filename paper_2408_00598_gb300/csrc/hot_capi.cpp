@@ -133,6 +133,9 @@ int hot_create(hot_ctx** out, const hot_config* cfg) {
     hot::Ctx& x = h->impl;
     x.cfg = c;
     x.device = c.device;
+    if (c.autotune_cache) x.tune_cache = c.autotune_cache;   // the caller's string is not kept
+    x.cfg.autotune_cache = nullptr;
+    hot::autotune_load(&x);
     if (c.stream) {
         x.stream = (cudaStream_t)c.stream;
         x.own_stream = false;
@@ -336,6 +339,26 @@ int hot_barycentric_map(const int32_t* src, const int32_t* dst, const double* ma
                         int ndst, int D, double* out, double* weight, int nsrc, void* stream) {
     HOT_GUARD_BEGIN
     return hot::barycentric_map(src, dst, mass, nnz, y, ndst, D, out, weight, nsrc, (cudaStream_t)stream);
+    HOT_GUARD_END
+}
+
+int hot_autotune(hot_ctx* ctx, int S, int* tile_rows, double* us_per_iter) {
+    HOT_GUARD_BEGIN
+    if (!ctx) {
+        set_error("ctx is NULL");
+        return HOT_EINVAL;
+    }
+    hot::Ctx& x = ctx->impl;
+    std::lock_guard<std::mutex> g(x.mu);
+    HOT_CK(cudaSetDevice(x.device));
+    return hot::autotune(&x, S, tile_rows, us_per_iter);
+    HOT_GUARD_END
+}
+
+int hot_autotune_cache_lookup(const char* path, const char* device, int precision, int S, int* tile_rows,
+                              double* us_per_iter) {
+    HOT_GUARD_BEGIN
+    return hot::autotune_cache_lookup(path, device, precision, S, tile_rows, us_per_iter);
     HOT_GUARD_END
 }
 

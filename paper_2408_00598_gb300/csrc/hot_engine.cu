@@ -144,7 +144,7 @@ int inst_create(const PairHost& p, int fp64, const hot_config& cfg, double tol, 
     const size_t o_rs2 = take(2 * SS * F2);
     const size_t o_rs02 = take(2 * SS * F2);
     const size_t o_K2 = take(2 * SS * F2);
-    const size_t o_vec2 = take(4 * (size_t)S * F2);
+    const size_t o_vec2 = take((2 + 2 * (size_t)((S + 63) / 64)) * (size_t)S * F2);
     const size_t o_dab2 = take(4 * SS * F2);
     const size_t o_zero_end = off;                 // everything above starts at 0
     const size_t o_mu1f = take(SS * F2);
@@ -159,6 +159,8 @@ int inst_create(const PairHost& p, int fp64, const hot_config& cfg, double tol, 
     const size_t o_rm = take(S * 8);
     const size_t o_k1 = take((size_t)I->n_k1 * 8);
     const size_t o_dp = take(2 * (size_t)S * 8);
+    const size_t o_cu = take((size_t)2 * S * I->nb * 8);
+    const size_t o_cD = take(2 * (size_t)S * 8);
     const size_t o_ctl = take(sizeof(HotCtl));
     I->small_bytes = off;
 
@@ -233,6 +235,8 @@ int inst_create(const PairHost& p, int fp64, const hot_config& cfg, double tol, 
     d.rowmu2 = (double*)(sm + o_rm);
     d.k1_part = (double*)(sm + o_k1);
     d.dobj_part = (double*)(sm + o_dp);
+    d.cu_part = (double*)(sm + o_cu);
+    d.cD_part = (double*)(sm + o_cD);
     d.rs2 = fp64 ? nullptr : (float2*)(sm + o_rs2);
     d.rs02 = fp64 ? nullptr : (float2*)(sm + o_rs02);
     d.K2 = fp64 ? nullptr : (float2*)(sm + o_K2);
@@ -403,9 +407,11 @@ int Batch::ensure_graph() {
     if (graph) return HOT_OK;
     if (!cap_stream) HOT_CK(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
     ld = make_launch_dims(device, fp64);
+    LaunchDims lg = ld;
+    lg.pdl = 1;                 // inside the graph the kernels chain programmatically
     HOT_CK(cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal));
-    for (int j = 0; j < K; ++j) launch_iteration(d_work, ld, fp64, j, j == K - 1, cap_stream);
-    launch_block_end(d_work, ld, fp64, K, a1, a2, a3, cap_stream);
+    for (int j = 0; j < K; ++j) launch_iteration(d_work, lg, fp64, j, j == K - 1, cap_stream);
+    launch_block_end(d_work, lg, fp64, K, a1, a2, a3, cap_stream);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(cap_stream, &g);
     if (e != cudaSuccess) {
@@ -479,7 +485,8 @@ int run_solve(Ctx* ctx, const std::vector<PairHost>& pairs, double tol, long lon
     };
     for (const PairHost& p : pairs) {
         Inst* I = nullptr;
-        int rc = inst_create(p, fp64, ctx->cfg, tol, max_iter, ctx->tile_override, st, &I);
+        const int tr = ctx->tile_override ? ctx->tile_override : tuned_tile_rows(ctx, p.S, fp64);
+        int rc = inst_create(p, fp64, ctx->cfg, tol, max_iter, tr, st, &I);
         if (rc != HOT_OK) {
             cleanup();
             return rc;

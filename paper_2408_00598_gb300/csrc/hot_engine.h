@@ -109,7 +109,10 @@ struct Ctx {
     std::map<unsigned long long, Solution> solutions;
     std::atomic<unsigned long long> next_id{1};
     std::unique_ptr<ServeState> serve;
-    int tile_override = 0;                 // testing hook: force TR (0 = default)
+    int tile_override = 0;                 // force TR (0 = tuned or default); the autotuner sets it
+    std::mutex tune_mu;                    // guards tuned (the serve thread reads it)
+    std::map<int, std::pair<int, double>> tuned[2];   // [fp64][S] -> (TR, us per iteration)
+    std::string tune_cache;                // hot_config.autotune_cache, copied
     Ctx();
     ~Ctx();
 };
@@ -120,6 +123,13 @@ void fill_result(const Inst* I, hot_result* r);
 int recover_plan(Ctx* ctx, Inst* I, int32_t* src, int32_t* dst, double* mass, int space, size_t cap, size_t* nnz,
                  double* marg_l1, cudaStream_t st);
 int export_flows(Inst* I, double* x, int space, cudaStream_t st);
+
+// tile-shape autotuner (hot_autotune.cpp)
+std::vector<int> tile_candidates(int S, int fp64);
+int tuned_tile_rows(Ctx* ctx, int S, int fp64);          // 0: not tuned
+void autotune_load(Ctx* ctx);
+int autotune(Ctx* ctx, int S, int* tr_out, double* us_out);
+int autotune_cache_lookup(const char* path, const char* device, int precision, int S, int* tr, double* us);
 
 // serve loop (hot_serve.cpp)
 void serve_shutdown(Ctx* ctx);

@@ -131,13 +131,15 @@ struct HotInst {
     double* rowmu2;        // [S] sum_l mu2(k, l)
     double* k1_part;       // [n_k1] partial ||A x - b||^2
     double* dobj_part;     // [2S] partial <b, y>
+    double* cu_part;       // [2S*nb] <c, u> per tile (FP32 mode, set per cycle)
+    double* cD_part;       // [2S] <c, A^T(y-bar - y0)> per slab (FP32 mode, check iterations)
     // FP32 bulk mode only (null in FP64 mode): the per-iteration Prop. 3
     // arithmetic runs on double-float pairs (hi, lo) of FP32 values, whose
     // sum carries about 48 significant bits, instead of FP64
     float2* rs2;           // [2S][S] row sums of u + d (last sweep; = rs02 after a restart)
     float2* rs02;          // [2S][S] row sums of u (fixed within a cycle)
     float2* K2;            // [2S][S] (mu - colsum u)/(sigma m) per slab column (/(sigma n) for f2), fixed within a cycle
-    float2* vec2;          // [4][S] T1, T2, P1, P2 of u + d
+    float2* vec2;          // T1 [S], T2 [S], then P1 and P2 as [2][ceil(S/64)][S] partials, of u + d
     float2* dab2;          // [2S][2S] pieces of A^T(y-bar - y0)
     float2* mu1f;          // [S][S] mu1 as pairs
     float2* mu2f;          // [S][S] mu2 as pairs
@@ -173,13 +175,15 @@ struct LaunchDims {
     int grid_vec;
     int grid_k1;
     int grid_inst;
+    int pdl;               // launch with programmatic stream serialisation (graph capture)
 };
 
 // FP64: k_vec, k_marg, k_alpha, k_sweep; FP32 bulk: k_vec32, k_alpha32, k_sweep
 inline int launches_per_iteration(int fp64) { return fp64 ? 4 : 3; }
 constexpr int kLaunchesBlockEnd = 8;       // k_kkt1, k_check, 3 x k_restart, k_restart_sigma, k_anchor, k_block_end
-// work items of k_vec32 per instance: T1/T2 in items of 8 outputs, P1/P2 in items of 32
-inline int vec32_items(int S) { return 2 * ((S + 7) / 8) + 2 * ((S + 31) / 32); }
+// work items of k_vec32 per instance: T1/T2 in items of 8 outputs, P1/P2 in
+// items of 32 columns x 64 rows (one partial per 64-row block)
+inline int vec32_items(int S) { return 2 * ((S + 7) / 8) + 2 * ((S + 31) / 32) * ((S + 63) / 64); }
 void launch_solve_kernels(const WorkDev* w, const LaunchDims& ld, int fp64, int j, bool check, cudaStream_t st);
 void launch_sweep(const WorkDev* w, const LaunchDims& ld, int fp64, int j, bool check, cudaStream_t st);
 void launch_iteration(const WorkDev* w, const LaunchDims& ld, int fp64, int j, bool check, cudaStream_t st);

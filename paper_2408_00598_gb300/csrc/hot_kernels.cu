@@ -191,6 +191,19 @@ __device__ __forceinline__ void block_sum_df(DF (&v)[NV], float2* sh) {
     __syncthreads();
 }
 
+// ------------------------------------------------- programmatic launches --
+// Every kernel of the iteration and block-end chain is launched with
+// programmatic stream serialisation: its CTAs may be scheduled while the
+// previous kernel drains, and griddepcontrol.wait (a hardware wait, first
+// statement of every such kernel, in every CTA) holds them until that kernel
+// has completed and its writes are visible.  Because every CTA waits before
+// touching memory, completion stays transitive along the chain.  The trigger
+// right after lets the next kernel be scheduled as early as possible.
+__device__ __forceinline__ void pdl_begin() {
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
 // ------------------------------------------------------ per-tile parameters --
 
 struct P64 {
@@ -336,6 +349,7 @@ __device__ __forceinline__ bool resolve_tile(const WorkDev* __restrict__ W, int 
 // P1[k] = sum_j rowsum(f1 slab j)[k], P2[j] = sum_k rowsum(f2 slab k)[j];
 // row sums are those of u + d (the slab sums of u are kept separately).
 __global__ void __launch_bounds__(kThreads) k_vec(const WorkDev* __restrict__ W) {
+    pdl_begin();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ninst = W->ninst;
     const int nitems = W->pre_vec[ninst];
@@ -384,6 +398,7 @@ __global__ void __launch_bounds__(kThreads) k_vec(const WorkDev* __restrict__ W)
 // k_alpha (one CTA per slab) then forms the slab's entries with products only
 // (FP64 division is slow on this part; reciprocals are taken once).
 __global__ void __launch_bounds__(kThreads) k_marg(const WorkDev* __restrict__ W) {
+    pdl_begin();
     extern __shared__ double sv[];                   // 7 * S: T1 T2 P1 P2 colmu1 rowmu2, then s
     __shared__ double s_red[4 * 32];
     const int ninst = W->ninst;
@@ -472,6 +487,7 @@ __global__ void __launch_bounds__(kThreads) k_marg(const WorkDev* __restrict__ W
 // arithmetic on top of the per-cycle split of a0.
 template <bool CHECK>
 __global__ void __launch_bounds__(kThreads) k_alpha(const WorkDev* __restrict__ W) {
+    pdl_begin();
     __shared__ double s_red[4 * 32];
     __shared__ float s_max[32];
     __shared__ int s_t[4];
@@ -569,10 +585,16 @@ __global__ void __launch_bounds__(kThreads) k_alpha(const WorkDev* __restrict__ 
 //
 // k_vec32: T1, T2, P1, P2 of u + d.  A work item is one CTA: for T1/T2 (sums
 // along contiguous rows) 8 outputs, one warp each; for P1/P2 (sums down the
-// columns of the row-sum matrices) 32 outputs, one per lane, rows split over
-// the warps and combined in a fixed order.
+// columns of the row-sum matrices) 32 columns x kVecRows rows, one column per
+// lane and kVecRows / 8 rows per warp, combined in a fixed order into one
+// partial per row block (k_alpha32 adds the partials).  Every lane issues
+// its loads before it adds, so an item costs about one L2 round trip.
+constexpr int kVecRows = 64;
+
 __global__ void __launch_bounds__(kThreads) k_vec32(const WorkDev* __restrict__ W) {
+    pdl_begin();
     constexpr int kW = kThreads / 32;
+    constexpr int kRW = kVecRows / kW;               // rows per warp in a P item
     __shared__ float2 s_p[kThreads];
     __shared__ int s_t[3];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -589,32 +611,50 @@ __global__ void __launch_bounds__(kThreads) k_vec32(const WorkDev* __restrict__ 
         if (s_t[2] == ST_RUNNING) {
             const HotInst& I = W->inst[s_t[0]];
             const int S = I.S;
-            const int q8 = (S + 7) / 8, q32 = (S + 31) / 32;
+            const int q8 = (S + 7) / 8, q32 = (S + 31) / 32, np = (S + kVecRows - 1) / kVecRows;
             const int item = s_t[1];
             const float2* __restrict__ rs = I.rs2;           // row sums of u + d
             if (item < 2 * q8) {
                 const int which = item / q8;                 // 0: T1 (f1 slab totals), 1: T2
                 const int q = (item % q8) * 8 + warp;
                 if (q < S) {                                  // warp-uniform
-                    const size_t row = (size_t)(which * S + q) * S;
+                    const float2* row = rs + (size_t)(which * S + q) * S;
                     DF acc{0.f, 0.f};
-                    for (int t = lane; t < S; t += 32) acc = df_add(acc, df_ld(rs[row + t]));
+                    for (int t0 = 0; t0 < S; t0 += 8 * 32) {
+                        float2 v[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const int t = t0 + u * 32 + lane;
+                            v[u] = t < S ? row[t] : make_float2(0.f, 0.f);
+                        }
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) acc = df_add(acc, df_ld(v[u]));
+                    }
                     acc = warp_sum_df(acc);
                     if (lane == 0) I.vec2[which * S + q] = df_st(acc);
                 }
             } else {
                 const int it2 = item - 2 * q8;
-                const int which = it2 / q32;                 // 0: P1 (over f1 slabs), 1: P2
-                const int q = (it2 % q32) * 32 + lane;
+                const int which = it2 / (q32 * np);          // 0: P1 (over f1 slabs), 1: P2
+                const int rem = it2 - which * q32 * np;
+                const int part = rem / q32;                  // row block
+                const int q = (rem - part * q32) * 32 + lane;
+                const int t0 = part * kVecRows + warp * kRW;
+                float2 v[kRW];
+#pragma unroll
+                for (int u = 0; u < kRW; ++u) {
+                    const int t = t0 + u;
+                    v[u] = (q < S && t < S) ? rs[(size_t)(which * S + t) * S + q] : make_float2(0.f, 0.f);
+                }
                 DF acc{0.f, 0.f};
-                if (q < S)
-                    for (int t = warp; t < S; t += kW) acc = df_add(acc, df_ld(rs[(size_t)(which * S + t) * S + q]));
+#pragma unroll
+                for (int u = 0; u < kRW; ++u) acc = df_add(acc, df_ld(v[u]));
                 s_p[threadIdx.x] = df_st(acc);
                 __syncthreads();
                 if (warp == 0 && q < S) {
                     DF tot = df_ld(s_p[lane]);
                     for (int w = 1; w < kW; ++w) tot = df_add(tot, df_ld(s_p[w * 32 + lane]));
-                    I.vec2[(2 + which) * S + q] = df_st(tot);
+                    I.vec2[2 * S + ((size_t)which * np + part) * S + q] = df_st(tot);
                 }
             }
         }
@@ -622,11 +662,32 @@ __global__ void __launch_bounds__(kThreads) k_vec32(const WorkDev* __restrict__ 
     }
 }
 
-// Scalars of Prop. 3 shared by a CTA (formed by thread 0).
-struct AlphaK {
-    DF is, in, im, imn, imin, iw, dl, sumd, isim, isin, fix;
-    DF cst, dsiw, tin, yasum, T3in;
+// Inputs of this thread's first entries of a slab (row entry e = tid and
+// column entry e = tid), loaded together with the instance-wide vectors so
+// that a slab costs one round trip of loads.
+struct AlphaIn {
+    float2 ra, rb;        // row sums of u + d: f2 slab k row j, f1 slab j row k
+    float2 a0r, a0c;      // anchor pieces of the row and the column entry
+    float2 k2, mu;        // column anchor constant and (check) the marginal
+    float kd;             // column total of the delta over the bands
 };
+__device__ __forceinline__ AlphaIn alpha_in(const HotInst& I, int slab, int e, bool check) {
+    const int S = I.S, nb = I.nb;
+    AlphaIn a;
+    const bool f1 = slab < S;
+    const int j = f1 ? slab : e, k = f1 ? e : slab - S;
+    a.ra = I.rs2[(size_t)(S + k) * S + j];
+    a.rb = I.rs2[(size_t)j * S + k];
+    const size_t o = (size_t)slab * 2 * S;
+    a.a0r = I.ab0_32[o + e];
+    a.a0c = I.ab0_32[o + S + e];
+    a.k2 = I.K2[(size_t)slab * S + e];
+    a.mu = check ? (f1 ? I.mu1f[(size_t)e * S + slab] : I.mu2f[(size_t)(slab - S) * S + e]) : make_float2(0.f, 0.f);
+    float kd = 0.f;
+    for (int b = 0; b < nb; ++b) kd += I.cs32[((size_t)slab * nb + b) * S + e];
+    a.kd = kd;
+    return a;
+}
 
 // The instance-wide O(S) stage: from T1, T2, P1, P2 (k_vec32) the vectors
 //   mvA_q = a_q/n - (1/m + 1/n) bb_q      (column part of y1-hat)
@@ -636,36 +697,52 @@ struct AlphaK {
 // into sq[0..3][q].  With e_q = rowR1_q + r3_q and d the diagonal of W-hat,
 // every global scalar follows from four sums: sum a, sum bb, T3 = sum r3 and
 // sum d_q e_q, since s_q = (e_q + cst)/(m+n) with
-// cst = sum a/n - (1/m+1/n) sum bb + T3/n.
-__device__ void alpha32_stage(const HotInst& I, float2 (*sq)[kMaxS], float2* s_red, AlphaK& K) {
+// cst = sum a/n - (1/m+1/n) sum bb + T3/n.  Each thread forms the scalars
+// from the block sums itself (no single-thread section, no extra barrier).
+struct StageIn {
+    float2 T1, T2, P1, P2, cm, rm;   // q = threadIdx.x (P1, P2: first row-block partial)
+    float kdl;                        // thread S-1: delta column total at the dropped (m, n) entry
+};
+__device__ __forceinline__ StageIn stage_in(const HotInst& I, int q) {
     const int S = I.S, nb = I.nb;
-    if (threadIdx.x == 0) {
-        const CycleK& C = *I.cyc;
-        K.is = df_ld(C.is);
-        K.in = df_ld(C.in);
-        K.im = df_ld(C.im);
-        K.imn = df_ld(C.imn);
-        K.imin = df_ld(C.imin);
-        K.iw = df_ld(C.iw);
-        K.dl = df_ld(C.dl);
-        K.sumd = df_ld(C.sumd);
-        K.isim = df_ld(C.isim);
-        K.isin = df_ld(C.isin);
-        // the dropped (m, n) row of eq. (7): column S-1 of the last f2 slab
-        float kd = 0.f;
-        for (int b = 0; b < nb; ++b) kd += I.cs32[((size_t)(2 * S - 1) * nb + b) * S + (S - 1)];
-        K.fix = df_mul(df_add(df_ld(C.mk), -kd), K.is);
-    }
-    __syncthreads();
-    const DF is = K.is, fix = K.fix, im = K.im, dl = K.dl;
     const float2* __restrict__ v = I.vec2;
+    const int np = (S + kVecRows - 1) / kVecRows;
+    StageIn s;
+    s.T1 = v[q];
+    s.T2 = v[S + q];
+    s.P1 = v[2 * S + q];
+    s.P2 = v[2 * S + (size_t)np * S + q];
+    s.cm = I.cm2[q];
+    s.rm = I.rm2[q];
+    s.kdl = 0.f;
+    if (q == S - 1)
+        for (int b = 0; b < nb; ++b) s.kdl += I.cs32[((size_t)(2 * S - 1) * nb + b) * S + (S - 1)];
+    return s;
+}
+
+// The cycle constants are read where they are used (L1 broadcasts) rather
+// than held in registers.
+__device__ void alpha32_stage(const HotInst& I, const StageIn& pre, float2 (*sq)[kMaxS], float2* s_red) {
+    const int S = I.S;
+    const CycleK& C = *I.cyc;
+    const float2* __restrict__ v = I.vec2;
+    const int np = (S + kVecRows - 1) / kVecRows;
+    const DF is = df_ld(C.is), im = df_ld(C.im), dl = df_ld(C.dl);
+    const DF mk = df_ld(C.mk);
     DF red[4] = {DF{0.f, 0.f}, DF{0.f, 0.f}, DF{0.f, 0.f}, DF{0.f, 0.f}};
     for (int q = threadIdx.x; q < S; q += blockDim.x) {
-        const DF T1 = df_ld(v[q]), T2 = df_ld(v[S + q]), P1 = df_ld(v[2 * S + q]), P2 = df_ld(v[3 * S + q]);
+        const StageIn s = q == (int)threadIdx.x ? pre : stage_in(I, q);
+        const DF T1 = df_ld(s.T1), T2 = df_ld(s.T2);
+        DF P1 = df_ld(s.P1), P2 = df_ld(s.P2);
+        for (int b = 1; b < np; ++b) {
+            P1 = df_add(P1, df_ld(v[2 * S + (size_t)b * S + q]));
+            P2 = df_add(P2, df_ld(v[2 * S + (size_t)(np + b) * S + q]));
+        }
         const DF A = df_mul(df_sub(P2, T1), is);                     // a_q = -(T1 - P2)/sigma
-        const DF B = df_mul(df_sub(df_ld(I.cm2[q]), T1), is);         // bb_q
-        DF R3 = df_mul(df_sub(df_ld(I.rm2[q]), T2), is);              // r3_q
-        if (q == S - 1) R3 = df_sub(R3, fix);
+        const DF B = df_mul(df_sub(df_ld(s.cm), T1), is);             // bb_q
+        DF R3 = df_mul(df_sub(df_ld(s.rm), T2), is);                  // r3_q
+        // the dropped (m, n) row of eq. (7): column S-1 of the last f2 slab
+        if (q == S - 1) R3 = df_sub(R3, df_mul(df_add(mk, -s.kdl), is));
         const DF e = df_add(df_mul(df_sub(T2, P1), is), R3);          // rowR1_q + r3_q
         sq[0][q] = df_st(A);
         sq[1][q] = df_st(B);
@@ -676,23 +753,17 @@ __device__ void alpha32_stage(const HotInst& I, float2 (*sq)[kMaxS], float2* s_r
         red[2] = df_add(red[2], R3);
         red[3] = df_add(red[3], df_mul(e, q == S - 1 ? dl : im));
     }
-    block_sum_df<4>(red, s_red);
-    if (threadIdx.x == 0) {
-        const DF T3 = red[2];
-        const DF cst = df_add(df_sub(df_mul(red[0], K.in), df_mul(red[1], K.imin)), df_mul(T3, K.in));
-        const DF ds = df_mul(df_add(red[3], df_mul(cst, K.sumd)), K.imn);      // sum d_q s_q
-        const DF dsiw = df_mul(ds, K.iw);
-        const DF tsum = df_neg(df_add(ds, df_mul(dsiw, K.sumd)));              // 1^T W-hat s
-        const DF tin = df_mul(tsum, K.in);
-        K.cst = cst;
-        K.dsiw = dsiw;
-        K.tin = tin;
-        K.yasum = df_add(tsum, df_mul(tin, (float)S));                         // 1^T y1a
-        K.T3in = df_mul(T3, K.in);
-    }
-    __syncthreads();
-    const DF in = K.in, imn = K.imn, imin = K.imin, cst = K.cst, dsiw = K.dsiw, tin = K.tin;
-    const DF yasum = K.yasum, T3in = K.T3in;
+    block_sum_df<4>(red, s_red);                 // ends with a barrier: sq is published too
+    const DF in = df_ld(C.in), imn = df_ld(C.imn), imin = df_ld(C.imin);
+    const DF T3 = red[2];
+    const DF cst = df_add(df_sub(df_mul(red[0], in), df_mul(red[1], imin)), df_mul(T3, in));
+    const DF sumd = df_ld(C.sumd);
+    const DF ds = df_mul(df_add(red[3], df_mul(cst, sumd)), imn);          // sum d_q s_q
+    const DF dsiw = df_mul(ds, df_ld(C.iw));
+    const DF tsum = df_neg(df_add(ds, df_mul(dsiw, sumd)));                // 1^T W-hat s
+    const DF tin = df_mul(tsum, in);
+    const DF yasum = df_add(tsum, df_mul(tin, (float)S));                  // 1^T y1a
+    const DF T3in = df_mul(T3, in);
     const DF T3in2 = df_mul(T3in, in);
     const float mpn = (float)(2 * S);
     for (int q = threadIdx.x; q < S; q += blockDim.x) {
@@ -712,107 +783,100 @@ __device__ void alpha32_stage(const HotInst& I, float2 (*sq)[kMaxS], float2* s_r
 // and max |A^T y| pieces.  Slabs are taken in contiguous runs per CTA so that
 // the instance-wide stage is formed once per instance and CTA.
 template <bool CHECK>
-__global__ void __launch_bounds__(kThreads) k_alpha32(const WorkDev* __restrict__ W, int j) {
+__global__ void __launch_bounds__(kThreads, 3) k_alpha32(const WorkDev* __restrict__ W, int j) {
+    pdl_begin();
     __shared__ float2 sq[4][kMaxS];
     __shared__ float2 s_red[4 * 32];
     __shared__ float s_max[32];
-    __shared__ AlphaK K;
-    __shared__ int s_t[4];
     const int ninst = W->ninst;
     const int nslab = W->pre_slab[ninst];
     const int chunk = (nslab + gridDim.x - 1) / gridDim.x;
     const int t0 = blockIdx.x * chunk, t1 = min(nslab, t0 + chunk);
+    const int tid = threadIdx.x;
     int cached = -1;
     for (int t = t0; t < t1; ++t) {
-        if (threadIdx.x == 0) {
-            const int i = find_inst(W->pre_slab, ninst, t);
-            s_t[0] = i;
-            s_t[1] = t - W->pre_slab[i];
-            s_t[2] = W->inst[i].ctl->status;
+        // every thread resolves the slab itself (uniform, no barrier)
+        const int inst = find_inst(W->pre_slab, ninst, t);
+        const HotInst& I = W->inst[inst];
+        if (I.ctl->status != ST_RUNNING) continue;
+        const int slab = t - W->pre_slab[inst];
+        const int S = I.S;
+        // one round of loads: this thread's first entries, the cycle
+        // constants and (for a new instance) the stage inputs
+        const bool have = tid < S;
+        AlphaIn pin{};
+        if (have) pin = alpha_in(I, slab, tid, CHECK);
+        const CycleK& C = *I.cyc;
+        if (inst != cached) {
+            StageIn sin{};
+            if (have) sin = stage_in(I, tid);
+            alpha32_stage(I, sin, sq, s_red);
+            cached = inst;
         }
-        __syncthreads();
-        if (s_t[2] != ST_RUNNING) {
-            __syncthreads();
-            continue;
-        }
-        const HotInst& I = W->inst[s_t[0]];
-        if (s_t[0] != cached) {                          // block-uniform
-            alpha32_stage(I, sq, s_red, K);
-            cached = s_t[0];
-        }
-        const int slab = s_t[1];
-        const int S = I.S, nb = I.nb;
-        if (slab == 0 && threadIdx.x == 0) *I.p32 = make_p32(I.ctl->sigma, I.ctl->k + j, I.h, I.gadmm, I.relax);
-        const DF is = K.is, imn = K.imn;
-        const float2* __restrict__ rs = I.rs2;             // row sums of u + d
-        const float2* __restrict__ K2 = I.K2 + (size_t)slab * S;
+        if (slab == 0 && tid == 0) *I.p32 = make_p32(I.ctl->sigma, I.ctl->k + j, I.h, I.gadmm, I.relax);
+        const DF is = df_ld(C.is), imn = df_ld(C.imn);
         const size_t o = (size_t)slab * 2 * S;
-        const float grid = (float)(1.0 / I.h), igrid = (float)I.h;
+        const float igrid = (float)I.h, grid = 1.0f / igrid;       // powers of two: exact
         float ymax = 0.f;
         DF dob{0.f, 0.f};
+        // <c, A^T(y-bar - y0)> of the slab: the cost is separable, so it is
+        // sum_r dalpha_r C(r) + sum_c dbeta_c C(c), C(x) = sum_{y<S} (x - y)^2
+        DF cdd{0.f, 0.f};
+        auto costsum = [&](int x) -> DF {
+            const long long Sx = S, X = x;
+            const long long C = Sx * X * X - X * Sx * (Sx - 1) + (Sx - 1) * Sx * (2 * Sx - 1) / 6;
+            const float hi = (float)C;
+            return DF{hi, (float)(C - (long long)hi)};
+        };
         // idx < S: alpha (row) entries, idx >= S: beta (column) entries; returns the full piece on check iterations
-        auto put = [&](int idx, DF dv) -> DF {
+        auto put = [&](int idx, DF dv, float2 a0) -> DF {
             I.dab2[o + idx] = df_st(dv);
             const float df = df_f(dv);
             const float dh = rintf(df * grid) * igrid;          // on the grid 2^-E
-            const float2 a0 = I.ab0_32[o + idx];
             I.ab32[o + idx] = make_float4(a0.x + dh, a0.y + (df - dh), df, 0.f);
             DF full{0.f, 0.f};
             if (CHECK) {
                 full = df_add(DF{a0.x, a0.y}, dv);
                 ymax = fmaxf(ymax, fabsf(full.hi));
+                cdd = df_add(cdd, df_mul(dv, costsum(idx < S ? idx : idx - S)));
             }
             return full;
         };
-        auto kap_delta = [&](int c) -> float {                 // column total of the delta over the bands
-            float k = 0.f;
-            for (int b = 0; b < nb; ++b) k += I.cs32[((size_t)slab * nb + b) * S + c];
-            return k;
-        };
-        if (slab < S) {
-            const int j = slab;
-            const DF colj = df_ld(sq[0][j]);
-            for (int k = threadIdx.x; k < S; k += blockDim.x) {
-                // R1(k, j) = -(rowsum f1 slab j - rowsum f2 slab k)/sigma
-                const DF R1 = df_mul(df_sub(df_ld(rs[(size_t)(S + k) * S + j]), df_ld(rs[(size_t)j * S + k])), is);
-                put(k, df_mul(df_add(df_add(R1, colj), df_ld(sq[1][k])), imn));     // y1(k, j)
+        const bool f1 = slab < S;
+        // row entries: f1 slab j gives y1(k, j) for every k, f2 slab k gives -y1(k, j) for every j
+        const DF fixed_row = f1 ? df_ld(sq[0][slab]) : df_ld(sq[1][slab - S]);
+        for (int e = tid; e < S; e += kThreads) {
+            const AlphaIn a = e == tid ? pin : alpha_in(I, slab, e, CHECK);
+            // R1(k, j) = -(rowsum f1 slab j - rowsum f2 slab k)/sigma
+            const DF R1 = df_mul(df_sub(df_ld(a.ra), df_ld(a.rb)), is);
+            const DF other = f1 ? df_ld(sq[1][e]) : df_ld(sq[0][e]);
+            const DF y1 = df_mul(df_add(df_add(R1, fixed_row), other), imn);
+            put(e, f1 ? y1 : df_neg(y1), a.a0r);
+        }
+        // column entries: y2(i, j) on f1 slab j, y3(k, l) on f2 slab k (y3(m, n) = 0)
+        const DF colc = f1 ? df_mul(df_ld(sq[2][slab]), df_neg(df_ld(C.im))) : df_mul(df_ld(sq[3][slab - S]), df_ld(C.in));
+        const DF isc = f1 ? df_ld(C.isim) : df_ld(C.isin);
+        for (int e = tid; e < S; e += kThreads) {
+            const AlphaIn a = e == tid ? pin : alpha_in(I, slab, e, CHECK);
+            if (!f1 && slab == 2 * S - 1 && e == S - 1) {
+                put(S + e, DF{0.f, 0.f}, a.a0c);
+                continue;
             }
-            const DF sy_im = df_mul(df_ld(sq[2][j]), K.im);
-            const DF isim = K.isim;
-            for (int i = threadIdx.x; i < S; i += blockDim.x) {
-                const DF dv = df_sub(df_sub(df_ld(K2[i]), df_mul(isim, kap_delta(i))), sy_im);   // y2(i, j)
-                const DF full = put(S + i, dv);
-                if (CHECK) dob = df_add(dob, df_mul(df_ld(I.mu1f[(size_t)i * S + j]), full));
-            }
-        } else {
-            const int k = slab - S;
-            const DF rowk = df_ld(sq[1][k]);
-            for (int j = threadIdx.x; j < S; j += blockDim.x) {
-                const DF R1 = df_mul(df_sub(df_ld(rs[(size_t)(S + k) * S + j]), df_ld(rs[(size_t)j * S + k])), is);
-                put(j, df_neg(df_mul(df_add(df_add(R1, df_ld(sq[0][j])), rowk), imn)));   // -y1(k, j)
-            }
-            const DF sp_in = df_mul(df_ld(sq[3][k]), K.in);
-            const DF isin = K.isin;
-            for (int l = threadIdx.x; l < S; l += blockDim.x) {
-                if (k == S - 1 && l == S - 1) {
-                    put(S + l, DF{0.f, 0.f});                   // no row: y3(m, n) = 0
-                    continue;
-                }
-                const DF dv = df_add(df_sub(df_ld(K2[l]), df_mul(isin, kap_delta(l))), sp_in);   // y3(k, l)
-                const DF full = put(S + l, dv);
-                if (CHECK) dob = df_add(dob, df_mul(df_ld(I.mu2f[(size_t)k * S + l]), full));
-            }
+            const DF dv = df_add(df_sub(df_ld(a.k2), df_mul(isc, a.kd)), colc);
+            const DF full = put(S + e, dv, a.a0c);
+            if (CHECK) dob = df_add(dob, df_mul(df_ld(a.mu), full));
         }
         if (CHECK) {
-            DF red[1] = {dob};
-            block_sum_df<1>(red, s_red);
+            DF red[2] = {dob, cdd};
+            block_sum_df<2>(red, s_red);
             const float bm = block_max(ymax, s_max);
-            if (threadIdx.x == 0) {
+            if (tid == 0) {
                 I.dobj_part[slab] = df_val(red[0]);
+                I.cD_part[slab] = df_val(red[1]);
                 atomicMax(&I.ctl->ymax_bits, __float_as_uint(bm));
             }
         }
-        __syncthreads();
+        __syncthreads();           // sq may be rewritten for the next slab's instance
     }
 }
 
@@ -864,6 +928,7 @@ __device__ __forceinline__ void anchor_slab(const HotInst& I, int slab, double s
 }
 
 __global__ void __launch_bounds__(kThreads) k_anchor(const WorkDev* __restrict__ W) {
+    pdl_begin();
     __shared__ int s_t[4];
     const int ninst = W->ninst;
     const int nslab = W->pre_slab[ninst];
@@ -894,6 +959,7 @@ __global__ void __launch_bounds__(kThreads) k_anchor_one(HotInst I, double sigma
 // FP64 mode: Steps 2-4 of Algorithm 2 on one tile (TR rows of one slab) per
 // loop trip.
 __global__ void __launch_bounds__(kThreads, 2) k_sweep64(const WorkDev* __restrict__ W, int j, int check) {
+    pdl_begin();
     constexpr int NV = 2;
     constexpr int kRowN = kRowSmemBytes / sizeof(double) + 256;
     __shared__ __align__(16) double s_row[kRowN];
@@ -1043,6 +1109,7 @@ __device__ __forceinline__ TileD tile_desc(const WorkDev* __restrict__ W, int t,
 
 template <bool CHECK>
 __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkDev* __restrict__ W, int j) {
+    pdl_begin();
     constexpr int NV = 4;
     constexpr int kW = kThreads / 32;
     constexpr int kRowN = kRowSmemBytes / sizeof(float) + 256;
@@ -1170,8 +1237,10 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkD
 #pragma unroll
         for (int e = 0; e < NV; ++e) cacc[e] = xacc[e] = 0.f;
         // KKT partials: FP32 chains of at most 64 terms per thread and tile
-        // (a tile has TR * S / 1024 <= 16 passes), summed over the CTA in pairs
+        // (a tile has TR * S / 1024 <= 16 passes), summed over the CTA in pairs;
+        // the objective's share <c, d> (k32[4] unused) as exact products in a pair
         float k32[kNK] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        DF cd{0.f, 0.f};
         int rr = ro;                              // this thread's row, relative to r0
 #pragma unroll 1
         for (int q = 0; q < dc.npass; ++q, ++n) {
@@ -1208,7 +1277,8 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkD
                         k32[1] = fmaf(mn, mn, k32[1]);
                         k32[2] = fmaf(xb, xb, k32[2]);
                         k32[3] = fmaf(zb, zb, k32[3]);
-                        k32[4] = fmaf(dcol * dcol, xb, k32[4]);
+                        const float cq = dcol * dcol, pd = cq * dd[e];
+                        cd = df_add(cd, DF{pd, fmaf(cq, dd[e], -pd)});
                         xacc[e] += xb;
                     }
                     cacc[e] += out[e];
@@ -1262,7 +1332,8 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkD
         if constexpr (CHECK) {
             DF kd[kNK];
 #pragma unroll
-            for (int qq = 0; qq < kNK; ++qq) kd[qq] = DF{k32[qq], 0.f};
+            for (int qq = 0; qq < kNK - 1; ++qq) kd[qq] = DF{k32[qq], 0.f};
+            kd[kNK - 1] = cd;
             block_sum_df<kNK>(kd, s_red);        // its barriers also publish s_rdf
             if (tid == 0) {
                 double* o = I.tile_kkt + ((size_t)slab * nb + band) * kNK;
@@ -1392,6 +1463,10 @@ __device__ __forceinline__ void restart_tile(const HotInst& I, int slab, int ban
                     if constexpr (F32) {
                         rsf = df_add(rsf, (float)nu_[e]);
                         fcol[e] = df_add(fcol[e], (float)nu_[e]);
+                        // <c, u>: (r-c)^2 u exactly as a pair (the integer cost is exact in FP32)
+                        const float dc = (float)r - (float)(c0 + e), cq = dc * dc;
+                        const float p = cq * (float)nu_[e];
+                        fr[0] = df_add(fr[0], DF{p, fmaf(cq, (float)nu_[e], -p)});
                     } else {
                         rsd += nu_[e];
                         ccol[e] += nu_[e];
@@ -1421,6 +1496,11 @@ __device__ __forceinline__ void restart_tile(const HotInst& I, int slab, int ban
             o[1] = racc[1];
         }
     } else if constexpr (MODE == 1) {
+        if constexpr (F32) {
+            double cu[1] = {racc[0]};                     // df_val(fr[0]): <c, u> of this thread's share
+            block_sum<1>(cu, s_red);
+            if (threadIdx.x == 0) I.cu_part[(size_t)slab * nb + band] = cu[0];
+        }
         __syncthreads();
         if (active)
 #pragma unroll
@@ -1454,6 +1534,7 @@ __device__ __forceinline__ void restart_tile(const HotInst& I, int slab, int ban
 
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kThreads) k_restart(const WorkDev* __restrict__ W) {
+    pdl_begin();
     __shared__ double s_row[MODE == 1 ? kRowSmemBytes / 8 * 2 : 1];
     __shared__ double s_col[MODE == 1 ? kThreads * 4 : 1];
     __shared__ double s_red[2 * 32];
@@ -1488,6 +1569,7 @@ __global__ void __launch_bounds__(kThreads) k_init(HotInst I, double sigma0) {
     constexpr int NV = V::N;
     __shared__ double s_row[kRowSmemBytes / 8 * 2];
     __shared__ double s_col[kThreads * 4];
+    __shared__ double s_red[32];
     const int S = I.S, nb = I.nb, TR = I.TR;
     const int NC = S / NV;
     const int P = kThreads / NC;
@@ -1498,6 +1580,7 @@ __global__ void __launch_bounds__(kThreads) k_init(HotInst I, double sigma0) {
         const int slab = t / nb, band = t % nb;
         const int r0 = band * TR, r1 = min(S, r0 + TR);
         const size_t off = (size_t)slab * S * S;
+        DF cuf{0.f, 0.f};
         double ccol[NV];
         DF fcol[NV];
 #pragma unroll
@@ -1518,6 +1601,8 @@ __global__ void __launch_bounds__(kThreads) k_init(HotInst I, double sigma0) {
                     if constexpr (std::is_same<T, float>::value) {
                         rsf = df_add(rsf, (float)uu[e]);
                         fcol[e] = df_add(fcol[e], (float)uu[e]);
+                        const float cq = (float)(dc * dc), p = cq * (float)uu[e];
+                        cuf = df_add(cuf, DF{p, fmaf(cq, (float)uu[e], -p)});   // <c, u>
                     } else {
                         rs += (double)uu[e];
                         ccol[e] += (double)uu[e];
@@ -1543,6 +1628,11 @@ __global__ void __launch_bounds__(kThreads) k_init(HotInst I, double sigma0) {
         for (int c = threadIdx.x; c < S; c += blockDim.x) I.cs0_part[cbase + c] = sum_f64_strided(s_col + c, P, S);
         for (int rr = threadIdx.x; rr < r1 - r0; rr += blockDim.x)
             I.rs0[(size_t)slab * S + r0 + rr] = sum_f64_strided(s_row + rr * NC, NC, 1);
+        if constexpr (std::is_same<T, float>::value) {
+            double cu[1] = {df_val(cuf)};
+            block_sum<1>(cu, s_red);
+            if (threadIdx.x == 0) I.cu_part[(size_t)slab * nb + band] = cu[0];
+        }
         __syncthreads();
     }
 }
@@ -1550,6 +1640,7 @@ __global__ void __launch_bounds__(kThreads) k_init(HotInst I, double sigma0) {
 // --------------------------------------------------------------- k_kkt1 --
 // Partial sums of ||A x-bar - b||^2 from the x-bar slab sums.
 __global__ void __launch_bounds__(kThreads) k_kkt1(const WorkDev* __restrict__ W) {
+    pdl_begin();
     __shared__ double s_red[32];
     __shared__ int s_t[3];
     const int ninst = W->ninst;
@@ -1599,6 +1690,7 @@ __global__ void __launch_bounds__(kThreads) k_kkt1(const WorkDev* __restrict__ W
 // Stopping rule eq. (kkt_res) and the restart rule, one CTA per instance.
 __global__ void __launch_bounds__(kThreads) k_check(const WorkDev* __restrict__ W, int K, double a1, double a2,
                                                     double a3) {
+    pdl_begin();
     __shared__ double s_red[8 * 32];
     const int ninst = W->ninst;
     for (int i = blockIdx.x; i < ninst; i += gridDim.x) {
@@ -1608,13 +1700,21 @@ __global__ void __launch_bounds__(kThreads) k_check(const WorkDev* __restrict__ 
         const int S = I.S, nb = I.nb;
         const int ntile = 2 * S * nb;
         double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        for (int q = threadIdx.x; q < ntile; q += blockDim.x)
+        for (int q = threadIdx.x; q < ntile; q += blockDim.x) {
             for (int e = 0; e < kNK; ++e) v[e] += I.tile_kkt[(size_t)q * kNK + e];
+            if (!I.fp64) v[7] += I.cu_part[q];
+        }
         for (int q = threadIdx.x; q < I.n_k1; q += blockDim.x) v[5] += I.k1_part[q];
-        for (int q = threadIdx.x; q < 2 * S; q += blockDim.x) v[6] += I.dobj_part[q];
+        for (int q = threadIdx.x; q < 2 * S; q += blockDim.x) {
+            v[6] += I.dobj_part[q];
+            if (!I.fp64) v[4] += C->sigma * I.cD_part[q];
+        }
         block_sum<8>(v, s_red);
         if (threadIdx.x == 0) {
-            const double r2 = v[0], mn2 = v[1], x2 = v[2], z2 = v[3], cx = v[4], ax2 = v[5], dob = v[6];
+            // FP32 mode: <c, x-bar> = <c, u> + <c, d> + sigma <c, A^T(y-bar - y0)>
+            // from exact per-tile and per-slab parts (the per-element x-bar is
+            // rounded where u + d nearly cancels)
+            const double r2 = v[0], mn2 = v[1], x2 = v[2], z2 = v[3], cx = v[4] + v[7], ax2 = v[5], dob = v[6];
             const double scale = 1.0 / I.h;
             const double rel_dual = sqrt(r2) / (1.0 + I.norm_c);
             const double rel_comp = sqrt(mn2) / (1.0 + sqrt(x2) + sqrt(z2));
@@ -1664,8 +1764,9 @@ __global__ void __launch_bounds__(kThreads) k_check(const WorkDev* __restrict__ 
     }
 }
 
-// Sigma update at a restart: sigma <- sqrt(sigma ||x-bar - x_r|| / ||z-bar - z_r||).
+// Sigma update at a restart: sigma <- sqrt(sigma ||x-bar - x_r|| / ||z-bar - z_r||) on the grid 2^(j/16).
 __global__ void __launch_bounds__(kThreads) k_restart_sigma(const WorkDev* __restrict__ W) {
+    pdl_begin();
     __shared__ double s_red[2 * 32];
     const int ninst = W->ninst;
     for (int i = blockIdx.x; i < ninst; i += gridDim.x) {
@@ -1685,7 +1786,9 @@ __global__ void __launch_bounds__(kThreads) k_restart_sigma(const WorkDev* __res
             C->dx2 = v[0];
             C->dz2 = v[1];
             C->sigma_old = old;
-            if (dx > 0.0 && dz > 0.0 && isfinite(dx / dz)) C->sigma = sqrt(old * (dx / dz));
+            // geometric mean of the old sigma and the movement ratio, rounded
+            // to the grid 2^(j/16) (so rounding noise in dx, dz does not move it)
+            if (dx > 0.0 && dz > 0.0 && isfinite(dx / dz)) C->sigma = exp2(rint(log2(sqrt(old * (dx / dz))) * 16.0) / 16.0);
             C->k = 0;
             C->r0 = -1.0;
             C->rprev = -1.0;
@@ -1696,6 +1799,7 @@ __global__ void __launch_bounds__(kThreads) k_restart_sigma(const WorkDev* __res
 }
 
 __global__ void k_block_end(const WorkDev* __restrict__ W) {
+    pdl_begin();
     const int ninst = W->ninst;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ninst; i += gridDim.x * blockDim.x) {
         HotCtl* C = W->inst[i].ctl;
@@ -1735,6 +1839,7 @@ LaunchDims make_launch_dims(int device, int fp64) {
     }
     d.grid_k1 = sms * 2;
     d.grid_inst = sms * 2;
+    d.pdl = 0;
     return d;
 }
 
@@ -1768,26 +1873,42 @@ cudaError_t kernels_init(int device) {
     return e;
 }
 
+// One launch of the chain: programmatic stream serialisation when ld.pdl is
+// set (graph capture), a plain launch otherwise (profiled mode, where events
+// sit between the kernels).
+template <typename... KArgs, typename... Args>
+static void launch(const LaunchDims& ld, void (*k)(KArgs...), int grid, size_t smem, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = ld.pdl ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 void launch_solve_kernels(const WorkDev* w, const LaunchDims& ld, int fp64, int j, bool check, cudaStream_t st) {
     if (fp64) {
-        k_vec<<<ld.grid_vec, kThreads, 0, st>>>(w);
-        k_marg<<<ld.grid_inst, kThreads, 7 * kMaxS * 8, st>>>(w);
-        if (check) k_alpha<true><<<ld.grid_slab, kThreads, 0, st>>>(w);
-        else k_alpha<false><<<ld.grid_slab, kThreads, 0, st>>>(w);
+        launch(ld, k_vec, ld.grid_vec, 0, st, w);
+        launch(ld, k_marg, ld.grid_inst, 7 * kMaxS * 8, st, w);
+        launch(ld, check ? k_alpha<true> : k_alpha<false>, ld.grid_slab, 0, st, w);
     } else {
-        k_vec32<<<ld.grid_vec, kThreads, 0, st>>>(w);
-        if (check) k_alpha32<true><<<ld.grid_slab, kThreads, 0, st>>>(w, j);
-        else k_alpha32<false><<<ld.grid_slab, kThreads, 0, st>>>(w, j);
+        launch(ld, k_vec32, ld.grid_vec, 0, st, w);
+        launch(ld, check ? k_alpha32<true> : k_alpha32<false>, ld.grid_slab, 0, st, w, j);
     }
 }
 
 void launch_sweep(const WorkDev* w, const LaunchDims& ld, int fp64, int j, bool check, cudaStream_t st) {
-    if (fp64) {
-        k_sweep64<<<check ? ld.grid_tile_chk : ld.grid_tile, kThreads, 0, st>>>(w, j, check ? 1 : 0);
-    } else {
-        if (check) k_sweep32<true><<<ld.grid_tile_chk, kThreads, kSweepSmemChk, st>>>(w, j);
-        else k_sweep32<false><<<ld.grid_tile, kThreads, kSweepSmem, st>>>(w, j);
-    }
+    if (fp64)
+        launch(ld, k_sweep64, check ? ld.grid_tile_chk : ld.grid_tile, 0, st, w, j, check ? 1 : 0);
+    else if (check)
+        launch(ld, k_sweep32<true>, ld.grid_tile_chk, kSweepSmemChk, st, w, j);
+    else
+        launch(ld, k_sweep32<false>, ld.grid_tile, kSweepSmem, st, w, j);
 }
 
 void launch_iteration(const WorkDev* w, const LaunchDims& ld, int fp64, int j, bool check, cudaStream_t st) {
@@ -1797,22 +1918,22 @@ void launch_iteration(const WorkDev* w, const LaunchDims& ld, int fp64, int j, b
 
 void launch_block_end(const WorkDev* w, const LaunchDims& ld, int fp64, int K, double a1, double a2, double a3,
                       cudaStream_t st) {
-    k_kkt1<<<ld.grid_k1, kThreads, 0, st>>>(w);
-    k_check<<<ld.grid_inst, kThreads, 0, st>>>(w, K, a1, a2, a3);
+    launch(ld, k_kkt1, ld.grid_k1, 0, st, w);
+    launch(ld, k_check, ld.grid_inst, 0, st, w, K, a1, a2, a3);
     if (fp64) {
-        k_restart<double, 0><<<ld.grid_rst, kThreads, 0, st>>>(w);
-        k_restart_sigma<<<ld.grid_inst, kThreads, 0, st>>>(w);
-        k_restart<double, 1><<<ld.grid_rst, kThreads, 0, st>>>(w);
-        k_anchor<<<ld.grid_slab, kThreads, 0, st>>>(w);
-        k_restart<double, 2><<<ld.grid_rst, kThreads, 0, st>>>(w);
+        launch(ld, k_restart<double, 0>, ld.grid_rst, 0, st, w);
+        launch(ld, k_restart_sigma, ld.grid_inst, 0, st, w);
+        launch(ld, k_restart<double, 1>, ld.grid_rst, 0, st, w);
+        launch(ld, k_anchor, ld.grid_slab, 0, st, w);
+        launch(ld, k_restart<double, 2>, ld.grid_rst, 0, st, w);
     } else {
-        k_restart<float, 0><<<ld.grid_rst, kThreads, 0, st>>>(w);
-        k_restart_sigma<<<ld.grid_inst, kThreads, 0, st>>>(w);
-        k_restart<float, 1><<<ld.grid_rst, kThreads, 0, st>>>(w);
-        k_anchor<<<ld.grid_slab, kThreads, 0, st>>>(w);
-        k_restart<float, 2><<<ld.grid_rst, kThreads, 0, st>>>(w);
+        launch(ld, k_restart<float, 0>, ld.grid_rst, 0, st, w);
+        launch(ld, k_restart_sigma, ld.grid_inst, 0, st, w);
+        launch(ld, k_restart<float, 1>, ld.grid_rst, 0, st, w);
+        launch(ld, k_anchor, ld.grid_slab, 0, st, w);
+        launch(ld, k_restart<float, 2>, ld.grid_rst, 0, st, w);
     }
-    k_block_end<<<ld.grid_inst, kThreads, 0, st>>>(w);
+    launch(ld, k_block_end, ld.grid_inst, 0, st, w);
 }
 
 }  // namespace hot

@@ -52,12 +52,18 @@ struct ServeState {
     std::vector<double> lat_ms, queue_ms;
 };
 
-static size_t inst_bytes_estimate(int S, int fp64) {
+static int serve_tile_rows(Ctx* ctx, int S, int fp64) {
+    const int t = tuned_tile_rows(ctx, S, fp64);
+    return t ? t : tile_rows(S, fp64, sweep_grid(fp64));
+}
+
+static size_t inst_bytes_estimate(Ctx* ctx, int S, int fp64) {
     const size_t V = 2ull * S * S * S;
     const size_t big = 5 * (V * (fp64 ? 8 : 4) + 256);
-    const int tr = tile_rows(S, fp64, sweep_grid(fp64));
+    const int tr = serve_tile_rows(ctx, S, fp64);
     const size_t nb = (S + tr - 1) / tr;
-    const size_t small = (size_t)S * S * (8 * 4 + 8 * 4 + 8 * 6 * nb + 8 * 2 + 16) + 1024 * 64;
+    size_t small = (size_t)S * S * (8 * 4 + 8 * 4 + 8 * 6 * nb + 8 * 2 + 16) + 1024 * 64;
+    if (!fp64) small += (size_t)S * S * (112 + 8 * nb);       // double-float arrays of FP32 mode
     return big + small;
 }
 
@@ -105,7 +111,7 @@ static void serve_loop(Ctx* ctx) {
                     finish_req(ctx, s, r, HOT_ECANCELLED);
                     continue;
                 }
-                const size_t need = inst_bytes_estimate(r->pair.S, fp64);
+                const size_t need = inst_bytes_estimate(ctx, r->pair.S, fp64);
                 if (s->in_use + need > s->budget) {
                     if (s->active.empty() && admit.empty() && s->in_use == 0) {
                         // can never fit
@@ -131,7 +137,7 @@ static void serve_loop(Ctx* ctx) {
         for (Req* r : admit) {
             Inst* I = nullptr;
             r->t_admit = Clock::now();
-            const int rc = inst_create(r->pair, fp64, ctx->cfg, r->tol, r->max_iter, 0, s->st, &I);
+            const int rc = inst_create(r->pair, fp64, ctx->cfg, r->tol, r->max_iter, tuned_tile_rows(ctx, r->pair.S, fp64), s->st, &I);
             std::lock_guard<std::mutex> g(s->mu);
             if (rc != HOT_OK) {
                 s->in_use -= std::min(s->in_use, r->bytes);

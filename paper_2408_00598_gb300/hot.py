@@ -135,6 +135,8 @@ def load_library(path=None):
         "hot_forget": (i, [vp, ull]),
         "hot_serve_stats_get": (i, [vp, P(hot_serve_stats)]),
         "hot_barycentric_map": (i, [vp, vp, vp, sz, vp, i, i, vp, vp, i, vp]),
+        "hot_autotune": (i, [vp, i, P(i), P(d)]),
+        "hot_autotune_cache_lookup": (i, [ctypes.c_char_p, ctypes.c_char_p, i, i, P(i), P(d)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -192,6 +194,19 @@ def hot_barycentric_map(src, dst, mass, y, nsrc, out=None, weight=None, stream=N
     if rc != HOT_OK:
         raise _err(lib, None, rc)
     return out, weight
+
+
+def hot_autotune_cache_lookup(path, device, precision, S):
+    """(TR, microseconds per iteration) of an autotune cache entry, or None."""
+    lib = load_library()
+    tr = ctypes.c_int()
+    us = ctypes.c_double()
+    rc = lib.hot_autotune_cache_lookup(path.encode(), device.encode(), precision, S, ctypes.byref(tr), ctypes.byref(us))
+    if rc == HOT_ENOTFOUND:
+        return None
+    if rc != HOT_OK:
+        raise _err(lib, None, rc)
+    return tr.value, us.value
 
 def hot_create(cfg=None):
     lib = load_library()
@@ -417,6 +432,16 @@ class Context:
             self.close()
         except Exception:
             pass
+
+    def autotune(self, S):
+        """Time the candidate tile heights for S x S and keep the fastest: (TR, us per iteration)."""
+        lib = load_library()
+        tr = ctypes.c_int()
+        us = ctypes.c_double()
+        rc = lib.hot_autotune(self.ctx, S, ctypes.byref(tr), ctypes.byref(us))
+        if rc != HOT_OK:
+            raise _err(lib, self.ctx, rc)
+        return tr.value, us.value
 
     def solve(self, mu, nu, tol=1e-6, max_iter=100000):
         return hot_solve(self.ctx, mu, nu, tol, max_iter)
