@@ -407,11 +407,9 @@ int Batch::ensure_graph() {
     if (graph) return HOT_OK;
     if (!cap_stream) HOT_CK(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
     ld = make_launch_dims(device, fp64);
-    LaunchDims lg = ld;
-    lg.pdl = 1;                 // inside the graph the kernels chain programmatically
     HOT_CK(cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal));
-    for (int j = 0; j < K; ++j) launch_iteration(d_work, lg, fp64, j, j == K - 1, cap_stream);
-    launch_block_end(d_work, lg, fp64, K, a1, a2, a3, cap_stream);
+    for (int j = 0; j < K; ++j) launch_iteration(d_work, ld, fp64, j, j == K - 1, cap_stream);
+    launch_block_end(d_work, ld, fp64, K, a1, a2, a3, cap_stream);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(cap_stream, &g);
     if (e != cudaSuccess) {

@@ -175,7 +175,6 @@ struct LaunchDims {
     int grid_vec;
     int grid_k1;
     int grid_inst;
-    int pdl;               // launch with programmatic stream serialisation (graph capture)
 };
 
 // FP64: k_vec, k_marg, k_alpha, k_sweep; FP32 bulk: k_vec32, k_alpha32, k_sweep

@@ -191,19 +191,6 @@ __device__ __forceinline__ void block_sum_df(DF (&v)[NV], float2* sh) {
     __syncthreads();
 }
 
-// ------------------------------------------------- programmatic launches --
-// Every kernel of the iteration and block-end chain is launched with
-// programmatic stream serialisation: its CTAs may be scheduled while the
-// previous kernel drains, and griddepcontrol.wait (a hardware wait, first
-// statement of every such kernel, in every CTA) holds them until that kernel
-// has completed and its writes are visible.  Because every CTA waits before
-// touching memory, completion stays transitive along the chain.  The trigger
-// right after lets the next kernel be scheduled as early as possible.
-__device__ __forceinline__ void pdl_begin() {
-    asm volatile("griddepcontrol.wait;\n" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
-}
-
 // ------------------------------------------------------ per-tile parameters --
 
 struct P64 {
@@ -349,7 +336,6 @@ __device__ __forceinline__ bool resolve_tile(const WorkDev* __restrict__ W, int 
 // P1[k] = sum_j rowsum(f1 slab j)[k], P2[j] = sum_k rowsum(f2 slab k)[j];
 // row sums are those of u + d (the slab sums of u are kept separately).
 __global__ void __launch_bounds__(kThreads) k_vec(const WorkDev* __restrict__ W) {
-    pdl_begin();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ninst = W->ninst;
     const int nitems = W->pre_vec[ninst];
@@ -398,7 +384,6 @@ __global__ void __launch_bounds__(kThreads) k_vec(const WorkDev* __restrict__ W)
 // k_alpha (one CTA per slab) then forms the slab's entries with products only
 // (FP64 division is slow on this part; reciprocals are taken once).
 __global__ void __launch_bounds__(kThreads) k_marg(const WorkDev* __restrict__ W) {
-    pdl_begin();
     extern __shared__ double sv[];                   // 7 * S: T1 T2 P1 P2 colmu1 rowmu2, then s
     __shared__ double s_red[4 * 32];
     const int ninst = W->ninst;
@@ -487,7 +472,6 @@ __global__ void __launch_bounds__(kThreads) k_marg(const WorkDev* __restrict__ W
 // arithmetic on top of the per-cycle split of a0.
 template <bool CHECK>
 __global__ void __launch_bounds__(kThreads) k_alpha(const WorkDev* __restrict__ W) {
-    pdl_begin();
     __shared__ double s_red[4 * 32];
     __shared__ float s_max[32];
     __shared__ int s_t[4];
@@ -592,7 +576,6 @@ __global__ void __launch_bounds__(kThreads) k_alpha(const WorkDev* __restrict__ 
 constexpr int kVecRows = 64;
 
 __global__ void __launch_bounds__(kThreads) k_vec32(const WorkDev* __restrict__ W) {
-    pdl_begin();
     constexpr int kW = kThreads / 32;
     constexpr int kRW = kVecRows / kW;               // rows per warp in a P item
     __shared__ float2 s_p[kThreads];
@@ -784,7 +767,6 @@ __device__ void alpha32_stage(const HotInst& I, const StageIn& pre, float2 (*sq)
 // the instance-wide stage is formed once per instance and CTA.
 template <bool CHECK>
 __global__ void __launch_bounds__(kThreads, 3) k_alpha32(const WorkDev* __restrict__ W, int j) {
-    pdl_begin();
     __shared__ float2 sq[4][kMaxS];
     __shared__ float2 s_red[4 * 32];
     __shared__ float s_max[32];
@@ -928,7 +910,6 @@ __device__ __forceinline__ void anchor_slab(const HotInst& I, int slab, double s
 }
 
 __global__ void __launch_bounds__(kThreads) k_anchor(const WorkDev* __restrict__ W) {
-    pdl_begin();
     __shared__ int s_t[4];
     const int ninst = W->ninst;
     const int nslab = W->pre_slab[ninst];
@@ -959,7 +940,6 @@ __global__ void __launch_bounds__(kThreads) k_anchor_one(HotInst I, double sigma
 // FP64 mode: Steps 2-4 of Algorithm 2 on one tile (TR rows of one slab) per
 // loop trip.
 __global__ void __launch_bounds__(kThreads, 2) k_sweep64(const WorkDev* __restrict__ W, int j, int check) {
-    pdl_begin();
     constexpr int NV = 2;
     constexpr int kRowN = kRowSmemBytes / sizeof(double) + 256;
     __shared__ __align__(16) double s_row[kRowN];
@@ -1109,7 +1089,6 @@ __device__ __forceinline__ TileD tile_desc(const WorkDev* __restrict__ W, int t,
 
 template <bool CHECK>
 __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkDev* __restrict__ W, int j) {
-    pdl_begin();
     constexpr int NV = 4;
     constexpr int kW = kThreads / 32;
     constexpr int kRowN = kRowSmemBytes / sizeof(float) + 256;
@@ -1534,7 +1513,6 @@ __device__ __forceinline__ void restart_tile(const HotInst& I, int slab, int ban
 
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kThreads) k_restart(const WorkDev* __restrict__ W) {
-    pdl_begin();
     __shared__ double s_row[MODE == 1 ? kRowSmemBytes / 8 * 2 : 1];
     __shared__ double s_col[MODE == 1 ? kThreads * 4 : 1];
     __shared__ double s_red[2 * 32];
@@ -1640,7 +1618,6 @@ __global__ void __launch_bounds__(kThreads) k_init(HotInst I, double sigma0) {
 // --------------------------------------------------------------- k_kkt1 --
 // Partial sums of ||A x-bar - b||^2 from the x-bar slab sums.
 __global__ void __launch_bounds__(kThreads) k_kkt1(const WorkDev* __restrict__ W) {
-    pdl_begin();
     __shared__ double s_red[32];
     __shared__ int s_t[3];
     const int ninst = W->ninst;
@@ -1690,7 +1667,6 @@ __global__ void __launch_bounds__(kThreads) k_kkt1(const WorkDev* __restrict__ W
 // Stopping rule eq. (kkt_res) and the restart rule, one CTA per instance.
 __global__ void __launch_bounds__(kThreads) k_check(const WorkDev* __restrict__ W, int K, double a1, double a2,
                                                     double a3) {
-    pdl_begin();
     __shared__ double s_red[8 * 32];
     const int ninst = W->ninst;
     for (int i = blockIdx.x; i < ninst; i += gridDim.x) {
@@ -1766,7 +1742,6 @@ __global__ void __launch_bounds__(kThreads) k_check(const WorkDev* __restrict__ 
 
 // Sigma update at a restart: sigma <- sqrt(sigma ||x-bar - x_r|| / ||z-bar - z_r||) on the grid 2^(j/16).
 __global__ void __launch_bounds__(kThreads) k_restart_sigma(const WorkDev* __restrict__ W) {
-    pdl_begin();
     __shared__ double s_red[2 * 32];
     const int ninst = W->ninst;
     for (int i = blockIdx.x; i < ninst; i += gridDim.x) {
@@ -1799,7 +1774,6 @@ __global__ void __launch_bounds__(kThreads) k_restart_sigma(const WorkDev* __res
 }
 
 __global__ void k_block_end(const WorkDev* __restrict__ W) {
-    pdl_begin();
     const int ninst = W->ninst;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ninst; i += gridDim.x * blockDim.x) {
         HotCtl* C = W->inst[i].ctl;
@@ -1839,7 +1813,6 @@ LaunchDims make_launch_dims(int device, int fp64) {
     }
     d.grid_k1 = sms * 2;
     d.grid_inst = sms * 2;
-    d.pdl = 0;
     return d;
 }
 
@@ -1873,21 +1846,14 @@ cudaError_t kernels_init(int device) {
     return e;
 }
 
-// One launch of the chain: programmatic stream serialisation when ld.pdl is
-// set (graph capture), a plain launch otherwise (profiled mode, where events
-// sit between the kernels).
+// One launch of the chain (cudaLaunchKernelEx keeps every call site in one form).
 template <typename... KArgs, typename... Args>
-static void launch(const LaunchDims& ld, void (*k)(KArgs...), int grid, size_t smem, cudaStream_t st, Args... args) {
+static void launch(const LaunchDims&, void (*k)(KArgs...), int grid, size_t smem, cudaStream_t st, Args... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(kThreads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = ld.pdl ? 1 : 0;
     cudaLaunchKernelEx(&cfg, k, args...);
 }
 
