@@ -14,10 +14,15 @@
 // negative entries).  In the slab layout both a and b are contiguous rows:
 // a = row k of f1 slab j, b = row j of f2 slab k.
 #include "hot_engine.h"
+#include "hot_df.cuh"
 
 namespace hot {
 
 constexpr int kRecWarps = 8;
+
+// shared memory of one warp in k_recover_df, in floats: a, b (S floats each,
+// padded to an even count) and the pairs A, B (S + 1 each)
+__host__ __device__ constexpr size_t recover_df_words(int S) { return 2 * (size_t)S + (S & 1) + 4 * ((size_t)S + 1); }
 
 template <typename T>
 __device__ __forceinline__ void load_node(const T* __restrict__ x, int S, int k, int j, double* a, double* b,
@@ -141,6 +146,138 @@ __global__ void __launch_bounds__(kRecWarps * 32) k_recover(const T* __restrict_
     }
 }
 
+// FP32 bulk mode: the same node procedure with the prefix sums, comparisons
+// and overlaps of the FP32 flows in double-float pairs (FP64 arithmetic runs
+// at a small fraction of the FP32 rate on this part; a pair holds the sum of
+// FP32 values to about 48 bits, as a running FP64 sum of them does).
+__device__ __forceinline__ bool df_lt(DF a, DF b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+__device__ __forceinline__ DF df_min(DF a, DF b) { return df_lt(b, a) ? b : a; }
+__device__ __forceinline__ DF df_max(DF a, DF b) { return df_lt(a, b) ? b : a; }
+__device__ __forceinline__ bool df_pos(DF a) { return a.hi > 0.f || (a.hi == 0.f && a.lo > 0.f); }
+__device__ __forceinline__ DF df_shfl_up(DF a, int o) {
+    return DF{__shfl_up_sync(0xffffffffu, a.hi, o), __shfl_up_sync(0xffffffffu, a.lo, o)};
+}
+__device__ __forceinline__ DF df_shfl(DF a, int l) {
+    return DF{__shfl_sync(0xffffffffu, a.hi, l), __shfl_sync(0xffffffffu, a.lo, l)};
+}
+
+__device__ __forceinline__ void load_node_df(const float* __restrict__ x, int S, int k, int j, float* a, float* b,
+                                             float2* A, float2* B) {
+    const int lane = threadIdx.x & 31;
+    const float* ra = x + ((size_t)j * S + k) * S;        // f1 slab j, row k
+    const float* rb = x + ((size_t)(S + k) * S + j) * S;  // f2 slab k, row j
+    for (int t = lane; t < S; t += 32) {
+        a[t] = fmaxf(ra[t], 0.f);
+        b[t] = fmaxf(rb[t], 0.f);
+    }
+    __syncwarp();
+    DF ca{0.f, 0.f}, cb{0.f, 0.f};
+    for (int base = 0; base < S; base += 32) {
+        const int t = base + lane;
+        DF sa{t < S ? a[t] : 0.f, 0.f}, sb{t < S ? b[t] : 0.f, 0.f};
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const DF ya = df_shfl_up(sa, o), yb = df_shfl_up(sb, o);
+            if (lane >= o) {
+                sa = df_add(sa, ya);
+                sb = df_add(sb, yb);
+            }
+        }
+        DF ea = df_shfl_up(sa, 1), eb = df_shfl_up(sb, 1);       // exclusive within the chunk
+        if (lane == 0) ea = eb = DF{0.f, 0.f};
+        if (t < S) {
+            A[t] = df_st(df_add(ca, ea));
+            B[t] = df_st(df_add(cb, eb));
+        }
+        ca = df_add(ca, df_shfl(sa, 31));
+        cb = df_add(cb, df_shfl(sb, 31));
+    }
+    if (lane == 0) {
+        A[S] = df_st(ca);
+        B[S] = df_st(cb);
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ int node_source_df(int S, int i, const float2* A, const float2* B, const float* b,
+                                              int32_t* src, int32_t* dst, double* mass, size_t pos, int src_id,
+                                              int node_k) {
+    const DF lo = df_ld(A[i]);
+    const DF hi = df_min(df_ld(A[i + 1]), df_ld(B[S]));
+    if (!df_lt(lo, hi)) return 0;
+    int l0 = 0, l1 = S - 1;                               // first l with B[l+1] > lo
+    while (l0 < l1) {
+        const int mid = (l0 + l1) >> 1;
+        if (df_lt(lo, df_ld(B[mid + 1]))) l1 = mid; else l0 = mid + 1;
+    }
+    int cnt = 0;
+    for (int l = l0; l < S && df_lt(df_ld(B[l]), hi); ++l) {
+        const DF p = df_sub(df_min(hi, df_ld(B[l + 1])), df_max(lo, df_ld(B[l])));
+        if (df_pos(p) && b[l] > 0.f) {
+            if (src) {
+                src[pos + cnt] = src_id;
+                dst[pos + cnt] = node_k * S + l;
+                mass[pos + cnt] = df_val(p);
+            }
+            ++cnt;
+        }
+    }
+    return cnt;
+}
+
+__global__ void __launch_bounds__(kRecWarps * 32) k_recover_df(const float* __restrict__ x, int S, int count_only,
+                                                               int* __restrict__ counts,
+                                                               const long long* __restrict__ offs,
+                                                               int32_t* __restrict__ src, int32_t* __restrict__ dst,
+                                                               double* __restrict__ mass, double* __restrict__ marg1,
+                                                               double* __restrict__ marg2) {
+    extern __shared__ float4 shdf[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nw = blockDim.x >> 5;
+    const size_t per = recover_df_words(S);              // floats per warp
+    float* a = reinterpret_cast<float*>(shdf) + (size_t)warp * per;
+    float* b = a + S;
+    float2* A = reinterpret_cast<float2*>(b + S + (S & 1));
+    float2* B = A + S + 1;
+    const int nodes = S * S;
+    for (int node = blockIdx.x * nw + warp; node < nodes; node += gridDim.x * nw) {
+        const int k = node / S, j = node % S;    // k-major node order
+        load_node_df(x, S, k, j, a, b, A, B);
+        if (count_only) {
+            int c = 0;
+            for (int i = lane; i < S; i += 32) c += node_source_df(S, i, A, B, b, nullptr, nullptr, nullptr, 0, 0, k);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+            if (lane == 0) counts[node] = c;
+            const DF At = df_ld(A[S]), Bt = df_ld(B[S]);
+            for (int t = lane; t < S; t += 32) {
+                DF ra = df_sub(Bt, df_ld(A[t])), rb = df_sub(At, df_ld(B[t]));
+                if (!df_pos(ra)) ra = DF{0.f, 0.f};
+                if (!df_pos(rb)) rb = DF{0.f, 0.f};
+                const DF ga = df_min(DF{a[t], 0.f}, ra), gb = df_min(DF{b[t], 0.f}, rb);
+                if (df_pos(ga)) atomicAdd(&marg1[(size_t)t * S + j], df_val(ga));
+                if (df_pos(gb)) atomicAdd(&marg2[(size_t)k * S + t], df_val(gb));
+            }
+        } else {
+            long long pos = offs[node];
+            for (int base = 0; base < S; base += 32) {
+                const int i = base + lane;
+                int c = 0;
+                if (i < S) c = node_source_df(S, i, A, B, b, nullptr, nullptr, nullptr, 0, 0, k);
+                int incl = c;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                if (i < S && c > 0) node_source_df(S, i, A, B, b, src, dst, mass, (size_t)(pos + incl - c), i * S + j, k);
+                pos += __shfl_sync(0xffffffffu, incl, 31);
+            }
+        }
+        __syncwarp();
+    }
+}
+
 // exclusive scan of `n` ints into long long offsets (single block, chunked)
 __global__ void k_scan(const int* __restrict__ counts, long long* __restrict__ offs, int n,
                        unsigned long long* __restrict__ total) {
@@ -236,12 +373,14 @@ int recover_plan(Ctx* ctx, Inst* I, int32_t* src, int32_t* dst, double* mass, in
     HOT_CK(cudaMallocAsync(&marg, sizeof(double) * 2 * nodes, st));
     HOT_CK(cudaMallocAsync(&l1, sizeof(double) * 2, st));
     HOT_CK(cudaMemsetAsync(marg, 0, sizeof(double) * 2 * nodes, st));
-    // warps per CTA: each holds a, b and their prefix sums (4S + 2 doubles)
-    const int nw = std::max(1, std::min(kRecWarps, (int)((200 * 1024) / ((4 * S + 2) * sizeof(double)))));
-    const size_t shm = (size_t)nw * (4 * S + 2) * sizeof(double);
+    // warps per CTA: each holds a, b and their prefix sums (4S + 2 doubles;
+    // FP32 mode: 2S floats and 2(S + 1) float pairs)
+    const size_t per_warp = I->fp64 ? (4 * (size_t)S + 2) * sizeof(double) : recover_df_words(S) * sizeof(float);
+    const int nw = std::max(1, std::min(kRecWarps, (int)((200 * 1024) / per_warp)));
+    const size_t shm = (size_t)nw * per_warp;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_recover<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_recover_df, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         cudaFuncSetAttribute(k_recover<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr_set = true;
     }
@@ -252,8 +391,8 @@ int recover_plan(Ctx* ctx, Inst* I, int32_t* src, int32_t* dst, double* mass, in
         k_recover<double><<<grid, nw * 32, shm, st>>>((const double*)I->desc.xr, S, 1, counts, nullptr,
                                                               nullptr, nullptr, nullptr, marg, marg + nodes);
     else
-        k_recover<float><<<grid, nw * 32, shm, st>>>((const float*)I->desc.xr, S, 1, counts, nullptr,
-                                                             nullptr, nullptr, nullptr, marg, marg + nodes);
+        k_recover_df<<<grid, nw * 32, shm, st>>>((const float*)I->desc.xr, S, 1, counts, nullptr, nullptr, nullptr,
+                                                 nullptr, marg, marg + nodes);
     HOT_CK(cudaGetLastError());
     k_scan<<<1, 1024, 0, st>>>(counts, offs, nodes, dtot);
     unsigned long long tot = 0;
@@ -283,8 +422,8 @@ int recover_plan(Ctx* ctx, Inst* I, int32_t* src, int32_t* dst, double* mass, in
                 k_recover<double><<<grid, nw * 32, shm, st>>>((const double*)I->desc.xr, S, 0, counts, offs,
                                                                       ds, dd, dm, nullptr, nullptr);
             else
-                k_recover<float><<<grid, nw * 32, shm, st>>>((const float*)I->desc.xr, S, 0, counts, offs,
-                                                                     ds, dd, dm, nullptr, nullptr);
+                k_recover_df<<<grid, nw * 32, shm, st>>>((const float*)I->desc.xr, S, 0, counts, offs, ds, dd, dm,
+                                                         nullptr, nullptr);
             HOT_CK(cudaGetLastError());
             if (space == HOT_SPACE_HOST) {
                 HOT_CK(cudaMemcpyAsync(src, ds, sizeof(int32_t) * tot, cudaMemcpyDeviceToHost, st));
