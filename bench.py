@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=512)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--duration", type=float, default=60.0)
+    ap.add_argument("--max-drain", type=float, default=180.0,
+                    help="serve mode: seconds to wait for the queue after the arrivals stop; the rest is cancelled")
     ap.add_argument("--compare-fp64", action="store_true",
                     help="batch mode: also solve the same pairs one by one in FP64 mode (the plain GPU form)")
     return ap.parse_args()
@@ -427,9 +429,19 @@ def bench_serve(args, dist):
             nxt += rng.exponential(1.0 / args.rate)
         else:
             time.sleep(min(0.001, nxt - now))
+    # drain: wait for the queue at most --max-drain seconds, then cancel what
+    # is left (an offered load above capacity never drains; the run reports
+    # how much of it was served)
     done = 0
+    unserved = 0
+    deadline = t_start + args.duration + args.max_drain
     for t in tickets:
-        st, _ = ctx.wait(t, timeout_ms=-1)
+        left_ms = max(0.0, (deadline - time.perf_counter()) * 1000.0)
+        st, _ = ctx.wait(t, timeout_ms=left_ms)
+        if st in (hot.HOT_PENDING, hot.HOT_TIMEOUT):
+            ctx.cancel(t)
+            st, _ = ctx.wait(t, timeout_ms=-1)
+            unserved += 1
         done += st == hot.HOT_OK
     t_all = time.perf_counter() - t_start
     s = ctx.serve_stats()
@@ -439,7 +451,8 @@ def bench_serve(args, dist):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "Poisson %g req/s for %gs, S in %s" % (args.rate, args.duration, sizes)},
             "p50_ms": s["p50_ms"], "p99_ms": s["p99_ms"], "mean_queue_ms": s["mean_queue_ms"],
-            "completed": s["completed"], "drain_s": round(t_all - args.duration, 2)}
+            "completed": s["completed"], "unserved_cancelled": unserved, "submitted": len(tickets),
+            "drain_s": round(t_all - args.duration, 2)}
 
 
 def main():
