@@ -153,6 +153,19 @@ HOT_API const char *hot_last_error(hot_ctx *ctx);
 HOT_API int hot_solve(hot_ctx *ctx, const double *mu, const double *nu, int m, int n, int space,
               double tol, long long max_iter, hot_result *out);
 
+/* hot_solve on bins with given coordinates (Sec. IV-B, App. E: colour and
+ * point-cloud bins need not sit on a unit grid): the cost of moving mass
+ * from bin (i, j) to bin (k, l) is (xs[i] - xs[k])^2 + (ys[j] - ys[l])^2.
+ *   xs: host, m doubles (coordinates of the row index i, k)
+ *   ys: host, n doubles (coordinates of the column index j, l)
+ *   xs = ys = NULL: the unit grid 0..m-1, 0..n-1 (as hot_solve).
+ * FP32 bulk mode keeps its exact reduced-cost arithmetic only for integer
+ * coordinates: it takes integers in [-2048, 2048] and returns HOT_EINVAL for
+ * others (use HOT_FP64).  The cost is scaled by the power of two
+ * 2^ceil(log2 max c); results are unscaled as for hot_solve. */
+HOT_API int hot_solve_coords(hot_ctx *ctx, const double *mu, const double *nu, int m, int n, int space,
+                             const double *xs, const double *ys, double tol, long long max_iter, hot_result *out);
+
 /* Solve `count` independent pairs in one batched, graph-captured device loop;
  * each pair stops on its own when it converges.  mus[q], nus[q]: host or
  * device (space) arrays of ms[q]*ns[q] doubles.  out: `count` results.

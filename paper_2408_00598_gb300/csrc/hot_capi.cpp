@@ -183,6 +183,29 @@ int hot_solve(hot_ctx* ctx, const double* mu, const double* nu, int m, int n, in
     HOT_GUARD_END
 }
 
+int hot_solve_coords(hot_ctx* ctx, const double* mu, const double* nu, int m, int n, int space, const double* xs,
+                     const double* ys, double tol, long long max_iter, hot_result* out) {
+    HOT_GUARD_BEGIN
+    if (!ctx || !out) {
+        set_error("ctx or out is NULL");
+        return HOT_EINVAL;
+    }
+    if (!(tol >= 0.0) || max_iter <= 0) {
+        set_error("tol must be >= 0 and max_iter > 0");
+        return HOT_EINVAL;
+    }
+    hot::Ctx& x = ctx->impl;
+    std::lock_guard<std::mutex> g(x.mu);
+    HOT_CK(cudaSetDevice(x.device));
+    std::vector<hot::PairHost> pairs(1);
+    const int fp64 = x.cfg.precision == HOT_FP64;
+    int rc = hot::validate_pair(mu, nu, m, n, space, fp64, pairs[0]);
+    if (rc == HOT_OK) rc = hot::set_coordinates(xs, ys, m, n, fp64, pairs[0]);
+    if (rc != HOT_OK) return rc;
+    return hot::run_solve(&x, pairs, tol, max_iter, true, out);
+    HOT_GUARD_END
+}
+
 int hot_solve_profiled(hot_ctx* ctx, const double* mu, const double* nu, int m, int n, int space, double tol,
                        long long max_iter, hot_result* out, hot_kernel_times* kt) {
     HOT_GUARD_BEGIN

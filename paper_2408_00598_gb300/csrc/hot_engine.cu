@@ -37,6 +37,35 @@ int tile_rows(int S, int fp64, int grid) {
     return tr;
 }
 
+int set_coordinates(const double* xs, const double* ys, int m, int n, int fp64, PairHost& out) {
+    out.xs.clear();
+    out.ys.clear();
+    if (!xs && !ys) return HOT_OK;
+    if (!xs || !ys) {
+        set_error("give both coordinate arrays or neither");
+        return HOT_EINVAL;
+    }
+    out.xs.assign(xs, xs + m);
+    out.ys.assign(ys, ys + n);
+    for (int w = 0; w < 2; ++w) {
+        const std::vector<double>& v = w ? out.ys : out.xs;
+        for (double x : v)
+            if (!std::isfinite(x)) {
+                set_error("coordinates must be finite");
+                return HOT_EINVAL;
+            }
+        if (!fp64)
+            for (double x : v)
+                // FP32 mode forms h (x_r - x_c)^2 from x_r^2, x_c^2 and x_r x_c, exact
+                // on the grid 2^-E only for integer coordinates of modest size
+                if (x != std::rint(x) || std::fabs(x) > 2048.0) {
+                    set_error("FP32 bulk mode takes integer coordinates in [-2048, 2048]; use HOT_FP64 for others");
+                    return HOT_EINVAL;
+                }
+    }
+    return HOT_OK;
+}
+
 int validate_pair(const double* mu, const double* nu, int m, int n, int space, int fp64, PairHost& out) {
     if (!mu || !nu) {
         set_error("null histogram pointer");
@@ -152,6 +181,9 @@ int inst_create(const PairHost& p, int fp64, const hot_config& cfg, double tol, 
     const size_t o_cm2 = take(S * F2);
     const size_t o_rm2 = take(S * F2);
     const size_t o_p32 = take(sizeof(P32));
+    const size_t o_X32 = take(2 * (size_t)S * sizeof(float));
+    const size_t o_X64 = take(2 * (size_t)S * sizeof(double));
+    const size_t o_cs2 = take(2 * (size_t)S * sizeof(float2));
     const size_t o_cyc = take(sizeof(CycleK));
     const size_t o_mu1 = take(SS * 8);
     const size_t o_mu2 = take(SS * 8);
@@ -185,19 +217,40 @@ int inst_create(const PairHost& p, int fp64, const hot_config& cfg, double tol, 
     d.stop_abs = cfg.stop_rule == HOT_STOP_ABSOLUTE ? 1 : 0;
     d.relax = cfg.relaxation;
     // power-of-two cost scale: smallest 2^E >= max c = (S-1)^2
-    const double cmax = (double)(S - 1) * (S - 1);
+    // bin coordinates of the two halves: f1 slabs use the row coordinates
+    // (i, k), f2 slabs the column coordinates (j, l); default 0..S-1
+    std::vector<double> X(2 * (size_t)S);
+    for (int r = 0; r < S; ++r) {
+        X[r] = p.xs.empty() ? (double)r : p.xs[r];
+        X[S + r] = p.ys.empty() ? (double)r : p.ys[r];
+    }
+    // power-of-two cost scale: smallest 2^E >= max c (E = 0 for a zero cost)
+    double cmax = 0.0;
+    for (int hlf = 0; hlf < 2; ++hlf) {
+        const auto mm = std::minmax_element(X.begin() + hlf * S, X.begin() + (hlf + 1) * S);
+        cmax = std::max(cmax, (*mm.second - *mm.first) * (*mm.second - *mm.first));
+    }
     int E = 0;
-    while (std::ldexp(1.0, E) < cmax) ++E;
+    if (cmax > 0.0) {
+        E = (int)std::ceil(std::log2(cmax));
+        while (std::ldexp(1.0, E) < cmax) ++E;
+        while (std::ldexp(1.0, E - 1) >= cmax) --E;
+    }
     d.E = E;
     d.h = std::ldexp(1.0, -E);
     I->cost_scale = std::ldexp(1.0, E);
+    // ||c||: every slab of a half has the same cost matrix; C(x) = sum_y (X_x - X_y)^2
     double c4 = 0.0;
-    for (int a = 0; a < S; ++a)
-        for (int t = 0; t < S; ++t) {
-            const double dd = (double)(a - t) * (a - t);
-            c4 += dd * dd;
-        }
-    d.norm_c = d.h * std::sqrt(2.0 * S * c4);
+    std::vector<double> csum(2 * (size_t)S, 0.0);
+    for (int hlf = 0; hlf < 2; ++hlf)
+        for (int a = 0; a < S; ++a)
+            for (int t = 0; t < S; ++t) {
+                const double dx = X[hlf * S + a] - X[hlf * S + t];
+                const double dd = dx * dx;
+                c4 += dd * dd;
+                csum[hlf * S + a] += dd;
+            }
+    d.norm_c = d.h * std::sqrt((double)S * c4);
     double b2 = 0.0;
     for (double x : p.mu1) b2 += x * x;
     for (double x : p.mu2) b2 += x * x;
@@ -247,6 +300,9 @@ int inst_create(const PairHost& p, int fp64, const hot_config& cfg, double tol, 
     d.cm2 = fp64 ? nullptr : (float2*)(sm + o_cm2);
     d.rm2 = fp64 ? nullptr : (float2*)(sm + o_rm2);
     d.p32 = (P32*)(sm + o_p32);
+    d.X32 = (float*)(sm + o_X32);
+    d.X64 = (double*)(sm + o_X64);
+    d.csum2 = (float2*)(sm + o_cs2);
     d.cyc = (CycleK*)(sm + o_cyc);
     d.ctl = (HotCtl*)(sm + o_ctl);
 
@@ -272,6 +328,19 @@ int inst_create(const PairHost& p, int fp64, const hot_config& cfg, double tol, 
     if (ee == cudaSuccess) ee = cudaMemcpyAsync(d.colmu1, cm.data(), S * 8, cudaMemcpyHostToDevice, st);
     if (ee == cudaSuccess) ee = cudaMemcpyAsync(d.rowmu2, rm.data(), S * 8, cudaMemcpyHostToDevice, st);
     if (ee == cudaSuccess) ee = cudaMemcpyAsync(d.ctl, &I->ctl_host, sizeof(HotCtl), cudaMemcpyHostToDevice, st);
+    {
+        // coordinates (FP32 copies are exact: FP32 mode takes integer coordinates)
+        // and the row cost sums C(x) as double-float pairs
+        std::vector<float> x32(X.begin(), X.end());
+        std::vector<float2> cs2(csum.size());
+        for (size_t q = 0; q < csum.size(); ++q) {
+            const float hh = (float)csum[q];
+            cs2[q] = make_float2(hh, (float)(csum[q] - (double)hh));
+        }
+        if (ee == cudaSuccess) ee = cudaMemcpyAsync((void*)d.X32, x32.data(), x32.size() * sizeof(float), cudaMemcpyHostToDevice, st);
+        if (ee == cudaSuccess) ee = cudaMemcpyAsync((void*)d.X64, X.data(), X.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+        if (ee == cudaSuccess) ee = cudaMemcpyAsync((void*)d.csum2, cs2.data(), cs2.size() * sizeof(float2), cudaMemcpyHostToDevice, st);
+    }
     if (!fp64) {
         // (hi, lo) pairs of the marginals: hi = fl32(x), lo = fl32(x - hi)
         auto pairs = [](const double* x, size_t n) {

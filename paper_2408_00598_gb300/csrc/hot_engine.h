@@ -50,7 +50,11 @@ struct Inst {
 struct PairHost {
     int S = 0;
     std::vector<double> mu1, mu2;
+    std::vector<double> xs, ys;            // bin coordinates (row index i/k, column index j/l); empty: 0..S-1
 };
+
+// Checks bin coordinates and stores them in `out` (NULL: uniform 0..S-1).
+int set_coordinates(const double* xs, const double* ys, int m, int n, int fp64, PairHost& out);
 
 int validate_pair(const double* mu, const double* nu, int m, int n, int space, int fp64, PairHost& out);
 // rows per sweep tile; grid: resident CTAs of the sweep (0: no balancing)

@@ -146,6 +146,9 @@ struct HotInst {
     float2* cm2;           // [S] colmu1 as pairs
     float2* rm2;           // [S] rowmu2 as pairs
     P32* p32;              // element constants of the current iteration
+    const float* X32;      // [2S] bin coordinates: rows/columns of f1 slabs, then of f2 slabs
+    const double* X64;     // the same in FP64
+    const float2* csum2;   // [2S] C(x) = sum_y (X_x - X_y)^2 per half, as pairs
     struct CycleK* cyc;    // Prop. 3 constants of the current cycle
     HotCtl* ctl;
 };

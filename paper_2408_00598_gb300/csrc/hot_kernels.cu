@@ -750,14 +750,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_alpha32(const WorkDev* __restri
         float ymax = 0.f;
         DF dob{0.f, 0.f};
         // <c, A^T(y-bar - y0)> of the slab: the cost is separable, so it is
-        // sum_r dalpha_r C(r) + sum_c dbeta_c C(c), C(x) = sum_{y<S} (x - y)^2
+        // sum_r dalpha_r C(r) + sum_c dbeta_c C(c), C(x) = sum_y (X_x - X_y)^2
         DF cdd{0.f, 0.f};
-        auto costsum = [&](int x) -> DF {
-            const long long Sx = S, X = x;
-            const long long C = Sx * X * X - X * Sx * (Sx - 1) + (Sx - 1) * Sx * (2 * Sx - 1) / 6;
-            const float hi = (float)C;
-            return DF{hi, (float)(C - (long long)hi)};
-        };
+        auto costsum = [&](int x) -> DF { return df_ld(I.csum2[(slab < S ? 0 : S) + x]); };
         // idx < S: alpha (row) entries, idx >= S: beta (column) entries; returns the full piece on check iterations
         auto put = [&](int idx, DF dv, float2 a0) -> DF {
             I.dab2[o + idx] = df_st(dv);
@@ -928,17 +923,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep64(const WorkDev* __restri
         const P64 p = s_p64;
         const double* ab = I.ab64 + (size_t)slab * 2 * S;
         const double* dab = I.dab64 + (size_t)slab * 2 * S;
+        const double* X = I.X64 + (slab < S ? 0 : S);          // bin coordinates of this half
         double bb[NV], db[NV], cf[NV];
 #pragma unroll
         for (int e = 0; e < NV; ++e) {
             bb[e] = active ? ab[S + c0 + e] : 0.0;
             db[e] = active ? dab[S + c0 + e] : 0.0;
-            cf[e] = (double)(c0 + e);
+            cf[e] = active ? X[c0 + e] : 0.0;
         }
         if (active) {
             for (int r = r0 + ro; r < r1; r += P) {
                 const double a = ab[r], da = dab[r];
-                const double rf = (double)r;
+                const double rf = X[r];
                 double uu[NV], dd[NV], out[NV], xo[NV];
                 VecT<double>::ld(u + (size_t)r * S + c0, uu);
                 VecT<double>::ld(din + (size_t)r * S + c0, dd);
@@ -1007,10 +1003,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep64(const WorkDev* __restri
 // travel in the group of each tile's first pass into a ring of their own, and
 // thread 0 leaves each tile's descriptor in a third ring for the compute side.
 //
-// The scaled cost is separable, h (r - c)^2 = h r^2 + h c^2 - 2 h r c, so the
-// grid part of the reduced cost is Gh = (A_r + B_c) - 2 h r c with
-// A_r = h r^2 - alpha_hi (per row) and B_c = h c^2 - beta_hi (per column):
-// every term is an integer multiple of 2^-E, so Gh is exact in FP32 as before.
+// The scaled cost is separable, h (x_r - x_c)^2 = h x_r^2 + h x_c^2 - 2 h x_r x_c
+// (x the bin coordinates of the slab's half, integers in FP32 mode), so the
+// grid part of the reduced cost is Gh = (A_r + B_c) - 2 h x_r x_c with
+// A_r = h x_r^2 - alpha_hi (per row) and B_c = h x_c^2 - beta_hi (per column):
+// every term is an integer multiple of 2^-E, so Gh is exact in FP32.
 struct TileD {
     int inst, slab, band, S, NC, P, r0, r1, npass;
 };
@@ -1118,8 +1115,8 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkD
     for (int q = 0; q < kStages - 1; ++q) issue(q);
 
     // ---- compute side
-    // per column of this thread: B_c = h c^2 - beta_hi (exact), beta_lo,
-    // dbeta, c; loaded for the next tile during the current tile's epilogue
+    // per column of this thread: B_c = h x_c^2 - beta_hi (exact), beta_lo,
+    // dbeta, x_c; loaded for the next tile during the current tile's epilogue
     float4 bq[NV];
     P32 p;
     auto load_cols = [&](const TileD& d) {
@@ -1149,9 +1146,10 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkD
         const bool active = ro < P;
         const int c0 = cg * NV;
         const float h = p.h;
+        const float* X = I.X32 + (slab < S ? 0 : S);           // bin coordinates of this half
 #pragma unroll
         for (int e = 0; e < NV; ++e) {
-            const float cf = (float)(c0 + e);
+            const float cf = active ? X[c0 + e] : 0.f;
             bq[e] = make_float4(fmaf(cf * cf, h, -bq[e].x), bq[e].y, bq[e].z, cf);
         }
         const float4* sa = s_alpha[ck % kStages];
@@ -1179,14 +1177,14 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkD
                 const float uu[NV] = {U.x, U.y, U.z, U.w};
                 const float dd[NV] = {D.x, D.y, D.z, D.w};
                 const float4 a = sa[rr];
-                const float rf = (float)(r0 + rr);
-                const float Ar = fmaf(rf * rf, h, -a.x);      // h r^2 - alpha_hi (exact)
+                const float rf = X[r0 + rr];
+                const float Ar = fmaf(rf * rf, h, -a.x);      // h x_r^2 - alpha_hi (exact)
                 const float m2hr = -2.f * h * rf;             // exact
                 float out[NV], xo[NV];
 #pragma unroll
                 for (int e = 0; e < NV; ++e) {
                     const float4 b = bq[e];
-                    const float Gh = fmaf(m2hr, b.w, Ar + b.x);   // h (r-c)^2 - alpha_hi - beta_hi
+                    const float Gh = fmaf(m2hr, b.w, Ar + b.x);   // h (x_r-x_c)^2 - alpha_hi - beta_hi
                     const float Gl = -(a.y + b.y);
                     const float Dv = a.z + b.z;                  // A^T (y-bar - y0)
                     const float s = uu[e] + dd[e];
@@ -1318,6 +1316,7 @@ __device__ __forceinline__ void restart_tile(const HotInst& I, int slab, int ban
     const double sig_old = (MODE == 1) ? I.ctl->sigma_old : I.ctl->sigma;
     const double sig_new = I.ctl->sigma;
     const int c0 = cg * NV;
+    const int xb0 = slab < S ? 0 : S;                // bin coordinates of this slab's half
     // sums that feed later iterations: FP64 (FP64 mode) or double-float (FP32 mode)
     double racc[2] = {0.0, 0.0};
     DF fr[2] = {DF{0.f, 0.f}, DF{0.f, 0.f}};
@@ -1339,7 +1338,7 @@ __device__ __forceinline__ void restart_tile(const HotInst& I, int slab, int ban
                 const float4 a = ab[r];
 #pragma unroll
                 for (int e = 0; e < NV; ++e) {
-                    const float dc = (float)r - (float)(c0 + e);
+                    const float dc = I.X32[xb0 + r] - I.X32[xb0 + c0 + e];
                     const E32 el = elem32(uu[e], dd[e], dc * dc, a, ab[S + c0 + e], p);
                     xz32(el, p, xbv[e], zbv[e]);
                     rv[e] = el.r;
@@ -1351,7 +1350,7 @@ __device__ __forceinline__ void restart_tile(const HotInst& I, int slab, int ban
                 const double a = ab[r], da = dab[r];
 #pragma unroll
                 for (int e = 0; e < NV; ++e) {
-                    const double dc = (double)r - (double)(c0 + e);
+                    const double dc = I.X64[xb0 + r] - I.X64[xb0 + c0 + e];
                     const E64 el = elem64(uu[e], dd[e], dc * dc, a, ab[S + c0 + e], da, dab[S + c0 + e], p);
                     xz64(el, p, xbv[e], zbv[e]);
                     rv[e] = el.r;
@@ -1391,7 +1390,7 @@ __device__ __forceinline__ void restart_tile(const HotInst& I, int slab, int ban
                         rsf = df_add(rsf, (float)nu_[e]);
                         fcol[e] = df_add(fcol[e], (float)nu_[e]);
                         // <c, u>: (r-c)^2 u exactly as a pair (the integer cost is exact in FP32)
-                        const float dc = (float)r - (float)(c0 + e), cq = dc * dc;
+                        const float dc = I.X32[xb0 + r] - I.X32[xb0 + c0 + e], cq = dc * dc;
                         const float p = cq * (float)nu_[e];
                         fr[0] = df_add(fr[0], DF{p, fmaf(cq, (float)nu_[e], -p)});
                     } else {
@@ -1521,7 +1520,8 @@ __global__ void __launch_bounds__(kThreads) k_init(HotInst I, double sigma0) {
                 double rs = 0.0;
 #pragma unroll
                 for (int e = 0; e < NV; ++e) {
-                    const double dc = (double)(r - (c0 + e));
+                    const int xb0 = slab < S ? 0 : S;
+                    const double dc = I.X64[xb0 + r] - I.X64[xb0 + c0 + e];
                     uu[e] = (T)(-sigma0 * (dc * dc * I.h));
                     zero[e] = T(0);
                     if constexpr (std::is_same<T, float>::value) {

@@ -124,6 +124,7 @@ def load_library(path=None):
         "hot_last_error": (ctypes.c_char_p, [vp]),
         "hot_solve": (i, [vp, vp, vp, i, i, i, d, ll, P(hot_result)]),
         "hot_solve_batch": (i, [vp, i, P(vp), P(vp), P(i), P(i), i, d, ll, P(hot_result)]),
+        "hot_solve_coords": (i, [vp, vp, vp, i, i, i, vp, vp, d, ll, P(hot_result)]),
         "hot_solve_profiled": (i, [vp, vp, vp, i, i, i, d, ll, P(hot_result), P(hot_kernel_times)]),
         "hot_get_flows": (i, [vp, ull, vp, i]),
         "hot_recover_plan": (i, [vp, ull, vp, vp, vp, i, sz, P(sz), P(d)]),
@@ -235,6 +236,26 @@ def hot_solve(ctx, mu, nu, tol=1e-6, max_iter=100000):
     m, n = mu.shape
     res = hot_result()
     rc = lib.hot_solve(ctx, pm, pn, m, n, sm, float(tol), int(max_iter), ctypes.byref(res))
+    if rc not in (HOT_OK, HOT_NOT_CONVERGED):
+        raise _err(lib, ctx, rc)
+    return res.to_dict()
+
+
+def hot_solve_coords(ctx, mu, nu, xs, ys, tol=1e-6, max_iter=100000):
+    """hot_solve with bin coordinates xs (rows, m values) and ys (columns, n values)."""
+    lib = load_library()
+    pm, sm, km = _ptr(mu)
+    pn, sn, kn = _ptr(nu)
+    if sm != sn:
+        raise HotError(HOT_EINVAL, "mu and nu must live in the same space")
+    m, n = mu.shape
+    ax = np.ascontiguousarray(xs, dtype=np.float64)
+    ay = np.ascontiguousarray(ys, dtype=np.float64)
+    if ax.shape != (m,) or ay.shape != (n,):
+        raise HotError(HOT_EINVAL, "xs must have m entries and ys n entries")
+    res = hot_result()
+    rc = lib.hot_solve_coords(ctx, pm, pn, m, n, sm, ax.ctypes.data, ay.ctypes.data, float(tol), int(max_iter),
+                              ctypes.byref(res))
     if rc not in (HOT_OK, HOT_NOT_CONVERGED):
         raise _err(lib, ctx, rc)
     return res.to_dict()
@@ -443,7 +464,9 @@ class Context:
             raise _err(lib, self.ctx, rc)
         return tr.value, us.value
 
-    def solve(self, mu, nu, tol=1e-6, max_iter=100000):
+    def solve(self, mu, nu, tol=1e-6, max_iter=100000, xs=None, ys=None):
+        if xs is not None or ys is not None:
+            return hot_solve_coords(self.ctx, mu, nu, xs, ys, tol, max_iter)
         return hot_solve(self.ctx, mu, nu, tol, max_iter)
 
     def solve_profiled(self, mu, nu, tol=1e-6, max_iter=100000):
