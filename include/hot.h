@@ -8,13 +8,15 @@
  * on an m x n grid, each non-negative with total mass 1, cost
  * c_{ij;kl} = (i-k)^2 + (j-l)^2; the library returns the optimal value of
  * eq. (1) computed through the equivalent reduced model eq. (3), and on request
- * the transport plan of Algorithm 1.
+ * the transport plan of Algorithm 1.  Plan entries run from source bin
+ * (i, j), index i*n + j of mu, to target bin (k, l), index k*n + l of nu.
  *
  * Conventions for every entry point:
  *   - histograms are row-major m x n arrays of double: mu[i*n + j] is the mass
  *     of bin (i, j) (row i, column j);
- *   - this version solves square grids, m == n == S, with S a multiple of 4,
- *     8 <= S <= 1024; other shapes return HOT_EINVAL;
+ *   - m and n are multiples of 4 in [8, 1024] (FP64 mode: [8, 512]); m may
+ *     differ from n (the cost along each axis is that axis' own squared
+ *     distance, Sec. II-A); other shapes return HOT_EINVAL;
  *   - a histogram is valid when every entry is finite and >= 0 and its sum is
  *     1 within 1e-9; unequal masses are rejected, never renormalised;
  *   - pointers marked "host or device" are read according to `space`
@@ -219,9 +221,9 @@ HOT_API int hot_solve_profiled(hot_ctx *ctx, const double *mu, const double *nu,
  * call time: code with a fixed, pre-accounted device-memory footprint, or a
  * latency-critical loop that must not pay for or synchronise on an
  * allocation).  Its scratch is a static device array inside the library,
- * sized for grids up to 256 x 256 (about 1.8 MB, held on every GPU that
- * loads the library until the process exits); larger grids return
- * HOT_EINVAL.  The first call on a device resolves that array's device
+ * sized for square grids up to 256 x 256 (about 1.8 MB, held on every GPU
+ * that loads the library until the process exits); larger or non-square
+ * grids (m != n) return HOT_EINVAL.  The first call on a device resolves that array's device
  * address (cudaGetSymbolAddress) and should therefore come before any stream
  * capture.
  *   x:       device, the flows in the vec order of hot_get_flows (m*m*n + m*n*n doubles)

@@ -7,7 +7,8 @@
 // the fastest per-iteration time is kept for that (precision, S).  The table
 // lives in the context and, when hot_config.autotune_cache names a file, in
 // that file (one line per entry: device, precision, S, TR, microseconds per
-// iteration), so later processes start tuned.
+// iteration), so later processes start tuned.  The table covers square S x S
+// grids; an m x n grid with m != n takes the rule of tile_rows.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -62,7 +63,7 @@ bool cache_append(const std::string& path, const std::string& dev, int fp64, int
 // Seeded white-noise histograms (host LCG; the values only need to be a
 // typical dense input, the tuner does not look at the result).
 void tune_pair(int S, PairHost& p) {
-    p.S = S;
+    p.m = p.n = S;
     p.mu1.assign((size_t)S * S, 0.0);
     p.mu2.assign((size_t)S * S, 0.0);
     unsigned long long z = 0x9E3779B97F4A7C15ull ^ (unsigned long long)S;
@@ -91,10 +92,11 @@ std::vector<int> tile_candidates(int S, int fp64) {
     return out;
 }
 
-int tuned_tile_rows(Ctx* ctx, int S, int fp64) {
+int tuned_tile_rows(Ctx* ctx, int m, int n, int fp64) {
+    if (m != n) return 0;
     std::lock_guard<std::mutex> g(ctx->tune_mu);
     auto& t = ctx->tuned[fp64 ? 1 : 0];
-    auto it = t.find(S);
+    auto it = t.find(m);
     return it == t.end() ? 0 : it->second.first;
 }
 

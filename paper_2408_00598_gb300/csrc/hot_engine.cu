@@ -20,20 +20,24 @@ const char* get_error() { return g_err.c_str(); }
 
 // ------------------------------------------------------------- validation --
 
-int tile_rows(int S, int fp64, int grid) {
+int tile_rows(int m, int n, int fp64, int grid) {
+    // one TR for both halves: the row-partial buffer holds TR rows of the
+    // longer slab side L = max(m, n)
+    const int L = std::max(m, n);
     if (fp64) {
-        // row-partial buffer: TR * S <= 4096
-        int tr = std::min(S, 4096 / S);
-        if (S >= 96) tr = std::min(tr, 32);
+        // row-partial buffer: TR * L <= 4096
+        int tr = std::min(L, 4096 / L);
+        if (L >= 96) tr = std::min(tr, 32);
         return std::max(tr, 1);
     }
-    // TR * S <= 16384 (row-partial buffer).  Tiles as tall as that allows
+    // TR * L <= 16384 (row-partial buffer).  Tiles as tall as that allows
     // (the per-tile set-up and reductions cost more than a ragged last round
     // of the persistent grid), halved while a slab-set this small leaves the
     // grid's CTAs under two tiles each and a tile keeps at least 4 passes
-    int tr = std::min(S, 16384 / S);
+    int tr = std::min(std::min(L, 16384 / L), kMaxTR);
+    auto tiles = [&](int t) { return (long long)n * ((m + t - 1) / t) + (long long)m * ((n + t - 1) / t); };
     if (grid > 0)
-        while (2LL * S * ((S + tr - 1) / tr) < 2LL * grid && (long long)(tr / 2) * S >= 4096) tr /= 2;
+        while (tiles(tr) < 2LL * grid && (long long)(tr / 2) * L >= 4096) tr /= 2;
     return tr;
 }
 
@@ -71,18 +75,16 @@ int validate_pair(const double* mu, const double* nu, int m, int n, int space, i
         set_error("null histogram pointer");
         return HOT_EINVAL;
     }
-    if (m != n) {
-        set_error("only square grids (m == n) are supported in this version");
-        return HOT_EINVAL;
-    }
-    const int S = m;
     const int smax = fp64 ? 512 : kMaxS;
-    if (S < 8 || S > smax || (S % 4) != 0) {
-        set_error("grid side must be a multiple of 4 in [8, " + std::to_string(smax) + "], got " + std::to_string(S));
-        return HOT_EINVAL;
-    }
-    out.S = S;
-    const size_t M = (size_t)S * S;
+    for (int side : {m, n})
+        if (side < 8 || side > smax || (side % 4) != 0) {
+            set_error("grid sides must be multiples of 4 in [8, " + std::to_string(smax) + "], got " +
+                      std::to_string(m) + " x " + std::to_string(n));
+            return HOT_EINVAL;
+        }
+    out.m = m;
+    out.n = n;
+    const size_t M = (size_t)m * n;
     out.mu1.resize(M);
     out.mu2.resize(M);
     if (space == HOT_SPACE_DEVICE) {
@@ -127,72 +129,79 @@ int inst_create(const PairHost& p, int fp64, const hot_config& cfg, double tol, 
                 cudaStream_t st, Inst** out) {
     *out = nullptr;
     std::unique_ptr<Inst> I(new Inst());
-    const int S = p.S;
-    I->S = S;
+    const int m = p.m, n = p.n, L = std::max(m, n);
+    I->m = m;
+    I->n = n;
     I->fp64 = fp64;
-    I->TR = tr_override > 0 ? tr_override : tile_rows(S, fp64, sweep_grid(fp64));
+    I->TR = tr_override > 0 ? tr_override : tile_rows(m, n, fp64, sweep_grid(fp64));
     const int NV = fp64 ? 2 : 4;
-    const int P = kThreads / (S / NV);
-    if (I->TR > S || (size_t)I->TR * S > (size_t)(fp64 ? 4096 : 16384) || P < 1) {
+    if (I->TR > (fp64 ? L : kMaxTR) || (size_t)I->TR * L > (size_t)(fp64 ? 4096 : 16384) ||
+        kThreads / (L / NV) < 1) {
         set_error("invalid tile rows for this grid");
         return HOT_EINVAL;
     }
-    I->nb = (S + I->TR - 1) / I->TR;
-    I->n_k1 = (3 * S * S - 1 + kThreads - 1) / kThreads;
-    const size_t V = 2ull * S * S * S;
+    I->nb1 = (m + I->TR - 1) / I->TR;
+    I->nb2 = (n + I->TR - 1) / I->TR;
+    const size_t MN = (size_t)m * n;
+    I->n_k1 = (int)((3 * MN - 1 + kThreads - 1) / kThreads);
+    // flow variables: n f1 slabs of m x m, m f2 slabs of n x n
+    const size_t V = MN * (size_t)(m + n);
     const size_t es = fp64 ? 8 : 4;
     I->big_bytes = 5 * align256(V * es);
 
-    // small-buffer layout
-    const size_t SS = (size_t)S * S;
+    // small-buffer layout; per-slab arrays hold 2mn entries (one per slab row:
+    // n slabs of m rows, m slabs of n rows), column partials one per band
+    const int ntiles = n * I->nb1 + m * I->nb2;
+    const size_t CP = (size_t)n * I->nb1 * m + (size_t)m * I->nb2 * n;   // column-partial entries
+    const int NS = m + n;                                                  // slabs
     size_t off = 0;
     auto take = [&](size_t bytes) {
         size_t o = off;
         off += align256(bytes);
         return o;
     };
-    const size_t o_ab32 = fp64 ? 0 : take(4 * SS * sizeof(float4));
-    const size_t o_ab0_32 = fp64 ? 0 : take(4 * SS * sizeof(float2));   // y0 = 0 at the start
-    const size_t o_ab64 = take(4 * SS * 8);
-    const size_t o_dab = take(4 * SS * 8);
-    const size_t o_ab0 = take(4 * SS * 8);      // A^T y0 pieces: y0 = 0 at the start
-    const size_t o_rs = take(2 * SS * 8);
-    const size_t o_cs = take(2 * SS * I->nb * 8);
-    const size_t o_cs32 = take(2 * SS * I->nb * 4);
-    const size_t o_R1a = take(2 * SS * 8);
-    const size_t o_kapa = take(2 * SS * 8);
-    const size_t o_rs0 = take(2 * SS * 8);
-    const size_t o_cs0 = take(2 * SS * I->nb * 8);
-    const size_t o_xrs = take(2 * SS * 8);
-    const size_t o_xcs = take(2 * SS * I->nb * 8);
-    const size_t o_tk = take((size_t)2 * S * I->nb * kNK * 8);
-    const size_t o_rp = take((size_t)2 * S * I->nb * 2 * 8);
-    const size_t o_vec = take(4 * (size_t)S * 8);
-    const size_t o_mvec = take(4 * (size_t)S * 8);
+    const size_t o_ab32 = fp64 ? 0 : take(4 * MN * sizeof(float4));
+    const size_t o_ab0_32 = fp64 ? 0 : take(4 * MN * sizeof(float2));   // y0 = 0 at the start
+    const size_t o_ab64 = take(4 * MN * 8);
+    const size_t o_dab = take(4 * MN * 8);
+    const size_t o_ab0 = take(4 * MN * 8);      // A^T y0 pieces: y0 = 0 at the start
+    const size_t o_rs = take(2 * MN * 8);
+    const size_t o_cs = take(CP * 8);
+    const size_t o_cs32 = take(CP * 4);
+    const size_t o_R1a = take(2 * MN * 8);
+    const size_t o_kapa = take(2 * MN * 8);
+    const size_t o_rs0 = take(2 * MN * 8);
+    const size_t o_cs0 = take(CP * 8);
+    const size_t o_xrs = take(2 * MN * 8);
+    const size_t o_xcs = take(CP * 8);
+    const size_t o_tk = take((size_t)ntiles * kNK * 8);
+    const size_t o_rp = take((size_t)ntiles * 2 * 8);
+    const size_t o_vec = take(4 * (size_t)L * 8);
+    const size_t o_mvec = take(4 * (size_t)L * 8);
     const size_t F2 = fp64 ? 0 : sizeof(float2);   // double-float arrays of FP32 mode
-    const size_t o_rs2 = take(2 * SS * F2);
-    const size_t o_rs02 = take(2 * SS * F2);
-    const size_t o_K2 = take(2 * SS * F2);
-    const size_t o_vec2 = take((2 + 2 * (size_t)((S + 63) / 64)) * (size_t)S * F2);
-    const size_t o_dab2 = take(4 * SS * F2);
+    const size_t o_rs2 = take(2 * MN * F2);
+    const size_t o_rs02 = take(2 * MN * F2);
+    const size_t o_K2 = take(2 * MN * F2);
+    const size_t o_vec2 = take(vec2_entries(m, n) * F2);
+    const size_t o_dab2 = take(4 * MN * F2);
     const size_t o_zero_end = off;                 // everything above starts at 0
-    const size_t o_mu1f = take(SS * F2);
-    const size_t o_mu2f = take(SS * F2);
-    const size_t o_cm2 = take(S * F2);
-    const size_t o_rm2 = take(S * F2);
+    const size_t o_mu1f = take(MN * F2);
+    const size_t o_mu2f = take(MN * F2);
+    const size_t o_cm2 = take(n * F2);
+    const size_t o_rm2 = take(m * F2);
     const size_t o_p32 = take(sizeof(P32));
-    const size_t o_X32 = take(2 * (size_t)S * sizeof(float));
-    const size_t o_X64 = take(2 * (size_t)S * sizeof(double));
-    const size_t o_cs2 = take(2 * (size_t)S * sizeof(float2));
+    const size_t o_X32 = take((size_t)NS * sizeof(float));
+    const size_t o_X64 = take((size_t)NS * sizeof(double));
+    const size_t o_cs2 = take((size_t)NS * sizeof(float2));
     const size_t o_cyc = take(sizeof(CycleK));
-    const size_t o_mu1 = take(SS * 8);
-    const size_t o_mu2 = take(SS * 8);
-    const size_t o_cm = take(S * 8);
-    const size_t o_rm = take(S * 8);
+    const size_t o_mu1 = take(MN * 8);
+    const size_t o_mu2 = take(MN * 8);
+    const size_t o_cm = take(n * 8);
+    const size_t o_rm = take(m * 8);
     const size_t o_k1 = take((size_t)I->n_k1 * 8);
-    const size_t o_dp = take(2 * (size_t)S * 8);
-    const size_t o_cu = take((size_t)2 * S * I->nb * 8);
-    const size_t o_cD = take(2 * (size_t)S * 8);
+    const size_t o_dp = take((size_t)NS * 8);
+    const size_t o_cu = take((size_t)ntiles * 8);
+    const size_t o_cD = take((size_t)NS * 8);
     const size_t o_ctl = take(sizeof(HotCtl));
     I->small_bytes = off;
 
@@ -208,26 +217,27 @@ int inst_create(const PairHost& p, int fp64, const hot_config& cfg, double tol, 
         return HOT_ENOMEM;
     }
     HotInst& d = I->desc;
-    d.S = S;
+    d.m = m;
+    d.n = n;
     d.TR = I->TR;
-    d.nb = I->nb;
+    d.nb1 = I->nb1;
+    d.nb2 = I->nb2;
     d.n_k1 = I->n_k1;
     d.fp64 = fp64;
     d.gadmm = cfg.method == HOT_METHOD_GADMM ? 1 : 0;
     d.stop_abs = cfg.stop_rule == HOT_STOP_ABSOLUTE ? 1 : 0;
     d.relax = cfg.relaxation;
-    // power-of-two cost scale: smallest 2^E >= max c = (S-1)^2
-    // bin coordinates of the two halves: f1 slabs use the row coordinates
-    // (i, k), f2 slabs the column coordinates (j, l); default 0..S-1
-    std::vector<double> X(2 * (size_t)S);
-    for (int r = 0; r < S; ++r) {
-        X[r] = p.xs.empty() ? (double)r : p.xs[r];
-        X[S + r] = p.ys.empty() ? (double)r : p.ys[r];
-    }
+    // bin coordinates: X[0, m) are the row coordinates (i, k) that the f1
+    // slabs' cost uses, X[m, m + n) the column coordinates (j, l) of the f2
+    // slabs; default 0, 1, ...
+    std::vector<double> X((size_t)NS);
+    for (int r = 0; r < m; ++r) X[r] = p.xs.empty() ? (double)r : p.xs[r];
+    for (int r = 0; r < n; ++r) X[m + r] = p.ys.empty() ? (double)r : p.ys[r];
+    const int hb[3] = {0, m, m + n};
     // power-of-two cost scale: smallest 2^E >= max c (E = 0 for a zero cost)
     double cmax = 0.0;
     for (int hlf = 0; hlf < 2; ++hlf) {
-        const auto mm = std::minmax_element(X.begin() + hlf * S, X.begin() + (hlf + 1) * S);
+        const auto mm = std::minmax_element(X.begin() + hb[hlf], X.begin() + hb[hlf + 1]);
         cmax = std::max(cmax, (*mm.second - *mm.first) * (*mm.second - *mm.first));
     }
     int E = 0;
@@ -239,22 +249,23 @@ int inst_create(const PairHost& p, int fp64, const hot_config& cfg, double tol, 
     d.E = E;
     d.h = std::ldexp(1.0, -E);
     I->cost_scale = std::ldexp(1.0, E);
-    // ||c||: every slab of a half has the same cost matrix; C(x) = sum_y (X_x - X_y)^2
-    double c4 = 0.0;
-    std::vector<double> csum(2 * (size_t)S, 0.0);
+    // ||c||: the n f1 slabs share one cost matrix, the m f2 slabs another;
+    // C(x) = sum_y (X_x - X_y)^2 within each half
+    double c4[2] = {0.0, 0.0};
+    std::vector<double> csum((size_t)NS, 0.0);
     for (int hlf = 0; hlf < 2; ++hlf)
-        for (int a = 0; a < S; ++a)
-            for (int t = 0; t < S; ++t) {
-                const double dx = X[hlf * S + a] - X[hlf * S + t];
+        for (int a = hb[hlf]; a < hb[hlf + 1]; ++a)
+            for (int t = hb[hlf]; t < hb[hlf + 1]; ++t) {
+                const double dx = X[a] - X[t];
                 const double dd = dx * dx;
-                c4 += dd * dd;
-                csum[hlf * S + a] += dd;
+                c4[hlf] += dd * dd;
+                csum[a] += dd;
             }
-    d.norm_c = d.h * std::sqrt((double)S * c4);
+    d.norm_c = d.h * std::sqrt((double)n * c4[0] + (double)m * c4[1]);
     double b2 = 0.0;
     for (double x : p.mu1) b2 += x * x;
     for (double x : p.mu2) b2 += x * x;
-    b2 -= p.mu2[SS - 1] * p.mu2[SS - 1];
+    b2 -= p.mu2[MN - 1] * p.mu2[MN - 1];
     d.norm_b = std::sqrt(b2);
     char* big = I->big;
     const size_t VB = align256(V * es);
@@ -307,11 +318,11 @@ int inst_create(const PairHost& p, int fp64, const hot_config& cfg, double tol, 
     d.ctl = (HotCtl*)(sm + o_ctl);
 
     // host-side constants uploaded once
-    std::vector<double> cm(S, 0.0), rm(S, 0.0);
-    for (int i = 0; i < S; ++i)
-        for (int j = 0; j < S; ++j) {
-            cm[j] += p.mu1[(size_t)i * S + j];
-            rm[i] += p.mu2[(size_t)i * S + j];
+    std::vector<double> cm(n, 0.0), rm(m, 0.0);
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < n; ++j) {
+            cm[j] += p.mu1[(size_t)i * n + j];
+            rm[i] += p.mu2[(size_t)i * n + j];
         }
     HotCtl c{};
     c.sigma = cfg.sigma0 > 0.0 ? cfg.sigma0 : d.norm_b / d.norm_c;
@@ -323,10 +334,10 @@ int inst_create(const PairHost& p, int fp64, const hot_config& cfg, double tol, 
     I->ctl_host = c;
 
     cudaError_t ee = cudaMemsetAsync(sm, 0, o_zero_end, st);
-    if (ee == cudaSuccess) ee = cudaMemcpyAsync(d.mu1, p.mu1.data(), SS * 8, cudaMemcpyHostToDevice, st);
-    if (ee == cudaSuccess) ee = cudaMemcpyAsync(d.mu2, p.mu2.data(), SS * 8, cudaMemcpyHostToDevice, st);
-    if (ee == cudaSuccess) ee = cudaMemcpyAsync(d.colmu1, cm.data(), S * 8, cudaMemcpyHostToDevice, st);
-    if (ee == cudaSuccess) ee = cudaMemcpyAsync(d.rowmu2, rm.data(), S * 8, cudaMemcpyHostToDevice, st);
+    if (ee == cudaSuccess) ee = cudaMemcpyAsync(d.mu1, p.mu1.data(), MN * 8, cudaMemcpyHostToDevice, st);
+    if (ee == cudaSuccess) ee = cudaMemcpyAsync(d.mu2, p.mu2.data(), MN * 8, cudaMemcpyHostToDevice, st);
+    if (ee == cudaSuccess) ee = cudaMemcpyAsync(d.colmu1, cm.data(), n * 8, cudaMemcpyHostToDevice, st);
+    if (ee == cudaSuccess) ee = cudaMemcpyAsync(d.rowmu2, rm.data(), m * 8, cudaMemcpyHostToDevice, st);
     if (ee == cudaSuccess) ee = cudaMemcpyAsync(d.ctl, &I->ctl_host, sizeof(HotCtl), cudaMemcpyHostToDevice, st);
     {
         // coordinates (FP32 copies are exact: FP32 mode takes integer coordinates)
@@ -351,12 +362,12 @@ int inst_create(const PairHost& p, int fp64, const hot_config& cfg, double tol, 
             }
             return v;
         };
-        const std::vector<float2> f1 = pairs(p.mu1.data(), SS), f2 = pairs(p.mu2.data(), SS);
-        const std::vector<float2> fc = pairs(cm.data(), S), fr = pairs(rm.data(), S);
-        if (ee == cudaSuccess) ee = cudaMemcpyAsync(d.mu1f, f1.data(), SS * F2, cudaMemcpyHostToDevice, st);
-        if (ee == cudaSuccess) ee = cudaMemcpyAsync(d.mu2f, f2.data(), SS * F2, cudaMemcpyHostToDevice, st);
-        if (ee == cudaSuccess) ee = cudaMemcpyAsync(d.cm2, fc.data(), S * F2, cudaMemcpyHostToDevice, st);
-        if (ee == cudaSuccess) ee = cudaMemcpyAsync(d.rm2, fr.data(), S * F2, cudaMemcpyHostToDevice, st);
+        const std::vector<float2> f1 = pairs(p.mu1.data(), MN), f2 = pairs(p.mu2.data(), MN);
+        const std::vector<float2> fc = pairs(cm.data(), n), fr = pairs(rm.data(), m);
+        if (ee == cudaSuccess) ee = cudaMemcpyAsync(d.mu1f, f1.data(), MN * F2, cudaMemcpyHostToDevice, st);
+        if (ee == cudaSuccess) ee = cudaMemcpyAsync(d.mu2f, f2.data(), MN * F2, cudaMemcpyHostToDevice, st);
+        if (ee == cudaSuccess) ee = cudaMemcpyAsync(d.cm2, fc.data(), n * F2, cudaMemcpyHostToDevice, st);
+        if (ee == cudaSuccess) ee = cudaMemcpyAsync(d.rm2, fr.data(), m * F2, cudaMemcpyHostToDevice, st);
         // pageable sources: the copies are staged before cudaMemcpyAsync returns
     }
     if (ee == cudaSuccess) {
@@ -446,10 +457,10 @@ int Batch::set_instances(const std::vector<Inst*>& v, cudaStream_t st) {
     int running = 0;
     for (int i = 0; i < n; ++i) {
         h_inst[i] = v[i]->desc;
-        const int S = v[i]->S;
-        pt[i + 1] = pt[i] + 2 * S * v[i]->nb;
-        ps[i + 1] = ps[i] + 2 * S;
-        pv[i + 1] = pv[i] + (v[i]->fp64 ? 4 * S : vec32_items(S));
+        const int m = v[i]->m, nn = v[i]->n;
+        pt[i + 1] = pt[i] + nn * v[i]->nb1 + m * v[i]->nb2;
+        ps[i + 1] = ps[i] + m + nn;
+        pv[i + 1] = pv[i] + (v[i]->fp64 ? 2 * (m + nn) : vec32_items(m, nn));
         pk[i + 1] = pk[i] + v[i]->n_k1;
         if (v[i]->ctl_host.status == ST_RUNNING) ++running;
     }
@@ -527,7 +538,8 @@ void fill_result(const Inst* I, hot_result* r) {
     float ym;
     std::memcpy(&ym, &yb, 4);
     r->max_abs_dual = ym;
-    r->m = r->n = I->S;
+    r->m = I->m;
+    r->n = I->n;
 }
 
 int run_solve(Ctx* ctx, const std::vector<PairHost>& pairs, double tol, long long max_iter, bool keep,
@@ -552,7 +564,7 @@ int run_solve(Ctx* ctx, const std::vector<PairHost>& pairs, double tol, long lon
     };
     for (const PairHost& p : pairs) {
         Inst* I = nullptr;
-        const int tr = ctx->tile_override ? ctx->tile_override : tuned_tile_rows(ctx, p.S, fp64);
+        const int tr = ctx->tile_override ? ctx->tile_override : tuned_tile_rows(ctx, p.m, p.n, fp64);
         int rc = inst_create(p, fp64, ctx->cfg, tol, max_iter, tr, st, &I);
         if (rc != HOT_OK) {
             cleanup();
@@ -650,7 +662,7 @@ int run_solve(Ctx* ctx, const std::vector<PairHost>& pairs, double tol, long lon
     for (auto& ee : pev) cudaEventDestroy(ee);
     if (kt) {
         double vb = 0.0;
-        for (Inst* I : insts) vb += 2.0 * I->S * (double)I->S * I->S * (fp64 ? 24.0 : 12.0);
+        for (Inst* I : insts) vb += (double)I->m * I->n * (I->m + I->n) * (fp64 ? 24.0 : 12.0);
         kt->sweep_bytes = vb;
     }
     if (e != cudaSuccess || err != HOT_OK) {

@@ -34,9 +34,9 @@ const char* get_error();
 
 // One instance's device memory and descriptor.
 struct Inst {
-    int S = 0;
+    int m = 0, n = 0;        // grid: the histograms are m x n
     int fp64 = 0;
-    int TR = 0, nb = 0, n_k1 = 0;
+    int TR = 0, nb1 = 0, nb2 = 0, n_k1 = 0;
     size_t big_bytes = 0, small_bytes = 0;
     char* big = nullptr;     // v0, d0, d1, xr, zr
     char* small = nullptr;   // sums, vectors, mu, ctl
@@ -48,17 +48,17 @@ struct Inst {
 
 // Host-side constants of a histogram pair (validated).
 struct PairHost {
-    int S = 0;
-    std::vector<double> mu1, mu2;
-    std::vector<double> xs, ys;            // bin coordinates (row index i/k, column index j/l); empty: 0..S-1
+    int m = 0, n = 0;
+    std::vector<double> mu1, mu2;          // m x n, row-major
+    std::vector<double> xs, ys;            // bin coordinates: xs[m] of rows i/k, ys[n] of columns j/l; empty: 0, 1, ...
 };
 
-// Checks bin coordinates and stores them in `out` (NULL: uniform 0..S-1).
+// Checks bin coordinates and stores them in `out` (NULL: uniform 0, 1, ...).
 int set_coordinates(const double* xs, const double* ys, int m, int n, int fp64, PairHost& out);
 
 int validate_pair(const double* mu, const double* nu, int m, int n, int space, int fp64, PairHost& out);
 // rows per sweep tile; grid: resident CTAs of the sweep (0: no balancing)
-int tile_rows(int S, int fp64, int grid);
+int tile_rows(int m, int n, int fp64, int grid);
 
 // Allocate and initialise an instance on stream `st` (inputs already validated).
 // Barycentric projection of a plan (hot_consumers.cu).
@@ -130,7 +130,7 @@ int export_flows(Inst* I, double* x, int space, cudaStream_t st);
 
 // tile-shape autotuner (hot_autotune.cpp)
 std::vector<int> tile_candidates(int S, int fp64);
-int tuned_tile_rows(Ctx* ctx, int S, int fp64);          // 0: not tuned
+int tuned_tile_rows(Ctx* ctx, int m, int n, int fp64);   // 0: not tuned (or m != n)
 void autotune_load(Ctx* ctx);
 int autotune(Ctx* ctx, int S, int* tr_out, double* us_out);
 int autotune_cache_lookup(const char* path, const char* device, int precision, int S, int* tr, double* us);

@@ -1,18 +1,19 @@
 // Device-side data structures shared by the HOT kernels and the host engine.
 //
-// Layout of one instance (square grid, m = n = S) in device memory.  The flow
-// vector x = [f1; f2] of the reduced model (eq. 3-4 of arXiv 2408.00598) is
-// stored as 2S "slabs" of S x S values, slab-major, row-major inside a slab:
-//   slab s <  S : f1 for column j = s;      row = k, col = i   (f1_{i,k,j})
-//   slab s >= S : f2 for row    k = s - S;  row = j, col = l   (f2_{k,j,l})
-// so element (s, r, c) sits at s*S*S + r*S + c.  In both halves the cost is
-// (r - c)^2 (eq. 4), A^T y at (s, r, c) is alpha_s[r] + beta_s[c] with
+// Layout of one instance (an m x n grid) in device memory.  The flow vector
+// x = [f1; f2] of the reduced model (eq. 3-4 of arXiv 2408.00598) is stored as
+// n + m "slabs", slab-major, row-major inside a slab:
+//   slab s <  n : f1 for column j = s;      m x m, row = k, col = i   (f1_{i,k,j})
+//   slab s >= n : f2 for row    k = s - n;  n x n, row = j, col = l   (f2_{k,j,l})
+// (offsets in the g_* helpers below).  In both halves the cost is
+// (X_r - X_c)^2 with X the bin coordinates of that axis (eq. 4), A^T y at
+// (s, r, c) is alpha_s[r] + beta_s[c] with
 //   f1 slab j: alpha[k] =  y1(k,j), beta[i] = y2(i,j)
-//   f2 slab k: alpha[j] = -y1(k,j), beta[l] = y3(k,l)   (y3(S-1,S-1) = 0),
+//   f2 slab k: alpha[j] = -y1(k,j), beta[l] = y3(k,l)   (y3(m-1,n-1) = 0),
 // and the row and column sums of a slab are the A x products:
 //   (A x)_1(k,j) = rowsum(f1 slab j)[k] - rowsum(f2 slab k)[j]
 //   (A x)_2(i,j) = colsum(f1 slab j)[i]
-//   (A x)_3(k,l) = colsum(f2 slab k)[l]        ((S-1,S-1) row dropped, eq. 7-8)
+//   (A x)_3(k,l) = colsum(f2 slab k)[l]        ((m-1,n-1) row dropped, eq. 7-8)
 // Every reduction of the method is therefore slab-local.
 //
 // The iterate is kept in the reduced form v = x + sigma z (the shadow sequence
@@ -35,7 +36,7 @@ constexpr int kThreads = 256;          // block size of the tile kernels
 constexpr int kNK = 5;                 // per-tile check partials: r^2, min^2, x^2, z^2, c.x
 constexpr int kRowSmemBytes = 16384;   // row-partial buffer of a sweep tile
 constexpr int kMaxS = 1024;
-constexpr int kMaxTR = 128;            // FP32 tiles: TR <= S and TR * S <= kRowSmemBytes / 4
+constexpr int kMaxTR = 128;            // FP32 tiles: TR * max(m, n) <= kRowSmemBytes / 4
 
 enum : int {
     ST_RUNNING = 0,
@@ -90,10 +91,10 @@ struct CycleK {
 
 // Per-instance descriptor (read-only while a block runs).
 struct HotInst {
-    int S;                 // grid side
-    int E;                 // cost scale 2^E >= (S-1)^2; scaled cost = (r-c)^2 * 2^-E
+    int m, n;              // grid: mu is m x n (rows i/k, columns j/l)
+    int E;                 // cost scale 2^E >= max c; scaled cost = c * 2^-E
     int TR;                // rows per sweep tile
-    int nb;                // bands (tiles) per slab = ceil(S / TR)
+    int nb1, nb2;          // bands (tiles) per f1 slab = ceil(m / TR), per f2 slab = ceil(n / TR)
     int n_k1;              // chunks of the A x - b kernel
     int fp64;              // 1: FP64 state, 0: FP32 anchor + delta
     int gadmm;             // 1: Step 4 of the generalized ADMM instead of Halpern's
@@ -102,56 +103,98 @@ struct HotInst {
     double h;              // 2^-E
     double norm_b;         // ||b||
     double norm_c;         // ||c|| of the scaled problem
-    void* u;               // anchor, reduced: u = v0 - sigma (c - A^T y0)   [2S][S][S]
-    void* d0;              // delta, ping             [2S][S][S]
-    void* d1;              // delta, pong             [2S][S][S]
+    // per-instance arrays, sized for the slab layout: V = mn(m + n) flow
+    // variables; "per slab row" arrays hold 2mn entries (g_row), "pieces" 4mn
+    // (alpha then beta of each slab), column partials one row per band (g_colp)
+    void* u;               // anchor, reduced: u = v0 - sigma (c - A^T y0)   [V]
+    void* d0;              // delta, ping             [V]
+    void* d1;              // delta, pong             [V]
     void* xr;              // x-bar at the last restart (final x-bar after the solve)
     void* zr;              // z-bar at the last restart
-    float4* ab32;          // [2S][2][S] (hi, lo, delta, 0) of alpha then beta, FP32 mode
-    float2* ab0_32;        // [2S][2][S] (hi, lo) split of ab0, FP32 mode (fixed within a cycle)
-    double* ab64;          // [2S][2][S] alpha then beta = A^T y-bar pieces (FP64 mode)
-    double* ab0;           // [2S][2][S] the same pieces of A^T y0 at the anchor
-    double* dab64;         // [2S][2][S] A^T (y-bar - y0) pieces
-    double* rs;            // [2S][S] row sums of the delta written by the last sweep
-    double* cs_part;       // [2S][nb][S] column partial sums of the delta (FP64 mode)
-    float* cs32;           // [2S][nb][S] column partial sums of the delta (FP32 mode)
-    double* R1a;           // [2S][S] anchor part of R1 along each slab's rows: -(rowsum f1 - rowsum f2)(u)/sigma
-    double* kapa;          // [2S][S] column totals of u per slab
-    double* rs0;           // [2S][S] row sums of u (FP64)
-    double* cs0_part;      // [2S][nb][S] column partial sums of u
-    double* xrs;           // [2S][S] row sums of x-bar (check iterations)
-    double* xcs_part;      // [2S][nb][S]
-    double* tile_kkt;      // [2S*nb][kNK]
-    double* rst_part;      // [2S*nb][2]
-    double* vecs;          // [4][S]: T1, T2, P1, P2 (slab totals and cross-slab row sums)
-    double* mvec;          // [4][S]: instance-wide vectors of Prop. 3 (k_marg)
-    double* mu1;           // [S][S] row-major mu1(i, j)
-    double* mu2;           // [S][S] row-major mu2(k, l)
-    double* colmu1;        // [S] sum_i mu1(i, j)
-    double* rowmu2;        // [S] sum_l mu2(k, l)
+    float4* ab32;          // [4mn] pieces (hi, lo, delta, 0) of alpha then beta, FP32 mode
+    float2* ab0_32;        // [4mn] (hi, lo) split of ab0, FP32 mode (fixed within a cycle)
+    double* ab64;          // [4mn] alpha then beta = A^T y-bar pieces (FP64 mode)
+    double* ab0;           // [4mn] the same pieces of A^T y0 at the anchor
+    double* dab64;         // [4mn] A^T (y-bar - y0) pieces
+    double* rs;            // [2mn] row sums of the delta written by the last sweep
+    double* cs_part;       // [slab][band][column] partial sums of the delta (FP64 mode)
+    float* cs32;           // [slab][band][column] partial sums of the delta (FP32 mode)
+    double* R1a;           // [2mn] anchor part of R1 along each slab's rows: -(rowsum f1 - rowsum f2)(u)/sigma
+    double* kapa;          // [2mn] column totals of u per slab
+    double* rs0;           // [2mn] row sums of u (FP64)
+    double* cs0_part;      // [slab][band][column] partial sums of u
+    double* xrs;           // [2mn] row sums of x-bar (check iterations)
+    double* xcs_part;      // [slab][band][column] partial sums of x-bar
+    double* tile_kkt;      // [tiles][kNK], tiles = n nb1 + m nb2
+    double* rst_part;      // [tiles][2]
+    double* vecs;          // [4][max(m, n)]: T1, T2, P1, P2 (slab totals and cross-slab row sums)
+    double* mvec;          // [4][max(m, n)]: instance-wide vectors of Prop. 3 (k_marg)
+    double* mu1;           // [m][n] row-major mu1(i, j)
+    double* mu2;           // [m][n] row-major mu2(k, l)
+    double* colmu1;        // [n] sum_i mu1(i, j)
+    double* rowmu2;        // [m] sum_l mu2(k, l)
     double* k1_part;       // [n_k1] partial ||A x - b||^2
-    double* dobj_part;     // [2S] partial <b, y>
-    double* cu_part;       // [2S*nb] <c, u> per tile (FP32 mode, set per cycle)
-    double* cD_part;       // [2S] <c, A^T(y-bar - y0)> per slab (FP32 mode, check iterations)
+    double* dobj_part;     // [m + n] partial <b, y> per slab
+    double* cu_part;       // [tiles] <c, u> per tile (FP32 mode, set per cycle)
+    double* cD_part;       // [m + n] <c, A^T(y-bar - y0)> per slab (FP32 mode, check iterations)
     // FP32 bulk mode only (null in FP64 mode): the per-iteration Prop. 3
     // arithmetic runs on double-float pairs (hi, lo) of FP32 values, whose
     // sum carries about 48 significant bits, instead of FP64
-    float2* rs2;           // [2S][S] row sums of u + d (last sweep; = rs02 after a restart)
-    float2* rs02;          // [2S][S] row sums of u (fixed within a cycle)
-    float2* K2;            // [2S][S] (mu - colsum u)/(sigma m) per slab column (/(sigma n) for f2), fixed within a cycle
-    float2* vec2;          // T1 [S], T2 [S], then P1 and P2 as [2][ceil(S/64)][S] partials, of u + d
-    float2* dab2;          // [2S][2S] pieces of A^T(y-bar - y0)
-    float2* mu1f;          // [S][S] mu1 as pairs
-    float2* mu2f;          // [S][S] mu2 as pairs
-    float2* cm2;           // [S] colmu1 as pairs
-    float2* rm2;           // [S] rowmu2 as pairs
+    float2* rs2;           // [2mn] row sums of u + d (last sweep; = rs02 after a restart)
+    float2* rs02;          // [2mn] row sums of u (fixed within a cycle)
+    float2* K2;            // [2mn] (mu - colsum u)/(sigma m) per slab column (/(sigma n) for f2), fixed within a cycle
+    float2* vec2;          // rows of max(m, n): T1, T2, then ceil(n/64) partials of P1 and ceil(m/64) of P2, of u + d
+    float2* dab2;          // [4mn] pieces of A^T(y-bar - y0)
+    float2* mu1f;          // [m][n] mu1 as pairs
+    float2* mu2f;          // [m][n] mu2 as pairs
+    float2* cm2;           // [n] colmu1 as pairs
+    float2* rm2;           // [m] rowmu2 as pairs
     P32* p32;              // element constants of the current iteration
-    const float* X32;      // [2S] bin coordinates: rows/columns of f1 slabs, then of f2 slabs
+    const float* X32;      // [m + n] bin coordinates: the m row coordinates (f1 slabs), then the n column ones (f2 slabs)
     const double* X64;     // the same in FP64
-    const float2* csum2;   // [2S] C(x) = sum_y (X_x - X_y)^2 per half, as pairs
+    const float2* csum2;   // [m + n] C(x) = sum_y (X_x - X_y)^2 within each axis, as pairs
     struct CycleK* cyc;    // Prop. 3 constants of the current cycle
     HotCtl* ctl;
 };
+
+// ---- geometry of an m x n instance.  f1 slabs s < n (one per column j) are
+// m x m (rows k, columns i); f2 slabs s = n + k (one per row k) are n x n
+// (rows j, columns l).  Per-slab arrays are packed slab after slab; for
+// m = n = S every offset below is the square layout's s S^2, s S, ...
+__host__ __device__ inline int g_nslab(const HotInst& I) { return I.n + I.m; }
+__host__ __device__ inline int g_side(const HotInst& I, int s) { return s < I.n ? I.m : I.n; }
+__host__ __device__ inline int g_nb(const HotInst& I, int s) { return s < I.n ? I.nb1 : I.nb2; }
+// first flow variable of slab s
+__host__ __device__ inline size_t g_elem(const HotInst& I, int s) {
+    return s < I.n ? (size_t)s * I.m * I.m : (size_t)I.n * I.m * I.m + (size_t)(s - I.n) * I.n * I.n;
+}
+// first entry of slab s in arrays with one entry per slab row (or column)
+__host__ __device__ inline size_t g_row(const HotInst& I, int s) {
+    return s < I.n ? (size_t)s * I.m : (size_t)I.n * I.m + (size_t)(s - I.n) * I.n;
+}
+// first entry of (slab s, band) in the column-partial arrays [slab][band][column]
+__host__ __device__ inline size_t g_colp(const HotInst& I, int s, int band) {
+    return s < I.n ? ((size_t)s * I.nb1 + band) * I.m
+                   : (size_t)I.n * I.nb1 * I.m + ((size_t)(s - I.n) * I.nb2 + band) * I.n;
+}
+__host__ __device__ inline int g_ntiles(const HotInst& I) { return I.n * I.nb1 + I.m * I.nb2; }
+__host__ __device__ inline int g_tile(const HotInst& I, int s, int band) {
+    return s < I.n ? s * I.nb1 + band : I.n * I.nb1 + (s - I.n) * I.nb2 + band;
+}
+__host__ __device__ inline void g_tile_slab(const HotInst& I, int t, int& s, int& band) {
+    if (t < I.n * I.nb1) {
+        s = t / I.nb1;
+        band = t - s * I.nb1;
+    } else {
+        const int q = t - I.n * I.nb1;
+        s = I.n + q / I.nb2;
+        band = q - (s - I.n) * I.nb2;
+    }
+}
+// first bin coordinate of slab s's half (row coordinates for f1, column for f2)
+__host__ __device__ inline int g_xbase(const HotInst& I, int s) { return s < I.n ? 0 : I.m; }
+// stride of the four instance-wide Prop. 3 vectors (indexed by j < n or k < m)
+__host__ __device__ inline int g_L(const HotInst& I) { return I.m > I.n ? I.m : I.n; }
 
 // Work tables of one batch, in device memory.  pre_* are prefix sums over the
 // instances of the number of work items each kernel family handles.
@@ -159,9 +202,9 @@ struct WorkDev {
     int ninst;
     int pad;
     HotInst* inst;         // [ninst]
-    int* pre_tile;         // sweep / restart tiles: 2S * nb per instance
-    int* pre_slab;         // k_alpha: 2S per instance
-    int* pre_vec;          // k_vec: 4S per instance (one warp each); k_vec32: vec32_items(S) CTA items
+    int* pre_tile;         // sweep / restart tiles: n nb1 + m nb2 per instance
+    int* pre_slab;         // k_alpha: m + n slabs per instance
+    int* pre_vec;          // k_vec: 2(m + n) per instance (one warp each); k_vec32: vec32_items(m, n) CTA items
     int* pre_k1;           // k_kkt1: n_k1 per instance
     int* n_running;        // instances still running
     int* st_out;           // [ninst] status of each instance after its last check
@@ -183,9 +226,18 @@ struct LaunchDims {
 // FP64: k_vec, k_marg, k_alpha, k_sweep; FP32 bulk: k_vec32, k_alpha32, k_sweep
 inline int launches_per_iteration(int fp64) { return fp64 ? 4 : 3; }
 constexpr int kLaunchesBlockEnd = 8;       // k_kkt1, k_check, 3 x k_restart, k_restart_sigma, k_anchor, k_block_end
-// work items of k_vec32 per instance: T1/T2 in items of 8 outputs, P1/P2 in
-// items of 32 columns x 64 rows (one partial per 64-row block)
-inline int vec32_items(int S) { return 2 * ((S + 7) / 8) + 2 * ((S + 31) / 32) * ((S + 63) / 64); }
+// work items of k_vec32 per instance: T1 (n outputs) and T2 (m outputs) in
+// items of 8, P1 (m columns over n rows) and P2 (n columns over m rows) in items
+// of 32 columns x 64 rows (one partial per 64-row block)
+inline int vec32_items(int m, int n) {
+    return (n + 7) / 8 + (m + 7) / 8 + ((m + 31) / 32) * ((n + 63) / 64) + ((n + 31) / 32) * ((m + 63) / 64);
+}
+// float2 entries of vec2: T1, T2, then the (n + 63)/64 partials of P1 and the
+// (m + 63)/64 partials of P2, each a row of max(m, n)
+inline size_t vec2_entries(int m, int n) {
+    const int L = m > n ? m : n;
+    return (size_t)(2 + (n + 63) / 64 + (m + 63) / 64) * L;
+}
 void launch_solve_kernels(const WorkDev* w, const LaunchDims& ld, int fp64, int j, bool check, cudaStream_t st);
 void launch_sweep(const WorkDev* w, const LaunchDims& ld, int fp64, int j, bool check, cudaStream_t st);
 void launch_iteration(const WorkDev* w, const LaunchDims& ld, int fp64, int j, bool check, cudaStream_t st);

@@ -273,16 +273,15 @@ __device__ __forceinline__ bool resolve_tile(const WorkDev* __restrict__ W, int 
     }
     __syncthreads();
     tc.inst = s_tile[0];
-    const HotInst& I = W->inst[tc.inst];
-    tc.slab = s_tile[1] / I.nb;
-    tc.band = s_tile[1] % I.nb;
+    g_tile_slab(W->inst[tc.inst], s_tile[1], tc.slab, tc.band);
     return true;
 }
 
 // ----------------------------------------------------------------- k_vec --
-// T1[j] = sum_k rowsum(f1 slab j)[k], T2[k] = sum_j rowsum(f2 slab k)[j],
-// P1[k] = sum_j rowsum(f1 slab j)[k], P2[j] = sum_k rowsum(f2 slab k)[j];
-// row sums are those of u + d (the slab sums of u are kept separately).
+// T1[j] = sum_k rowsum(f1 slab j)[k] (j < n), T2[k] = sum_j rowsum(f2 slab k)[j]
+// (k < m), P1[k] = sum_j rowsum(f1 slab j)[k], P2[j] = sum_k rowsum(f2 slab k)[j];
+// row sums are those of u + d (the slab sums of u are kept separately).  One
+// warp per output; outputs at vecs[which * L + index], L = max(m, n).
 __global__ void __launch_bounds__(kThreads) k_vec(const WorkDev* __restrict__ W) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ninst = W->ninst;
@@ -293,24 +292,32 @@ __global__ void __launch_bounds__(kThreads) k_vec(const WorkDev* __restrict__ W)
         const int i = find_inst(W->pre_vec, ninst, item);
         const HotInst& I = W->inst[i];
         if (I.ctl->status != ST_RUNNING) continue;
-        const int S = I.S;
-        const int q = item - W->pre_vec[i];
-        const int which = q / S, idx = q % S;
+        const int m = I.m, n = I.n, L = g_L(I);
+        int q = item - W->pre_vec[i];
+        int which;
+        if (q < n) which = 0;
+        else if ((q -= n) < m) which = 1;
+        else if ((q -= m) < m) which = 2;
+        else {
+            q -= m;
+            which = 3;
+        }
         const double* __restrict__ rs = I.rs;
         const double* __restrict__ rs0 = I.rs0;
+        const size_t f2 = (size_t)n * m;               // first row of the f2 half
         double acc = 0.0;
-        if (which == 0) {
-            for (int t = lane; t < S; t += 32) acc += rs[idx * S + t] + rs0[idx * S + t];
-        } else if (which == 1) {
-            for (int t = lane; t < S; t += 32) acc += rs[(S + idx) * S + t] + rs0[(S + idx) * S + t];
-        } else if (which == 2) {
-            for (int t = lane; t < S; t += 32) acc += rs[t * S + idx] + rs0[t * S + idx];
-        } else {
-            for (int t = lane; t < S; t += 32) acc += rs[(S + t) * S + idx] + rs0[(S + t) * S + idx];
+        if (which == 0) {                              // T1[j]: f1 slab j, its m rows
+            for (int t = lane; t < m; t += 32) acc += rs[(size_t)q * m + t] + rs0[(size_t)q * m + t];
+        } else if (which == 1) {                       // T2[k]: f2 slab k, its n rows
+            for (int t = lane; t < n; t += 32) acc += rs[f2 + (size_t)q * n + t] + rs0[f2 + (size_t)q * n + t];
+        } else if (which == 2) {                       // P1[k]: row k of every f1 slab
+            for (int t = lane; t < n; t += 32) acc += rs[(size_t)t * m + q] + rs0[(size_t)t * m + q];
+        } else {                                       // P2[j]: row j of every f2 slab
+            for (int t = lane; t < m; t += 32) acc += rs[f2 + (size_t)t * n + q] + rs0[f2 + (size_t)t * n + q];
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-        if (lane == 0) I.vecs[which * S + idx] = acc;
+        if (lane == 0) I.vecs[which * L + q] = acc;
     }
 }
 
@@ -318,96 +325,92 @@ __global__ void __launch_bounds__(kThreads) k_vec(const WorkDev* __restrict__ W)
 // Prop. 3 on R' = (b - A(u + d))/sigma, the right-hand side whose solution is
 // dy = y-bar - y0: with v = sigma g0 + u + d, the right-hand side of
 // eq. (update:y) is R = b/sigma - A(v/sigma - c) = AA^T y0 + R'.  R' comes
-// from the slab sums of u + d.  With m = n = S:
+// from the slab sums of u + d.  With j < n and k < m:
 //   a_j = sum_k R1(k,j), bb_j = sum_i R2(i,j), r3_k = sum_l R3(k,l), T3 = sum r3,
 //   y1-hat(k,j) = (R1(k,j) + a_j/n - (1/m+1/n) bb_j + r3_k/n + T3/n^2)/(m+n),
 //   s_k = sum_j y1-hat(k,j),  t = W-hat s,  y1^a = t + (1^T t / n) 1,
 //   y1 = y1-hat - y1^a,  y2(i,j) = (R2(i,j) - sum_k y1(k,j))/m,
 //   y3(k,l) = (R3(k,l) + sum_j y1(k,j))/n.
-// k_marg (one CTA per instance) forms the O(S) vectors shared by all slabs:
-//   mv[0..S)   a_j / n - (1/m + 1/n) bb_j        (column part of y1-hat)
-//   mv[S..2S)  r3_k / n + T3 / n^2 - (m+n) y1^a_k (row part of y1, times m+n)
-//   mv[2S..3S) sum_k y1(k,j)                      (for y2)
-//   mv[3S..4S) sum_j y1(k,j)                      (for y3)
+// k_marg (one CTA per instance) forms the O(m + n) vectors shared by all
+// slabs, at mv[w * L + index], L = max(m, n):
+//   w = 0: a_j / n - (1/m + 1/n) bb_j        (column part of y1-hat), j < n
+//   w = 1: r3_k / n + T3 / n^2 - (m+n) y1^a_k (row part of y1, times m+n), k < m
+//   w = 2: sum_k y1(k,j)                      (for y2), j < n
+//   w = 3: sum_j y1(k,j)                      (for y3), k < m
 // k_alpha (one CTA per slab) then forms the slab's entries with products only
 // (FP64 division is slow on this part; reciprocals are taken once).
 __global__ void __launch_bounds__(kThreads) k_marg(const WorkDev* __restrict__ W) {
-    extern __shared__ double sv[];                   // 7 * S: T1 T2 P1 P2 colmu1 rowmu2, then s
+    extern __shared__ double sv[];                   // 7 L: T1 T2 P1 P2 colmu1 rowmu2, then s
     __shared__ double s_red[4 * 32];
     const int ninst = W->ninst;
     for (int inst = blockIdx.x; inst < ninst; inst += gridDim.x) {
         const HotInst& I = W->inst[inst];
         if (I.ctl->status != ST_RUNNING) continue;     // block-uniform
-        const int S = I.S, nb = I.nb;
-        const double m = S, n = S;
+        const int mi = I.m, ni = I.n, L = g_L(I);
+        const double m = mi, n = ni;
         const double is = 1.0 / I.ctl->sigma;
         const double in_ = 1.0 / n, im = 1.0 / m, imn = 1.0 / (m + n);
         double* T1 = sv;
-        double* T2 = sv + S;
-        double* P1 = sv + 2 * S;
-        double* P2 = sv + 3 * S;
-        double* cm = sv + 4 * S;
-        double* rm = sv + 5 * S;
-        double* ss = sv + 6 * S;
-        for (int q = threadIdx.x; q < 4 * S; q += blockDim.x) sv[q] = I.vecs[q];
-        for (int q = threadIdx.x; q < S; q += blockDim.x) {
-            cm[q] = I.colmu1[q];
-            rm[q] = I.rowmu2[q];
-        }
-        // column S-1 of the last f2 slab: the dropped (m, n) row of eq. (7)
-        double kap_last = I.kapa[(size_t)(2 * S - 1) * S + (S - 1)];
-        for (int b = 0; b < nb; ++b) kap_last += I.cs_part[((size_t)(2 * S - 1) * nb + b) * S + (S - 1)];
-        const double mu_last = I.mu2[(size_t)(S - 1) * S + (S - 1)];
+        double* T2 = sv + L;
+        double* P1 = sv + 2 * L;
+        double* P2 = sv + 3 * L;
+        double* cm = sv + 4 * L;
+        double* rm = sv + 5 * L;
+        double* ss = sv + 6 * L;
+        for (int q = threadIdx.x; q < 4 * L; q += blockDim.x) sv[q] = I.vecs[q];
+        for (int q = threadIdx.x; q < ni; q += blockDim.x) cm[q] = I.colmu1[q];
+        for (int q = threadIdx.x; q < mi; q += blockDim.x) rm[q] = I.rowmu2[q];
+        // the dropped (m, n) row of eq. (7): column n-1 of the last f2 slab
+        const int sl = g_nslab(I) - 1;
+        double kap_last = I.kapa[g_row(I, sl) + (ni - 1)];
+        for (int b = 0; b < I.nb2; ++b) kap_last += I.cs_part[g_colp(I, sl, b) + (ni - 1)];
+        const double mu_last = I.mu2[(size_t)(mi - 1) * ni + (ni - 1)];
         __syncthreads();
-        auto A_ = [&](int q) { return -(T1[q] - P2[q]) * is; };
-        auto B_ = [&](int q) { return (cm[q] - T1[q]) * is; };
-        auto R3_ = [&](int q) {
-            double r = (rm[q] - T2[q]) * is;
-            if (q == S - 1) r -= (mu_last - kap_last) * is;
+        auto A_ = [&](int j) { return -(T1[j] - P2[j]) * is; };
+        auto B_ = [&](int j) { return (cm[j] - T1[j]) * is; };
+        auto R3_ = [&](int k) {
+            double r = (rm[k] - T2[k]) * is;
+            if (k == mi - 1) r -= (mu_last - kap_last) * is;
             return r;
         };
         double red[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int q = threadIdx.x; q < S; q += blockDim.x) {
-            red[0] += A_(q);
-            red[1] += B_(q);
-            red[2] += R3_(q);
+        for (int j = threadIdx.x; j < ni; j += blockDim.x) {
+            red[0] += A_(j);
+            red[1] += B_(j);
         }
+        for (int k = threadIdx.x; k < mi; k += blockDim.x) red[2] += R3_(k);
         block_sum<4>(red, s_red);
         const double Asum = red[0], Bsum = red[1], T3 = red[2];
         const double dl = (1.0 - in_) / (m + 1.0);
         const double iw = 1.0 / (im - dl);             // 1/w, w = 1/m - (1-1/n)/(m+1)
         red[0] = red[1] = red[2] = red[3] = 0.0;
-        for (int q = threadIdx.x; q < S; q += blockDim.x) {
-            const double rowR1 = -(P1[q] - T2[q]) * is;
-            const double s = (rowR1 + Asum * in_ - (im + in_) * Bsum + R3_(q) + T3 * in_) * imn;   // s_k
-            ss[q] = s;
-            red[0] += (q == S - 1 ? dl : im) * s;
+        for (int k = threadIdx.x; k < mi; k += blockDim.x) {
+            const double rowR1 = -(P1[k] - T2[k]) * is;
+            const double s = (rowR1 + Asum * in_ - (im + in_) * Bsum + R3_(k) + T3 * in_) * imn;   // s_k
+            ss[k] = s;
+            red[0] += (k == mi - 1 ? dl : im) * s;
         }
         block_sum<4>(red, s_red);
         const double ds = red[0];
         red[0] = red[1] = red[2] = red[3] = 0.0;
-        for (int q = threadIdx.x; q < S; q += blockDim.x) {
-            const double dq = (q == S - 1 ? dl : im);
-            red[0] += -dq * ss[q] - dq * ds * iw;       // 1^T W-hat s
+        for (int k = threadIdx.x; k < mi; k += blockDim.x) {
+            const double dq = (k == mi - 1 ? dl : im);
+            red[0] += -dq * ss[k] - dq * ds * iw;       // 1^T W-hat s
         }
         block_sum<4>(red, s_red);
         const double tsum = red[0];
-        red[0] = red[1] = red[2] = red[3] = 0.0;
-        for (int q = threadIdx.x; q < S; q += blockDim.x) {
-            const double dq = (q == S - 1 ? dl : im);
-            red[0] += -dq * ss[q] - dq * ds * iw + tsum * in_;
-        }
-        block_sum<4>(red, s_red);
-        const double yasum = red[0];
+        const double yasum = tsum + m * tsum * in_;    // 1^T y1^a over k < m
         double* mv = I.mvec;
-        for (int q = threadIdx.x; q < S; q += blockDim.x) {
-            const double dq = (q == S - 1 ? dl : im);
-            const double ya = -dq * ss[q] - dq * ds * iw + tsum * in_;   // y1^a
-            const double aq = A_(q), bq = B_(q);
-            mv[q] = aq * in_ - (im + in_) * bq;
-            mv[S + q] = R3_(q) * in_ + T3 * in_ * in_ - (m + n) * ya;
-            mv[2 * S + q] = (aq - bq + T3 * in_) * in_ - yasum;
-            mv[3 * S + q] = ss[q] - n * ya;
+        for (int k = threadIdx.x; k < mi; k += blockDim.x) {
+            const double dq = (k == mi - 1 ? dl : im);
+            const double ya = -dq * ss[k] - dq * ds * iw + tsum * in_;   // y1^a_k
+            mv[L + k] = R3_(k) * in_ + T3 * in_ * in_ - (m + n) * ya;
+            mv[3 * L + k] = ss[k] - n * ya;
+        }
+        for (int j = threadIdx.x; j < ni; j += blockDim.x) {
+            const double aq = A_(j), bq = B_(j);
+            mv[j] = aq * in_ - (im + in_) * bq;
+            mv[2 * L + j] = (aq - bq + T3 * in_) * in_ - yasum;
         }
         __syncthreads();
     }
@@ -415,9 +418,7 @@ __global__ void __launch_bounds__(kThreads) k_marg(const WorkDev* __restrict__ W
 
 // Per-slab entries of dy = A^T-pieces of y-bar - y0.  The anchor part of R
 // (row sums and column totals of u) is precomputed once per cycle by
-// k_anchor; here only the delta's sums enter.  FP32 mode splits each full
-// piece a0 + dy into a part on the grid 2^-E and a remainder using FP32
-// arithmetic on top of the per-cycle split of a0.
+// k_anchor; here only the delta's sums enter.
 template <bool CHECK>
 __global__ void __launch_bounds__(kThreads) k_alpha(const WorkDev* __restrict__ W) {
     __shared__ double s_red[4 * 32];
@@ -439,18 +440,19 @@ __global__ void __launch_bounds__(kThreads) k_alpha(const WorkDev* __restrict__ 
         }
         const HotInst& I = W->inst[s_t[0]];
         const int slab = s_t[1];
-        const int S = I.S, nb = I.nb;
-        const double m = S, n = S;
+        const int mi = I.m, ni = I.n, L = g_L(I), Ls = g_side(I, slab), nb = g_nb(I, slab);
+        const double m = mi, n = ni;
         const double is = 1.0 / I.ctl->sigma;
         const double im = 1.0 / m, in_ = 1.0 / n, imn = 1.0 / (m + n);
         const double* __restrict__ rs = I.rs;
         const double* __restrict__ mv = I.mvec;
-        const double* __restrict__ R1a = I.R1a + (size_t)slab * S;
-        const double* __restrict__ kapa = I.kapa + (size_t)slab * S;
-        const size_t o = (size_t)slab * 2 * S;
+        const double* __restrict__ R1a = I.R1a + g_row(I, slab);
+        const double* __restrict__ kapa = I.kapa + g_row(I, slab);
+        const size_t o = 2 * g_row(I, slab);
+        const size_t f2 = (size_t)ni * mi;            // first row of the f2 half
         float ymax = 0.f;
         double dob = 0.0;
-        // idx < S: alpha (row) entries, idx >= S: beta (column) entries; returns the full piece
+        // idx < Ls: alpha (row) entries, idx >= Ls: beta (column) entries; returns the full piece
         auto put = [&](int idx, double dv) -> double {
             I.dab64[o + idx] = dv;
             const double full = I.ab0[o + idx] + dv;
@@ -460,39 +462,39 @@ __global__ void __launch_bounds__(kThreads) k_alpha(const WorkDev* __restrict__ 
         };
         auto kap_delta = [&](int c) -> double {           // column total of the delta over the bands
             double k = 0.0;
-            for (int b = 0; b < nb; ++b) k += I.cs_part[((size_t)slab * nb + b) * S + c];
+            for (int b = 0; b < nb; ++b) k += I.cs_part[g_colp(I, slab, b) + c];
             return k;
         };
-        if (slab < S) {
+        if (slab < ni) {
             const int j = slab;
             const double colj = mv[j];
-            for (int k = threadIdx.x; k < S; k += blockDim.x) {
-                const double R1 = R1a[k] - (rs[(size_t)j * S + k] - rs[(size_t)(S + k) * S + j]) * is;
-                put(k, (R1 + colj + mv[S + k]) * imn);         // y1(k, j)
+            for (int k = threadIdx.x; k < mi; k += blockDim.x) {
+                const double R1 = R1a[k] - (rs[(size_t)j * mi + k] - rs[f2 + (size_t)k * ni + j]) * is;
+                put(k, (R1 + colj + mv[L + k]) * imn);        // y1(k, j)
             }
-            const double sy = mv[2 * S + j];
-            for (int i = threadIdx.x; i < S; i += blockDim.x) {
+            const double sy = mv[2 * L + j];
+            for (int i = threadIdx.x; i < mi; i += blockDim.x) {
                 const double kap = kapa[i] + kap_delta(i);
-                const double mu = I.mu1[(size_t)i * S + j];
-                const double full = put(S + i, ((mu - kap) * is - sy) * im);   // y2(i, j)
+                const double mu = I.mu1[(size_t)i * ni + j];
+                const double full = put(Ls + i, ((mu - kap) * is - sy) * im);  // y2(i, j)
                 if (CHECK) dob += mu * full;                                    // <b, y>: mu1 . y2
             }
         } else {
-            const int k = slab - S;
-            const double rowk = mv[S + k];
-            for (int j = threadIdx.x; j < S; j += blockDim.x) {
-                const double R1 = R1a[j] - (rs[(size_t)j * S + k] - rs[(size_t)(S + k) * S + j]) * is;
+            const int k = slab - ni;
+            const double rowk = mv[L + k];
+            for (int j = threadIdx.x; j < ni; j += blockDim.x) {
+                const double R1 = R1a[j] - (rs[(size_t)j * mi + k] - rs[f2 + (size_t)k * ni + j]) * is;
                 put(j, -(R1 + mv[j] + rowk) * imn);            // -y1(k, j): A2 = -1_n^T kron I_M
             }
-            const double sp = mv[3 * S + k];
-            for (int l = threadIdx.x; l < S; l += blockDim.x) {
-                if (k == S - 1 && l == S - 1) {
-                    put(S + l, 0.0);                           // no row: y3(m, n) = 0
+            const double sp = mv[3 * L + k];
+            for (int l = threadIdx.x; l < ni; l += blockDim.x) {
+                if (k == mi - 1 && l == ni - 1) {
+                    put(Ls + l, 0.0);                          // no row: y3(m, n) = 0
                     continue;
                 }
                 const double kap = kapa[l] + kap_delta(l);
-                const double mu = I.mu2[(size_t)k * S + l];
-                const double full = put(S + l, ((mu - kap) * is + sp) * in_);  // y3(k, l)
+                const double mu = I.mu2[(size_t)k * ni + l];
+                const double full = put(Ls + l, ((mu - kap) * is + sp) * in_); // y3(k, l)
                 if (CHECK) dob += mu * full;                                    // mu2 . y3
             }
         }
@@ -541,51 +543,60 @@ __global__ void __launch_bounds__(kThreads) k_vec32(const WorkDev* __restrict__ 
         __syncthreads();
         if (s_t[2] == ST_RUNNING) {
             const HotInst& I = W->inst[s_t[0]];
-            const int S = I.S;
-            const int q8 = (S + 7) / 8, q32 = (S + 31) / 32, np = (S + kVecRows - 1) / kVecRows;
-            const int item = s_t[1];
+            const int m = I.m, n = I.n, L = g_L(I);
+            const int t1 = (n + 7) / 8, t2 = (m + 7) / 8;
+            const int c1 = (m + 31) / 32, r1 = (n + kVecRows - 1) / kVecRows;   // P1: columns k, rows j
+            const int c2 = (n + 31) / 32, r2 = (m + kVecRows - 1) / kVecRows;   // P2: columns j, rows k
+            const size_t f2 = (size_t)n * m;                 // first row of the f2 half
+            int item = s_t[1];
             const float2* __restrict__ rs = I.rs2;           // row sums of u + d
-            if (item < 2 * q8) {
-                const int which = item / q8;                 // 0: T1 (f1 slab totals), 1: T2
-                const int q = (item % q8) * 8 + warp;
-                if (q < S) {                                  // warp-uniform
-                    const float2* row = rs + (size_t)(which * S + q) * S;
+            if (item < t1 + t2) {
+                // T1[j]: the m rows of f1 slab j; T2[k]: the n rows of f2 slab k
+                const int which = item < t1 ? 0 : 1;
+                const int q = (which ? item - t1 : item) * 8 + warp;
+                const int cnt = which ? m : n, len = which ? n : m;
+                if (q < cnt) {                                // warp-uniform
+                    const float2* row = rs + (which ? f2 + (size_t)q * n : (size_t)q * m);
                     DF acc{0.f, 0.f};
-                    for (int t0 = 0; t0 < S; t0 += 8 * 32) {
+                    for (int t0 = 0; t0 < len; t0 += 8 * 32) {
                         float2 v[8];
 #pragma unroll
                         for (int u = 0; u < 8; ++u) {
                             const int t = t0 + u * 32 + lane;
-                            v[u] = t < S ? row[t] : make_float2(0.f, 0.f);
+                            v[u] = t < len ? row[t] : make_float2(0.f, 0.f);
                         }
 #pragma unroll
                         for (int u = 0; u < 8; ++u) acc = df_add(acc, df_ld(v[u]));
                     }
                     acc = warp_sum_df(acc);
-                    if (lane == 0) I.vec2[which * S + q] = df_st(acc);
+                    if (lane == 0) I.vec2[which * L + q] = df_st(acc);
                 }
             } else {
-                const int it2 = item - 2 * q8;
-                const int which = it2 / (q32 * np);          // 0: P1 (over f1 slabs), 1: P2
-                const int rem = it2 - which * q32 * np;
-                const int part = rem / q32;                  // row block
-                const int q = (rem - part * q32) * 32 + lane;
+                item -= t1 + t2;
+                // P1[k] = sum_j rs(f1 slab j)[k]; P2[j] = sum_k rs(f2 slab k)[j]:
+                // 32 columns x kVecRows rows per item, one partial per row block
+                const int which = item < c1 * r1 ? 0 : 1;
+                if (which) item -= c1 * r1;
+                const int ncol = which ? n : m, nrow = which ? m : n, nc = which ? c2 : c1;
+                const int part = item / nc;
+                const int q = (item - part * nc) * 32 + lane;
                 const int t0 = part * kVecRows + warp * kRW;
                 float2 v[kRW];
 #pragma unroll
                 for (int u = 0; u < kRW; ++u) {
                     const int t = t0 + u;
-                    v[u] = (q < S && t < S) ? rs[(size_t)(which * S + t) * S + q] : make_float2(0.f, 0.f);
+                    const size_t idx = which ? f2 + (size_t)t * n + q : (size_t)t * m + q;
+                    v[u] = (q < ncol && t < nrow) ? rs[idx] : make_float2(0.f, 0.f);
                 }
                 DF acc{0.f, 0.f};
 #pragma unroll
                 for (int u = 0; u < kRW; ++u) acc = df_add(acc, df_ld(v[u]));
                 s_p[threadIdx.x] = df_st(acc);
                 __syncthreads();
-                if (warp == 0 && q < S) {
+                if (warp == 0 && q < ncol) {
                     DF tot = df_ld(s_p[lane]);
                     for (int w = 1; w < kW; ++w) tot = df_add(tot, df_ld(s_p[w * 32 + lane]));
-                    I.vec2[2 * S + ((size_t)which * np + part) * S + q] = df_st(tot);
+                    I.vec2[(size_t)(2 + (which ? r1 : 0) + part) * L + q] = df_st(tot);
                 }
             }
         }
@@ -603,108 +614,125 @@ struct AlphaIn {
     float kd;             // column total of the delta over the bands
 };
 __device__ __forceinline__ AlphaIn alpha_in(const HotInst& I, int slab, int e, bool check) {
-    const int S = I.S, nb = I.nb;
+    const int m = I.m, n = I.n, Ls = g_side(I, slab), nb = g_nb(I, slab);
     AlphaIn a;
-    const bool f1 = slab < S;
-    const int j = f1 ? slab : e, k = f1 ? e : slab - S;
-    a.ra = I.rs2[(size_t)(S + k) * S + j];
-    a.rb = I.rs2[(size_t)j * S + k];
-    const size_t o = (size_t)slab * 2 * S;
+    const bool f1 = slab < n;
+    const int j = f1 ? slab : e, k = f1 ? e : slab - n;
+    a.ra = I.rs2[(size_t)n * m + (size_t)k * n + j];
+    a.rb = I.rs2[(size_t)j * m + k];
+    const size_t o = 2 * g_row(I, slab);
     a.a0r = I.ab0_32[o + e];
-    a.a0c = I.ab0_32[o + S + e];
-    a.k2 = I.K2[(size_t)slab * S + e];
-    a.mu = check ? (f1 ? I.mu1f[(size_t)e * S + slab] : I.mu2f[(size_t)(slab - S) * S + e]) : make_float2(0.f, 0.f);
+    a.a0c = I.ab0_32[o + Ls + e];
+    a.k2 = I.K2[g_row(I, slab) + e];
+    a.mu = check ? (f1 ? I.mu1f[(size_t)e * n + slab] : I.mu2f[(size_t)(slab - n) * n + e]) : make_float2(0.f, 0.f);
     float kd = 0.f;
-    for (int b = 0; b < nb; ++b) kd += I.cs32[((size_t)slab * nb + b) * S + e];
+    for (int b = 0; b < nb; ++b) kd += I.cs32[g_colp(I, slab, b) + e];
     a.kd = kd;
     return a;
 }
 
-// The instance-wide O(S) stage: from T1, T2, P1, P2 (k_vec32) the vectors
-//   mvA_q = a_q/n - (1/m + 1/n) bb_q      (column part of y1-hat)
-//   mvS_q = r3_q/n + T3/n^2 - (m+n) y1a_q (row part of y1, times m+n)
-//   sy_q  = sum_k y1(k, q)                (for y2)
-//   sp_q  = sum_j y1(q, j)                (for y3)
-// into sq[0..3][q].  With e_q = rowR1_q + r3_q and d the diagonal of W-hat,
-// every global scalar follows from four sums: sum a, sum bb, T3 = sum r3 and
-// sum d_q e_q, since s_q = (e_q + cst)/(m+n) with
+// The instance-wide O(m + n) stage: from T1, T2, P1, P2 (k_vec32) the vectors
+//   mvA_j = a_j/n - (1/m + 1/n) bb_j      (column part of y1-hat), j < n
+//   mvS_k = r3_k/n + T3/n^2 - (m+n) y1a_k (row part of y1, times m+n), k < m
+//   sy_j  = sum_k y1(k, j)                (for y2)
+//   sp_k  = sum_j y1(k, j)                (for y3)
+// into sq[0][j], sq[1][k], sq[2][j], sq[3][k].  With e_k = rowR1_k + r3_k and d
+// the diagonal of W-hat, every global scalar follows from four sums: sum a,
+// sum bb, T3 = sum r3 and sum d_k e_k, since s_k = (e_k + cst)/(m+n) with
 // cst = sum a/n - (1/m+1/n) sum bb + T3/n.  Each thread forms the scalars
 // from the block sums itself (no single-thread section, no extra barrier).
 struct StageIn {
-    float2 T1, T2, P1, P2, cm, rm;   // q = threadIdx.x (P1, P2: first row-block partial)
-    float kdl;                        // thread S-1: delta column total at the dropped (m, n) entry
+    float2 T1, P2, cm;    // j = threadIdx.x < n (P2: first row-block partial)
+    float2 T2, P1, rm;    // k = threadIdx.x < m (P1: first row-block partial)
+    float kdl;            // thread m-1: delta column total at the dropped (m, n) entry
 };
 __device__ __forceinline__ StageIn stage_in(const HotInst& I, int q) {
-    const int S = I.S, nb = I.nb;
+    const int m = I.m, n = I.n, L = g_L(I);
     const float2* __restrict__ v = I.vec2;
-    const int np = (S + kVecRows - 1) / kVecRows;
-    StageIn s;
-    s.T1 = v[q];
-    s.T2 = v[S + q];
-    s.P1 = v[2 * S + q];
-    s.P2 = v[2 * S + (size_t)np * S + q];
-    s.cm = I.cm2[q];
-    s.rm = I.rm2[q];
+    const int r1 = (n + kVecRows - 1) / kVecRows;      // row blocks of P1
+    StageIn s{};
+    if (q < n) {
+        s.T1 = v[q];
+        s.P2 = v[(size_t)(2 + r1) * L + q];
+        s.cm = I.cm2[q];
+    }
+    if (q < m) {
+        s.T2 = v[L + q];
+        s.P1 = v[2 * (size_t)L + q];
+        s.rm = I.rm2[q];
+    }
     s.kdl = 0.f;
-    if (q == S - 1)
-        for (int b = 0; b < nb; ++b) s.kdl += I.cs32[((size_t)(2 * S - 1) * nb + b) * S + (S - 1)];
+    if (q == m - 1) {
+        const int sl = g_nslab(I) - 1;
+        for (int b = 0; b < I.nb2; ++b) s.kdl += I.cs32[g_colp(I, sl, b) + (n - 1)];
+    }
     return s;
 }
 
 // The cycle constants are read where they are used (L1 broadcasts) rather
 // than held in registers.
 __device__ void alpha32_stage(const HotInst& I, const StageIn& pre, float2 (*sq)[kMaxS], float2* s_red) {
-    const int S = I.S;
+    const int m = I.m, n = I.n, L = g_L(I);
     const CycleK& C = *I.cyc;
     const float2* __restrict__ v = I.vec2;
-    const int np = (S + kVecRows - 1) / kVecRows;
+    const int r1 = (n + kVecRows - 1) / kVecRows, r2 = (m + kVecRows - 1) / kVecRows;
     const DF is = df_ld(C.is), im = df_ld(C.im), dl = df_ld(C.dl);
     const DF mk = df_ld(C.mk);
     DF red[4] = {DF{0.f, 0.f}, DF{0.f, 0.f}, DF{0.f, 0.f}, DF{0.f, 0.f}};
-    for (int q = threadIdx.x; q < S; q += blockDim.x) {
+    const int top = m > n ? m : n;
+    for (int q = threadIdx.x; q < top; q += blockDim.x) {
         const StageIn s = q == (int)threadIdx.x ? pre : stage_in(I, q);
-        const DF T1 = df_ld(s.T1), T2 = df_ld(s.T2);
-        DF P1 = df_ld(s.P1), P2 = df_ld(s.P2);
-        for (int b = 1; b < np; ++b) {
-            P1 = df_add(P1, df_ld(v[2 * S + (size_t)b * S + q]));
-            P2 = df_add(P2, df_ld(v[2 * S + (size_t)(np + b) * S + q]));
+        if (q < n) {                                               // column quantities, j = q
+            DF P2 = df_ld(s.P2);
+            for (int b = 1; b < r2; ++b) P2 = df_add(P2, df_ld(v[(size_t)(2 + r1 + b) * L + q]));
+            const DF T1 = df_ld(s.T1);
+            const DF A = df_mul(df_sub(P2, T1), is);                 // a_j = -(T1 - P2)/sigma
+            const DF B = df_mul(df_sub(df_ld(s.cm), T1), is);         // bb_j
+            sq[0][q] = df_st(A);
+            sq[2][q] = df_st(B);
+            red[0] = df_add(red[0], A);
+            red[1] = df_add(red[1], B);
         }
-        const DF A = df_mul(df_sub(P2, T1), is);                     // a_q = -(T1 - P2)/sigma
-        const DF B = df_mul(df_sub(df_ld(s.cm), T1), is);             // bb_q
-        DF R3 = df_mul(df_sub(df_ld(s.rm), T2), is);                  // r3_q
-        // the dropped (m, n) row of eq. (7): column S-1 of the last f2 slab
-        if (q == S - 1) R3 = df_sub(R3, df_mul(df_add(mk, -s.kdl), is));
-        const DF e = df_add(df_mul(df_sub(T2, P1), is), R3);          // rowR1_q + r3_q
-        sq[0][q] = df_st(A);
-        sq[1][q] = df_st(B);
-        sq[2][q] = df_st(R3);
-        sq[3][q] = df_st(e);
-        red[0] = df_add(red[0], A);
-        red[1] = df_add(red[1], B);
-        red[2] = df_add(red[2], R3);
-        red[3] = df_add(red[3], df_mul(e, q == S - 1 ? dl : im));
+        if (q < m) {                                               // row quantities, k = q
+            DF P1 = df_ld(s.P1);
+            for (int b = 1; b < r1; ++b) P1 = df_add(P1, df_ld(v[(size_t)(2 + b) * L + q]));
+            const DF T2 = df_ld(s.T2);
+            DF R3 = df_mul(df_sub(df_ld(s.rm), T2), is);              // r3_k
+            // the dropped (m, n) row of eq. (7): column n-1 of the last f2 slab
+            if (q == m - 1) R3 = df_sub(R3, df_mul(df_add(mk, -s.kdl), is));
+            const DF e = df_add(df_mul(df_sub(T2, P1), is), R3);      // rowR1_k + r3_k
+            sq[1][q] = df_st(R3);
+            sq[3][q] = df_st(e);
+            red[2] = df_add(red[2], R3);
+            red[3] = df_add(red[3], df_mul(e, q == m - 1 ? dl : im));
+        }
     }
     block_sum_df<4>(red, s_red);                 // ends with a barrier: sq is published too
     const DF in = df_ld(C.in), imn = df_ld(C.imn), imin = df_ld(C.imin);
     const DF T3 = red[2];
     const DF cst = df_add(df_sub(df_mul(red[0], in), df_mul(red[1], imin)), df_mul(T3, in));
     const DF sumd = df_ld(C.sumd);
-    const DF ds = df_mul(df_add(red[3], df_mul(cst, sumd)), imn);          // sum d_q s_q
+    const DF ds = df_mul(df_add(red[3], df_mul(cst, sumd)), imn);          // sum d_k s_k
     const DF dsiw = df_mul(ds, df_ld(C.iw));
     const DF tsum = df_neg(df_add(ds, df_mul(dsiw, sumd)));                // 1^T W-hat s
     const DF tin = df_mul(tsum, in);
-    const DF yasum = df_add(tsum, df_mul(tin, (float)S));                  // 1^T y1a
+    const DF yasum = df_add(tsum, df_mul(tin, (float)m));                  // 1^T y1a over k < m
     const DF T3in = df_mul(T3, in);
     const DF T3in2 = df_mul(T3in, in);
-    const float mpn = (float)(2 * S);
-    for (int q = threadIdx.x; q < S; q += blockDim.x) {
-        const DF A = df_ld(sq[0][q]), B = df_ld(sq[1][q]), R3 = df_ld(sq[2][q]), e = df_ld(sq[3][q]);
-        const DF sk = df_mul(df_add(e, cst), imn);                             // s_q
-        const DF ya = df_add(df_neg(df_mul(df_add(sk, dsiw), q == S - 1 ? dl : im)), tin);   // y1a_q
-        sq[0][q] = df_st(df_sub(df_mul(A, in), df_mul(B, imin)));
-        sq[1][q] = df_st(df_sub(df_add(df_mul(R3, in), T3in2), df_mul(ya, mpn)));
-        sq[2][q] = df_st(df_sub(df_mul(df_add(df_sub(A, B), T3in), in), yasum));
-        sq[3][q] = df_st(df_sub(sk, df_mul(ya, (float)S)));
+    const float mpn = (float)(m + n);
+    for (int q = threadIdx.x; q < top; q += blockDim.x) {
+        if (q < n) {
+            const DF A = df_ld(sq[0][q]), B = df_ld(sq[2][q]);
+            sq[0][q] = df_st(df_sub(df_mul(A, in), df_mul(B, imin)));                    // mvA_j
+            sq[2][q] = df_st(df_sub(df_mul(df_add(df_sub(A, B), T3in), in), yasum));     // sy_j
+        }
+        if (q < m) {
+            const DF R3 = df_ld(sq[1][q]), e = df_ld(sq[3][q]);
+            const DF sk = df_mul(df_add(e, cst), imn);                                 // s_k
+            const DF ya = df_add(df_neg(df_mul(df_add(sk, dsiw), q == m - 1 ? dl : im)), tin);   // y1a_k
+            sq[1][q] = df_st(df_sub(df_add(df_mul(R3, in), T3in2), df_mul(ya, mpn)));  // mvS_k
+            sq[3][q] = df_st(df_sub(sk, df_mul(ya, (float)n)));                        // sp_k
+        }
     }
     __syncthreads();
 }
@@ -730,30 +758,28 @@ __global__ void __launch_bounds__(kThreads, 3) k_alpha32(const WorkDev* __restri
         const HotInst& I = W->inst[inst];
         if (I.ctl->status != ST_RUNNING) continue;
         const int slab = t - W->pre_slab[inst];
-        const int S = I.S;
+        const int m = I.m, n = I.n, Ls = g_side(I, slab);
         // one round of loads: this thread's first entries, the cycle
         // constants and (for a new instance) the stage inputs
-        const bool have = tid < S;
         AlphaIn pin{};
-        if (have) pin = alpha_in(I, slab, tid, CHECK);
+        if (tid < Ls) pin = alpha_in(I, slab, tid, CHECK);
         const CycleK& C = *I.cyc;
         if (inst != cached) {
-            StageIn sin{};
-            if (have) sin = stage_in(I, tid);
+            const StageIn sin = stage_in(I, tid);
             alpha32_stage(I, sin, sq, s_red);
             cached = inst;
         }
         if (slab == 0 && tid == 0) *I.p32 = make_p32(I.ctl->sigma, I.ctl->k + j, I.h, I.gadmm, I.relax);
         const DF is = df_ld(C.is), imn = df_ld(C.imn);
-        const size_t o = (size_t)slab * 2 * S;
+        const size_t o = 2 * g_row(I, slab);
         const float igrid = (float)I.h, grid = 1.0f / igrid;       // powers of two: exact
         float ymax = 0.f;
         DF dob{0.f, 0.f};
         // <c, A^T(y-bar - y0)> of the slab: the cost is separable, so it is
         // sum_r dalpha_r C(r) + sum_c dbeta_c C(c), C(x) = sum_y (X_x - X_y)^2
         DF cdd{0.f, 0.f};
-        auto costsum = [&](int x) -> DF { return df_ld(I.csum2[(slab < S ? 0 : S) + x]); };
-        // idx < S: alpha (row) entries, idx >= S: beta (column) entries; returns the full piece on check iterations
+        const float2* csum = I.csum2 + g_xbase(I, slab);
+        // idx < Ls: alpha (row) entries, idx >= Ls: beta (column) entries; returns the full piece on check iterations
         auto put = [&](int idx, DF dv, float2 a0) -> DF {
             I.dab2[o + idx] = df_st(dv);
             const float df = df_f(dv);
@@ -763,14 +789,14 @@ __global__ void __launch_bounds__(kThreads, 3) k_alpha32(const WorkDev* __restri
             if (CHECK) {
                 full = df_add(DF{a0.x, a0.y}, dv);
                 ymax = fmaxf(ymax, fabsf(full.hi));
-                cdd = df_add(cdd, df_mul(dv, costsum(idx < S ? idx : idx - S)));
+                cdd = df_add(cdd, df_mul(dv, df_ld(csum[idx < Ls ? idx : idx - Ls])));
             }
             return full;
         };
-        const bool f1 = slab < S;
+        const bool f1 = slab < n;
         // row entries: f1 slab j gives y1(k, j) for every k, f2 slab k gives -y1(k, j) for every j
-        const DF fixed_row = f1 ? df_ld(sq[0][slab]) : df_ld(sq[1][slab - S]);
-        for (int e = tid; e < S; e += kThreads) {
+        const DF fixed_row = f1 ? df_ld(sq[0][slab]) : df_ld(sq[1][slab - n]);
+        for (int e = tid; e < Ls; e += kThreads) {
             const AlphaIn a = e == tid ? pin : alpha_in(I, slab, e, CHECK);
             // R1(k, j) = -(rowsum f1 slab j - rowsum f2 slab k)/sigma
             const DF R1 = df_mul(df_sub(df_ld(a.ra), df_ld(a.rb)), is);
@@ -779,16 +805,16 @@ __global__ void __launch_bounds__(kThreads, 3) k_alpha32(const WorkDev* __restri
             put(e, f1 ? y1 : df_neg(y1), a.a0r);
         }
         // column entries: y2(i, j) on f1 slab j, y3(k, l) on f2 slab k (y3(m, n) = 0)
-        const DF colc = f1 ? df_mul(df_ld(sq[2][slab]), df_neg(df_ld(C.im))) : df_mul(df_ld(sq[3][slab - S]), df_ld(C.in));
+        const DF colc = f1 ? df_mul(df_ld(sq[2][slab]), df_neg(df_ld(C.im))) : df_mul(df_ld(sq[3][slab - n]), df_ld(C.in));
         const DF isc = f1 ? df_ld(C.isim) : df_ld(C.isin);
-        for (int e = tid; e < S; e += kThreads) {
+        for (int e = tid; e < Ls; e += kThreads) {
             const AlphaIn a = e == tid ? pin : alpha_in(I, slab, e, CHECK);
-            if (!f1 && slab == 2 * S - 1 && e == S - 1) {
-                put(S + e, DF{0.f, 0.f}, a.a0c);
+            if (!f1 && slab == n + m - 1 && e == n - 1) {
+                put(Ls + e, DF{0.f, 0.f}, a.a0c);
                 continue;
             }
             const DF dv = df_add(df_sub(df_ld(a.k2), df_mul(isc, a.kd)), colc);
-            const DF full = put(S + e, dv, a.a0c);
+            const DF full = put(Ls + e, dv, a.a0c);
             if (CHECK) dob = df_add(dob, df_mul(df_ld(a.mu), full));
         }
         if (CHECK) {
@@ -809,10 +835,11 @@ __global__ void __launch_bounds__(kThreads, 3) k_alpha32(const WorkDev* __restri
 // right-hand side, per slab: R1a along the slab's rows and the column totals
 // of u.  One CTA per slab.
 __device__ __forceinline__ void anchor_slab(const HotInst& I, int slab, double sigma) {
-    const int S = I.S, nb = I.nb;
+    const int mi = I.m, ni = I.n, Ls = g_side(I, slab), nb = g_nb(I, slab);
     const double is = 1.0 / sigma;
+    const size_t f2 = (size_t)ni * mi;                // first row of the f2 half
     if (!I.fp64 && slab == 0 && threadIdx.x == 0) {
-        const double m = S, n = S;
+        const double m = mi, n = ni;
         const double dl = (1.0 - 1.0 / n) / (m + 1.0);
         CycleK& K = *I.cyc;
         K.is = df_st(df_from(is));
@@ -822,32 +849,33 @@ __device__ __forceinline__ void anchor_slab(const HotInst& I, int slab, double s
         K.imin = df_st(df_from(1.0 / m + 1.0 / n));
         K.iw = df_st(df_from(1.0 / (1.0 / m - dl)));       // 1/w, w = 1/m - (1-1/n)/(m+1)
         K.dl = df_st(df_from(dl));
-        K.sumd = df_st(df_from((S - 1) / m + dl));
+        K.sumd = df_st(df_from((mi - 1) / m + dl));
         K.isim = df_st(df_from(is / m));
         K.isin = df_st(df_from(is / n));
     }
-    for (int q = threadIdx.x; q < S; q += blockDim.x) {
+    const bool last = slab == g_nslab(I) - 1;
+    const size_t ro = g_row(I, slab);
+    for (int q = threadIdx.x; q < Ls; q += blockDim.x) {
         // f1 slab j: rows k, R1(k, j); f2 slab k: rows j, R1(k, j)
-        const int j = slab < S ? slab : q;
-        const int k = slab < S ? q : slab - S;
-        I.R1a[(size_t)slab * S + q] = -(I.rs0[(size_t)j * S + k] - I.rs0[(size_t)(S + k) * S + j]) * is;
+        const int j = slab < ni ? slab : q;
+        const int k = slab < ni ? q : slab - ni;
+        I.R1a[ro + q] = -(I.rs0[(size_t)j * mi + k] - I.rs0[f2 + (size_t)k * ni + j]) * is;
         double kap = 0.0;
-        for (int b = 0; b < nb; ++b) kap += I.cs0_part[((size_t)slab * nb + b) * S + q];
-        I.kapa[(size_t)slab * S + q] = kap;
+        for (int b = 0; b < nb; ++b) kap += I.cs0_part[g_colp(I, slab, b) + q];
+        I.kapa[ro + q] = kap;
         if (!I.fp64) {
             // pairs for the FP32-mode solve: the row sums of u (also those of
             // u + d, d = 0 at the anchor); K2 is the sigma-scaled anchor part
             // of y2 (f1 slab j, column i) resp. y3 (f2 slab k, column l)
-            const float2 r0 = df_st(df_from(I.rs0[(size_t)slab * S + q]));
-            I.rs02[(size_t)slab * S + q] = r0;
-            I.rs2[(size_t)slab * S + q] = r0;
-            if (slab == 2 * S - 1 && q == S - 1)
-                I.cyc->mk = df_st(df_from(I.mu2[(size_t)(S - 1) * S + (S - 1)] - kap));
+            const float2 r0 = df_st(df_from(I.rs0[ro + q]));
+            I.rs02[ro + q] = r0;
+            I.rs2[ro + q] = r0;
+            if (last && q == ni - 1) I.cyc->mk = df_st(df_from(I.mu2[(size_t)(mi - 1) * ni + (ni - 1)] - kap));
             double k2;
-            if (slab < S) k2 = (I.mu1[(size_t)q * S + slab] - kap) * is / S;
-            else if (slab == 2 * S - 1 && q == S - 1) k2 = 0.0;
-            else k2 = (I.mu2[(size_t)(slab - S) * S + q] - kap) * is / S;
-            I.K2[(size_t)slab * S + q] = df_st(df_from(k2));
+            if (slab < ni) k2 = (I.mu1[(size_t)q * ni + slab] - kap) * is / mi;
+            else if (last && q == ni - 1) k2 = 0.0;
+            else k2 = (I.mu2[(size_t)(slab - ni) * ni + q] - kap) * is / ni;
+            I.K2[ro + q] = df_st(df_from(k2));
         }
     }
 }
@@ -876,7 +904,7 @@ __global__ void __launch_bounds__(kThreads) k_anchor(const WorkDev* __restrict__
 }
 
 __global__ void __launch_bounds__(kThreads) k_anchor_one(HotInst I, double sigma) {
-    for (int slab = blockIdx.x; slab < 2 * I.S; slab += gridDim.x) anchor_slab(I, slab, sigma);
+    for (int slab = blockIdx.x; slab < g_nslab(I); slab += gridDim.x) anchor_slab(I, slab, sigma);
 }
 
 // --------------------------------------------------------------- k_sweep --
@@ -902,14 +930,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep64(const WorkDev* __restri
             continue;
         }
         const HotInst& I = W->inst[tc.inst];
-        const int S = I.S, nb = I.nb, TR = I.TR;
         const int slab = tc.slab, band = tc.band;
+        const int S = g_side(I, slab), TR = I.TR;        // this slab's side
         const int NC = S / NV;
         const int P = kThreads / NC;
         const int cg = threadIdx.x % NC, ro = threadIdx.x / NC;
         const bool active = ro < P;
         const int r0 = band * TR, r1 = min(S, r0 + TR);
-        const size_t off = (size_t)slab * S * S;
+        const size_t off = g_elem(I, slab);
         const double* __restrict__ u = (const double*)I.u + off;
         const double* __restrict__ din = (const double*)((j & 1) ? I.d1 : I.d0) + off;
         double* __restrict__ dout = (double*)((j & 1) ? I.d0 : I.d1) + off;
@@ -921,9 +949,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep64(const WorkDev* __restri
         for (int e = 0; e < NV; ++e) cacc[e] = xacc[e] = 0.0;
         double k64[kNK] = {0.0, 0.0, 0.0, 0.0, 0.0};
         const P64 p = s_p64;
-        const double* ab = I.ab64 + (size_t)slab * 2 * S;
-        const double* dab = I.dab64 + (size_t)slab * 2 * S;
-        const double* X = I.X64 + (slab < S ? 0 : S);          // bin coordinates of this half
+        const double* ab = I.ab64 + 2 * g_row(I, slab);
+        const double* dab = I.dab64 + 2 * g_row(I, slab);
+        const double* X = I.X64 + g_xbase(I, slab);            // bin coordinates of this half
         double bb[NV], db[NV], cf[NV];
 #pragma unroll
         for (int e = 0; e < NV; ++e) {
@@ -972,19 +1000,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep64(const WorkDev* __restri
             }
         }
         __syncthreads();
-        const size_t cbase = ((size_t)slab * nb + band) * S;
+        const size_t cbase = g_colp(I, slab, band);
         for (int c = threadIdx.x; c < S; c += blockDim.x) {
             I.cs_part[cbase + c] = sum_f64_strided(s_col + c, P, S);
             if (check) I.xcs_part[cbase + c] = sum_f64_strided(s_xcol + c, P, S);
         }
         for (int rr = threadIdx.x; rr < r1 - r0; rr += blockDim.x) {
-            I.rs[(size_t)slab * S + r0 + rr] = sum_f64_strided(s_row + rr * (NC + 1), NC, 1);
-            if (check) I.xrs[(size_t)slab * S + r0 + rr] = sum_f64_strided(s_xrow + rr * (NC + 1), NC, 1);
+            I.rs[g_row(I, slab) + r0 + rr] = sum_f64_strided(s_row + rr * (NC + 1), NC, 1);
+            if (check) I.xrs[g_row(I, slab) + r0 + rr] = sum_f64_strided(s_xrow + rr * (NC + 1), NC, 1);
         }
         if (check) {
             block_sum<kNK>(k64, s_red);
             if (threadIdx.x == 0) {
-                double* o = I.tile_kkt + ((size_t)slab * nb + band) * kNK;
+                double* o = I.tile_kkt + (size_t)g_tile(I, slab, band) * kNK;
 #pragma unroll
                 for (int q = 0; q < kNK; ++q) o[q] = k64[q];
             }
@@ -1021,13 +1049,12 @@ __device__ __forceinline__ TileD tile_desc(const WorkDev* __restrict__ W, int t,
     const HotInst& I = W->inst[i];
     const int loc = t - W->pre_tile[i];
     d.inst = i;
-    d.S = I.S;
-    d.slab = loc / I.nb;
-    d.band = loc - d.slab * I.nb;
-    d.NC = I.S / 4;
+    g_tile_slab(I, loc, d.slab, d.band);
+    d.S = g_side(I, d.slab);
+    d.NC = d.S / 4;
     d.P = kThreads / d.NC;
     d.r0 = d.band * I.TR;
-    d.r1 = min(I.S, d.r0 + I.TR);
+    d.r1 = min(d.S, d.r0 + I.TR);
     if (I.ctl->status == ST_RUNNING) d.npass = (d.r1 - d.r0 + d.P - 1) / d.P;
     return d;
 }
@@ -1074,10 +1101,10 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkD
         if (t < ntiles) {
             const HotInst& I = W->inst[d.inst];
             const int ro = tid / d.NC, cg = tid - ro * d.NC;
-            const size_t base = ((size_t)d.slab * d.S + d.r0 + ro) * d.S + (size_t)cg * NV;
+            const size_t base = g_elem(I, d.slab) + ((size_t)d.r0 + ro) * d.S + (size_t)cg * NV;
             c.u = (const float*)I.u + base;
             c.d = (const float*)((j & 1) ? I.d1 : I.d0) + base;
-            c.a = I.ab32 + (size_t)d.slab * 2 * d.S + d.r0;
+            c.a = I.ab32 + 2 * g_row(I, d.slab) + d.r0;
             c.step = d.P * d.S;
             c.row = ro < d.P ? ro : kMaxS;           // threads past P rows copy nothing
             c.P = d.P;
@@ -1123,7 +1150,7 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkD
         const HotInst& I = W->inst[d.inst];
         const int ro = tid / d.NC, c0 = (tid - ro * d.NC) * NV;
         p = *I.p32;
-        const float4* ab = I.ab32 + (size_t)d.slab * 2 * d.S + d.S;
+        const float4* ab = I.ab32 + 2 * g_row(I, d.slab) + d.S;
 #pragma unroll
         for (int e = 0; e < NV; ++e)
             bq[e] = ro < d.P ? ab[c0 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1140,20 +1167,20 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkD
         const TileD dc = s_td[ck % kStages];
         if (!have) load_cols(dc);
         const HotInst& I = W->inst[dc.inst];
-        const int S = dc.S, NC = dc.NC, P = dc.P, nb = I.nb;
+        const int S = dc.S, NC = dc.NC, P = dc.P;
         const int slab = dc.slab, band = dc.band, r0 = dc.r0, nr = dc.r1 - dc.r0;
         const int ro = tid / NC, cg = tid - ro * NC;
         const bool active = ro < P;
         const int c0 = cg * NV;
         const float h = p.h;
-        const float* X = I.X32 + (slab < S ? 0 : S);           // bin coordinates of this half
+        const float* X = I.X32 + g_xbase(I, slab);             // bin coordinates of this half
 #pragma unroll
         for (int e = 0; e < NV; ++e) {
             const float cf = active ? X[c0 + e] : 0.f;
             bq[e] = make_float4(fmaf(cf * cf, h, -bq[e].x), bq[e].y, bq[e].z, cf);
         }
         const float4* sa = s_alpha[ck % kStages];
-        float* __restrict__ dout = (float*)((j & 1) ? I.d0 : I.d1) + ((size_t)slab * S + r0 + ro) * S + c0;
+        float* __restrict__ dout = (float*)((j & 1) ? I.d0 : I.d1) + g_elem(I, slab) + ((size_t)r0 + ro) * S + c0;
         const int ostep = P * S;
         float* srow = s_row + ro * (NC + 1) + cg;
         float* sxrow = s_xrow + (CHECK ? ro * (NC + 1) + cg : 0);
@@ -1229,7 +1256,7 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkD
         // under the reductions below
         have = !(c.it >= ntiles && ck + 1 >= c.ik);
         if (have) load_cols(s_td[(ck + 1) % kStages]);
-        const size_t cbase = ((size_t)slab * nb + band) * S;
+        const size_t cbase = g_colp(I, slab, band);
         for (int cc = tid; cc < S; cc += kThreads) {
             DF a{0.f, 0.f}, x{0.f, 0.f};
             for (int qq = 0; qq < P; ++qq) {
@@ -1261,7 +1288,7 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkD
             kd[kNK - 1] = cd;
             block_sum_df<kNK>(kd, s_red);        // its barriers also publish s_rdf
             if (tid == 0) {
-                double* o = I.tile_kkt + ((size_t)slab * nb + band) * kNK;
+                double* o = I.tile_kkt + (size_t)g_tile(I, slab, band) * kNK;
 #pragma unroll
                 for (int qq = 0; qq < kNK; ++qq) o[qq] = df_val(kd[qq]);
             }
@@ -1276,9 +1303,9 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkD
                 a = df_add(a, df_ld(s_rdf[w][r]));
                 if constexpr (CHECK) x = df_add(x, df_ld(s_xdf[w][r]));
             }
-            a = df_add(a, df_ld(I.rs02[(size_t)slab * S + r0 + r]));      // + row sum of u
-            I.rs2[(size_t)slab * S + r0 + r] = df_st(a);
-            if constexpr (CHECK) I.xrs[(size_t)slab * S + r0 + r] = df_val(x);
+            a = df_add(a, df_ld(I.rs02[g_row(I, slab) + r0 + r]));      // + row sum of u
+            I.rs2[g_row(I, slab) + r0 + r] = df_st(a);
+            if constexpr (CHECK) I.xrs[g_row(I, slab) + r0 + r] = df_val(x);
         }
     }
     cp_async_wait<0>();
@@ -1299,13 +1326,13 @@ __device__ __forceinline__ void restart_tile(const HotInst& I, int slab, int ban
     using V = VecT<T>;
     constexpr int NV = V::N;
     constexpr bool F32 = std::is_same<T, float>::value;
-    const int S = I.S, nb = I.nb, TR = I.TR;
+    const int S = g_side(I, slab), TR = I.TR;        // this slab's side
     const int NC = S / NV;
     const int P = kThreads / NC;
     const int cg = threadIdx.x % NC, ro = threadIdx.x / NC;
     const bool active = ro < P;
     const int r0 = band * TR, r1 = min(S, r0 + TR);
-    const size_t off = (size_t)slab * S * S;
+    const size_t off = g_elem(I, slab);
     T* u = (T*)I.u + off;
     const T* d1 = (const T*)I.d1 + off;
     T* d0 = (T*)I.d0 + off;
@@ -1316,7 +1343,7 @@ __device__ __forceinline__ void restart_tile(const HotInst& I, int slab, int ban
     const double sig_old = (MODE == 1) ? I.ctl->sigma_old : I.ctl->sigma;
     const double sig_new = I.ctl->sigma;
     const int c0 = cg * NV;
-    const int xb0 = slab < S ? 0 : S;                // bin coordinates of this slab's half
+    const int xb0 = g_xbase(I, slab);                // bin coordinates of this slab's half
     // sums that feed later iterations: FP64 (FP64 mode) or double-float (FP32 mode)
     double racc[2] = {0.0, 0.0};
     DF fr[2] = {DF{0.f, 0.f}, DF{0.f, 0.f}};
@@ -1334,7 +1361,7 @@ __device__ __forceinline__ void restart_tile(const HotInst& I, int slab, int ban
             V::ld(d1 + (size_t)r * S + c0, dd);
             if constexpr (F32) {
                 const P32 p = make_p32(sig_old, 0, I.h);
-                const float4* ab = I.ab32 + (size_t)slab * 2 * S;
+                const float4* ab = I.ab32 + 2 * g_row(I, slab);
                 const float4 a = ab[r];
 #pragma unroll
                 for (int e = 0; e < NV; ++e) {
@@ -1345,8 +1372,8 @@ __device__ __forceinline__ void restart_tile(const HotInst& I, int slab, int ban
                 }
             } else {
                 const P64 p = make_p64(sig_old, 0, I.h);
-                const double* ab = I.ab64 + (size_t)slab * 2 * S;
-                const double* dab = I.dab64 + (size_t)slab * 2 * S;
+                const double* ab = I.ab64 + 2 * g_row(I, slab);
+                const double* dab = I.dab64 + 2 * g_row(I, slab);
                 const double a = ab[r], da = dab[r];
 #pragma unroll
                 for (int e = 0; e < NV; ++e) {
@@ -1417,7 +1444,7 @@ __device__ __forceinline__ void restart_tile(const HotInst& I, int slab, int ban
     if constexpr (MODE == 0) {
         block_sum<2>(racc, s_red);
         if (threadIdx.x == 0) {
-            double* o = I.rst_part + ((size_t)slab * nb + band) * 2;
+            double* o = I.rst_part + (size_t)g_tile(I, slab, band) * 2;
             o[0] = racc[0];
             o[1] = racc[1];
         }
@@ -1425,21 +1452,21 @@ __device__ __forceinline__ void restart_tile(const HotInst& I, int slab, int ban
         if constexpr (F32) {
             double cu[1] = {racc[0]};                     // df_val(fr[0]): <c, u> of this thread's share
             block_sum<1>(cu, s_red);
-            if (threadIdx.x == 0) I.cu_part[(size_t)slab * nb + band] = cu[0];
+            if (threadIdx.x == 0) I.cu_part[g_tile(I, slab, band)] = cu[0];
         }
         __syncthreads();
         if (active)
 #pragma unroll
             for (int e = 0; e < NV; ++e) s_col[ro * S + c0 + e] = ccol[e];
         __syncthreads();
-        const size_t cbase = ((size_t)slab * nb + band) * S;
+        const size_t cbase = g_colp(I, slab, band);
         for (int c = threadIdx.x; c < S; c += blockDim.x) {
             I.cs0_part[cbase + c] = sum_f64_strided(s_col + c, P, S);
             I.cs_part[cbase + c] = 0.0;
             I.cs32[cbase + c] = 0.f;
         }
         // y0 <- y-bar: A^T y0 pieces of this tile's rows (and, for band 0, columns)
-        const size_t o = (size_t)slab * 2 * S;
+        const size_t o = 2 * g_row(I, slab);
         auto set_anchor = [&](int idx) {
             const double a0 = I.ab0[o + idx] + (F32 ? df_val(df_ld(I.dab2[o + idx])) : I.dab64[o + idx]);
             I.ab0[o + idx] = a0;
@@ -1449,8 +1476,8 @@ __device__ __forceinline__ void restart_tile(const HotInst& I, int slab, int ban
             }
         };
         for (int rr = threadIdx.x; rr < r1 - r0; rr += blockDim.x) {
-            I.rs0[(size_t)slab * S + r0 + rr] = sum_f64_strided(s_row + rr * NC, NC, 1);
-            if (!F32) I.rs[(size_t)slab * S + r0 + rr] = 0.0;      // FP32: k_anchor resets rs2
+            I.rs0[g_row(I, slab) + r0 + rr] = sum_f64_strided(s_row + rr * NC, NC, 1);
+            if (!F32) I.rs[g_row(I, slab) + r0 + rr] = 0.0;      // FP32: k_anchor resets rs2
             set_anchor(r0 + rr);
         }
         if (band == 0)
@@ -1495,16 +1522,18 @@ __global__ void __launch_bounds__(kThreads) k_init(HotInst I, double sigma0) {
     __shared__ double s_row[kRowSmemBytes / 8 * 2];
     __shared__ double s_col[kThreads * 4];
     __shared__ double s_red[32];
-    const int S = I.S, nb = I.nb, TR = I.TR;
-    const int NC = S / NV;
-    const int P = kThreads / NC;
-    const int cg = threadIdx.x % NC, ro = threadIdx.x / NC;
-    const bool active = ro < P;
-    const int c0 = cg * NV;
-    for (int t = blockIdx.x; t < 2 * S * nb; t += gridDim.x) {
-        const int slab = t / nb, band = t % nb;
+    const int TR = I.TR;
+    for (int t = blockIdx.x; t < g_ntiles(I); t += gridDim.x) {
+        int slab, band;
+        g_tile_slab(I, t, slab, band);
+        const int S = g_side(I, slab);                 // this slab's side
+        const int NC = S / NV;
+        const int P = kThreads / NC;
+        const int cg = threadIdx.x % NC, ro = threadIdx.x / NC;
+        const bool active = ro < P;
+        const int c0 = cg * NV;
         const int r0 = band * TR, r1 = min(S, r0 + TR);
-        const size_t off = (size_t)slab * S * S;
+        const size_t off = g_elem(I, slab);
         DF cuf{0.f, 0.f};
         double ccol[NV];
         DF fcol[NV];
@@ -1520,7 +1549,7 @@ __global__ void __launch_bounds__(kThreads) k_init(HotInst I, double sigma0) {
                 double rs = 0.0;
 #pragma unroll
                 for (int e = 0; e < NV; ++e) {
-                    const int xb0 = slab < S ? 0 : S;
+                    const int xb0 = g_xbase(I, slab);
                     const double dc = I.X64[xb0 + r] - I.X64[xb0 + c0 + e];
                     uu[e] = (T)(-sigma0 * (dc * dc * I.h));
                     zero[e] = T(0);
@@ -1550,14 +1579,14 @@ __global__ void __launch_bounds__(kThreads) k_init(HotInst I, double sigma0) {
 #pragma unroll
             for (int e = 0; e < NV; ++e) s_col[ro * S + c0 + e] = ccol[e];
         __syncthreads();
-        const size_t cbase = ((size_t)slab * nb + band) * S;
+        const size_t cbase = g_colp(I, slab, band);
         for (int c = threadIdx.x; c < S; c += blockDim.x) I.cs0_part[cbase + c] = sum_f64_strided(s_col + c, P, S);
         for (int rr = threadIdx.x; rr < r1 - r0; rr += blockDim.x)
-            I.rs0[(size_t)slab * S + r0 + rr] = sum_f64_strided(s_row + rr * NC, NC, 1);
+            I.rs0[g_row(I, slab) + r0 + rr] = sum_f64_strided(s_row + rr * NC, NC, 1);
         if constexpr (std::is_same<T, float>::value) {
             double cu[1] = {df_val(cuf)};
             block_sum<1>(cu, s_red);
-            if (threadIdx.x == 0) I.cu_part[(size_t)slab * nb + band] = cu[0];
+            if (threadIdx.x == 0) I.cu_part[g_tile(I, slab, band)] = cu[0];
         }
         __syncthreads();
     }
@@ -1583,25 +1612,25 @@ __global__ void __launch_bounds__(kThreads) k_kkt1(const WorkDev* __restrict__ W
             continue;
         }
         const HotInst& I = W->inst[s_t[0]];
-        const int S = I.S, nb = I.nb;
-        const int SS = S * S;
+        const int m = I.m, n = I.n;
+        const int MN = m * n;
         const int q = s_t[1] * kThreads + threadIdx.x;
         double v[1] = {0.0};
-        if (q < 3 * SS - 1) {
+        if (q < 3 * MN - 1) {
             double res;
-            if (q < SS) {
-                const int j = q / S, k = q % S;
-                res = I.xrs[(size_t)j * S + k] - I.xrs[(size_t)(S + k) * S + j];
-            } else if (q < 2 * SS) {
-                const int j = (q - SS) / S, i = (q - SS) % S;
+            if (q < MN) {                                  // conservation rows (k, j)
+                const int j = q / m, k = q % m;
+                res = I.xrs[(size_t)j * m + k] - I.xrs[(size_t)MN + (size_t)k * n + j];
+            } else if (q < 2 * MN) {                       // mu1 rows (i, j)
+                const int j = (q - MN) / m, i = (q - MN) % m;
                 double kap = 0.0;
-                for (int b = 0; b < nb; ++b) kap += I.xcs_part[((size_t)j * nb + b) * S + i];
-                res = kap - I.mu1[(size_t)i * S + j];
-            } else {
-                const int k = (q - 2 * SS) / S, l = (q - 2 * SS) % S;
+                for (int b = 0; b < I.nb1; ++b) kap += I.xcs_part[g_colp(I, j, b) + i];
+                res = kap - I.mu1[(size_t)i * n + j];
+            } else {                                       // mu2 rows (k, l), the last one dropped
+                const int k = (q - 2 * MN) / n, l = (q - 2 * MN) % n;
                 double kap = 0.0;
-                for (int b = 0; b < nb; ++b) kap += I.xcs_part[((size_t)(S + k) * nb + b) * S + l];
-                res = kap - I.mu2[(size_t)k * S + l];
+                for (int b = 0; b < I.nb2; ++b) kap += I.xcs_part[g_colp(I, n + k, b) + l];
+                res = kap - I.mu2[(size_t)k * n + l];
             }
             v[0] = res * res;
         }
@@ -1621,15 +1650,14 @@ __global__ void __launch_bounds__(kThreads) k_check(const WorkDev* __restrict__ 
         const HotInst& I = W->inst[i];
         HotCtl* C = I.ctl;
         if (C->status != ST_RUNNING) continue;   // block-uniform
-        const int S = I.S, nb = I.nb;
-        const int ntile = 2 * S * nb;
+        const int ntile = g_ntiles(I), nslab = g_nslab(I);
         double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         for (int q = threadIdx.x; q < ntile; q += blockDim.x) {
             for (int e = 0; e < kNK; ++e) v[e] += I.tile_kkt[(size_t)q * kNK + e];
             if (!I.fp64) v[7] += I.cu_part[q];
         }
         for (int q = threadIdx.x; q < I.n_k1; q += blockDim.x) v[5] += I.k1_part[q];
-        for (int q = threadIdx.x; q < 2 * S; q += blockDim.x) {
+        for (int q = threadIdx.x; q < nslab; q += blockDim.x) {
             v[6] += I.dobj_part[q];
             if (!I.fp64) v[4] += C->sigma * I.cD_part[q];
         }
@@ -1696,7 +1724,7 @@ __global__ void __launch_bounds__(kThreads) k_restart_sigma(const WorkDev* __res
         const HotInst& I = W->inst[i];
         HotCtl* C = I.ctl;
         if (C->status != ST_RUNNING || !C->restart_pending) continue;
-        const int ntile = 2 * I.S * I.nb;
+        const int ntile = g_ntiles(I);
         double v[2] = {0.0, 0.0};
         for (int q = threadIdx.x; q < ntile; q += blockDim.x) {
             v[0] += I.rst_part[(size_t)q * 2];
@@ -1778,11 +1806,11 @@ void launch_init(const HotInst& I, double sigma0, cudaStream_t st) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int tiles = 2 * I.S * I.nb;
+    const int tiles = g_ntiles(I);
     const int grid = tiles < sms * 4 ? tiles : sms * 4;
     if (I.fp64) k_init<double><<<grid, kThreads, 0, st>>>(I, sigma0);
     else k_init<float><<<grid, kThreads, 0, st>>>(I, sigma0);
-    k_anchor_one<<<2 * I.S < sms * 4 ? 2 * I.S : sms * 4, kThreads, 0, st>>>(I, sigma0);
+    k_anchor_one<<<g_nslab(I) < sms * 4 ? g_nslab(I) : sms * 4, kThreads, 0, st>>>(I, sigma0);
 }
 
 cudaError_t kernels_init(int device) {

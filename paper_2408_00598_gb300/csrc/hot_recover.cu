@@ -12,7 +12,9 @@
 // search and walks forward; entries are written in (node, i, l) order.
 // Flows are clipped at 0 first (an approximate solution may have small
 // negative entries).  In the slab layout both a and b are contiguous rows:
-// a = row k of f1 slab j, b = row j of f2 slab k.
+// a = row k of f1 slab j (m sources i), b = row j of f2 slab k (n sinks l).
+// A plan entry runs from source bin (i, j), index i n + j of mu, to target bin
+// (k, l), index k n + l of nu.
 #include "hot_engine.h"
 #include "hot_df.cuh"
 
@@ -20,26 +22,35 @@ namespace hot {
 
 constexpr int kRecWarps = 8;
 
-// shared memory of one warp in k_recover_df, in floats: a, b (S floats each,
-// padded to an even count) and the pairs A, B (S + 1 each)
-__host__ __device__ constexpr size_t recover_df_words(int S) { return 2 * (size_t)S + (S & 1) + 4 * ((size_t)S + 1); }
+// shared memory of one warp in k_recover_df, in floats: a (m floats), b (n
+// floats), padded to an even count, and the pairs A (m + 1), B (n + 1)
+__host__ __device__ constexpr size_t recover_df_words(int m, int n) {
+    return (size_t)m + n + ((m + n) & 1) + 2 * ((size_t)m + 1) + 2 * ((size_t)n + 1);
+}
+// the same for k_recover, in doubles
+__host__ __device__ constexpr size_t recover_words(int m, int n) { return 2 * ((size_t)m + n) + 2; }
+
+// first entries of f1 row k of slab j and of f2 row j of slab k
+__device__ __forceinline__ size_t node_row_a(int m, int k, int j) { return ((size_t)j * m + k) * m; }
+__device__ __forceinline__ size_t node_row_b(int m, int n, int k, int j) {
+    return (size_t)n * m * m + ((size_t)k * n + j) * n;
+}
 
 template <typename T>
-__device__ __forceinline__ void load_node(const T* __restrict__ x, int S, int k, int j, double* a, double* b,
+__device__ __forceinline__ void load_node(const T* __restrict__ x, int m, int n, int k, int j, double* a, double* b,
                                           double* A, double* B) {
     const int lane = threadIdx.x & 31;
-    const T* ra = x + ((size_t)j * S + k) * S;            // f1 slab j, row k
-    const T* rb = x + ((size_t)(S + k) * S + j) * S;      // f2 slab k, row j
-    for (int t = lane; t < S; t += 32) {
-        a[t] = fmax((double)ra[t], 0.0);
-        b[t] = fmax((double)rb[t], 0.0);
-    }
+    const T* ra = x + node_row_a(m, k, j);
+    const T* rb = x + node_row_b(m, n, k, j);
+    for (int t = lane; t < m; t += 32) a[t] = fmax((double)ra[t], 0.0);
+    for (int t = lane; t < n; t += 32) b[t] = fmax((double)rb[t], 0.0);
     __syncwarp();
     // exclusive prefix sums, sequential per 32-chunk with a warp scan (FP64)
     double carryA = 0.0, carryB = 0.0;
-    for (int base = 0; base < S; base += 32) {
+    const int L = m > n ? m : n;
+    for (int base = 0; base < L; base += 32) {
         const int t = base + lane;
-        double va = t < S ? a[t] : 0.0, vb = t < S ? b[t] : 0.0;
+        double va = t < m ? a[t] : 0.0, vb = t < n ? b[t] : 0.0;
         double sa = va, sb = vb;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -50,35 +61,33 @@ __device__ __forceinline__ void load_node(const T* __restrict__ x, int S, int k,
                 sb += yb;
             }
         }
-        if (t < S) {
-            A[t] = carryA + sa - va;
-            B[t] = carryB + sb - vb;
-        }
+        if (t < m) A[t] = carryA + sa - va;
+        if (t < n) B[t] = carryB + sb - vb;
         carryA += __shfl_sync(0xffffffffu, sa, 31);
         carryB += __shfl_sync(0xffffffffu, sb, 31);
     }
     if (lane == 0) {
-        A[S] = carryA;
-        B[S] = carryB;
+        A[m] = carryA;
+        B[n] = carryB;
     }
     __syncwarp();
 }
 
-// number of sinks overlapping source i (and optionally write them)
-__device__ __forceinline__ int node_source(int S, int i, const double* A, const double* B, const double* b,
+// number of sinks (of n) overlapping source i (and optionally write them)
+__device__ __forceinline__ int node_source(int n, int i, const double* A, const double* B, const double* b,
                                            int32_t* src, int32_t* dst, double* mass, size_t pos, int src_id,
-                                           int node_k, int node_j, int n) {
+                                           int node_k) {
     const double lo = A[i];
-    const double hi = fmin(A[i + 1], B[S]);
+    const double hi = fmin(A[i + 1], B[n]);
     if (!(hi > lo)) return 0;
     // first l with B[l+1] > lo
-    int l0 = 0, l1 = S - 1;
+    int l0 = 0, l1 = n - 1;
     while (l0 < l1) {
         const int mid = (l0 + l1) >> 1;
         if (B[mid + 1] > lo) l1 = mid; else l0 = mid + 1;
     }
     int cnt = 0;
-    for (int l = l0; l < S && B[l] < hi; ++l) {
+    for (int l = l0; l < n && B[l] < hi; ++l) {
         const double p = fmin(hi, B[l + 1]) - fmax(lo, B[l]);
         if (p > 0.0 && b[l] > 0.0) {
             if (src) {
@@ -93,7 +102,7 @@ __device__ __forceinline__ int node_source(int S, int i, const double* A, const 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kRecWarps * 32) k_recover(const T* __restrict__ x, int S, int count_only,
+__global__ void __launch_bounds__(kRecWarps * 32) k_recover(const T* __restrict__ x, int m, int n, int count_only,
                                                             int* __restrict__ counts,
                                                             const long long* __restrict__ offs,
                                                             int32_t* __restrict__ src, int32_t* __restrict__ dst,
@@ -102,43 +111,44 @@ __global__ void __launch_bounds__(kRecWarps * 32) k_recover(const T* __restrict_
     extern __shared__ double sh[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nw = blockDim.x >> 5;
-    double* a = sh + (size_t)warp * (4 * S + 2);
-    double* b = a + S;
-    double* A = b + S;
-    double* B = A + S + 1;
-    const int nodes = S * S;
+    double* a = sh + (size_t)warp * recover_words(m, n);
+    double* b = a + m;
+    double* A = b + n;
+    double* B = A + m + 1;
+    const int nodes = m * n;
     for (int node = blockIdx.x * nw + warp; node < nodes; node += gridDim.x * nw) {
-        const int k = node / S, j = node % S;    // k-major node order
-        load_node(x, S, k, j, a, b, A, B);
+        const int k = node / n, j = node % n;    // k-major node order
+        load_node(x, m, n, k, j, a, b, A, B);
         if (count_only) {
             int c = 0;
-            for (int i = lane; i < S; i += 32)
-                c += node_source(S, i, A, B, b, nullptr, nullptr, nullptr, 0, 0, k, j, S);
+            for (int i = lane; i < m; i += 32) c += node_source(n, i, A, B, b, nullptr, nullptr, nullptr, 0, 0, k);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
             if (lane == 0) counts[node] = c;
             // marginals of the plan: source (i, j) gets min(a_i, max(0, Btot - A_i)),
             // target (k, l) gets min(b_l, max(0, Atot - B_l))
-            for (int t = lane; t < S; t += 32) {
-                const double ga = fmin(a[t], fmax(0.0, B[S] - A[t]));
-                const double gb = fmin(b[t], fmax(0.0, A[S] - B[t]));
-                if (ga > 0.0) atomicAdd(&marg1[(size_t)t * S + j], ga);
-                if (gb > 0.0) atomicAdd(&marg2[(size_t)k * S + t], gb);
+            for (int t = lane; t < m; t += 32) {
+                const double ga = fmin(a[t], fmax(0.0, B[n] - A[t]));
+                if (ga > 0.0) atomicAdd(&marg1[(size_t)t * n + j], ga);
+            }
+            for (int t = lane; t < n; t += 32) {
+                const double gb = fmin(b[t], fmax(0.0, A[m] - B[t]));
+                if (gb > 0.0) atomicAdd(&marg2[(size_t)k * n + t], gb);
             }
         } else {
             long long pos = offs[node];
-            for (int base = 0; base < S; base += 32) {
+            for (int base = 0; base < m; base += 32) {
                 const int i = base + lane;
                 int c = 0;
-                if (i < S) c = node_source(S, i, A, B, b, nullptr, nullptr, nullptr, 0, 0, k, j, S);
+                if (i < m) c = node_source(n, i, A, B, b, nullptr, nullptr, nullptr, 0, 0, k);
                 int incl = c;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
                     const int y = __shfl_up_sync(0xffffffffu, incl, o);
                     if (lane >= o) incl += y;
                 }
-                if (i < S && c > 0)
-                    node_source(S, i, A, B, b, src, dst, mass, (size_t)(pos + incl - c), i * S + j, k, j, S);
+                if (i < m && c > 0)
+                    node_source(n, i, A, B, b, src, dst, mass, (size_t)(pos + incl - c), i * n + j, k);
                 pos += __shfl_sync(0xffffffffu, incl, 31);
             }
         }
@@ -161,20 +171,19 @@ __device__ __forceinline__ DF df_shfl(DF a, int l) {
     return DF{__shfl_sync(0xffffffffu, a.hi, l), __shfl_sync(0xffffffffu, a.lo, l)};
 }
 
-__device__ __forceinline__ void load_node_df(const float* __restrict__ x, int S, int k, int j, float* a, float* b,
-                                             float2* A, float2* B) {
+__device__ __forceinline__ void load_node_df(const float* __restrict__ x, int m, int n, int k, int j, float* a,
+                                             float* b, float2* A, float2* B) {
     const int lane = threadIdx.x & 31;
-    const float* ra = x + ((size_t)j * S + k) * S;        // f1 slab j, row k
-    const float* rb = x + ((size_t)(S + k) * S + j) * S;  // f2 slab k, row j
-    for (int t = lane; t < S; t += 32) {
-        a[t] = fmaxf(ra[t], 0.f);
-        b[t] = fmaxf(rb[t], 0.f);
-    }
+    const float* ra = x + node_row_a(m, k, j);
+    const float* rb = x + node_row_b(m, n, k, j);
+    for (int t = lane; t < m; t += 32) a[t] = fmaxf(ra[t], 0.f);
+    for (int t = lane; t < n; t += 32) b[t] = fmaxf(rb[t], 0.f);
     __syncwarp();
     DF ca{0.f, 0.f}, cb{0.f, 0.f};
-    for (int base = 0; base < S; base += 32) {
+    const int L = m > n ? m : n;
+    for (int base = 0; base < L; base += 32) {
         const int t = base + lane;
-        DF sa{t < S ? a[t] : 0.f, 0.f}, sb{t < S ? b[t] : 0.f, 0.f};
+        DF sa{t < m ? a[t] : 0.f, 0.f}, sb{t < n ? b[t] : 0.f, 0.f};
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const DF ya = df_shfl_up(sa, o), yb = df_shfl_up(sb, o);
@@ -185,38 +194,36 @@ __device__ __forceinline__ void load_node_df(const float* __restrict__ x, int S,
         }
         DF ea = df_shfl_up(sa, 1), eb = df_shfl_up(sb, 1);       // exclusive within the chunk
         if (lane == 0) ea = eb = DF{0.f, 0.f};
-        if (t < S) {
-            A[t] = df_st(df_add(ca, ea));
-            B[t] = df_st(df_add(cb, eb));
-        }
+        if (t < m) A[t] = df_st(df_add(ca, ea));
+        if (t < n) B[t] = df_st(df_add(cb, eb));
         ca = df_add(ca, df_shfl(sa, 31));
         cb = df_add(cb, df_shfl(sb, 31));
     }
     if (lane == 0) {
-        A[S] = df_st(ca);
-        B[S] = df_st(cb);
+        A[m] = df_st(ca);
+        B[n] = df_st(cb);
     }
     __syncwarp();
 }
 
-__device__ __forceinline__ int node_source_df(int S, int i, const float2* A, const float2* B, const float* b,
+__device__ __forceinline__ int node_source_df(int n, int i, const float2* A, const float2* B, const float* b,
                                               int32_t* src, int32_t* dst, double* mass, size_t pos, int src_id,
                                               int node_k) {
     const DF lo = df_ld(A[i]);
-    const DF hi = df_min(df_ld(A[i + 1]), df_ld(B[S]));
+    const DF hi = df_min(df_ld(A[i + 1]), df_ld(B[n]));
     if (!df_lt(lo, hi)) return 0;
-    int l0 = 0, l1 = S - 1;                               // first l with B[l+1] > lo
+    int l0 = 0, l1 = n - 1;                               // first l with B[l+1] > lo
     while (l0 < l1) {
         const int mid = (l0 + l1) >> 1;
         if (df_lt(lo, df_ld(B[mid + 1]))) l1 = mid; else l0 = mid + 1;
     }
     int cnt = 0;
-    for (int l = l0; l < S && df_lt(df_ld(B[l]), hi); ++l) {
+    for (int l = l0; l < n && df_lt(df_ld(B[l]), hi); ++l) {
         const DF p = df_sub(df_min(hi, df_ld(B[l + 1])), df_max(lo, df_ld(B[l])));
         if (df_pos(p) && b[l] > 0.f) {
             if (src) {
                 src[pos + cnt] = src_id;
-                dst[pos + cnt] = node_k * S + l;
+                dst[pos + cnt] = node_k * n + l;
                 mass[pos + cnt] = df_val(p);
             }
             ++cnt;
@@ -225,7 +232,8 @@ __device__ __forceinline__ int node_source_df(int S, int i, const float2* A, con
     return cnt;
 }
 
-__global__ void __launch_bounds__(kRecWarps * 32) k_recover_df(const float* __restrict__ x, int S, int count_only,
+__global__ void __launch_bounds__(kRecWarps * 32) k_recover_df(const float* __restrict__ x, int m, int n,
+                                                               int count_only,
                                                                int* __restrict__ counts,
                                                                const long long* __restrict__ offs,
                                                                int32_t* __restrict__ src, int32_t* __restrict__ dst,
@@ -234,43 +242,48 @@ __global__ void __launch_bounds__(kRecWarps * 32) k_recover_df(const float* __re
     extern __shared__ float4 shdf[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nw = blockDim.x >> 5;
-    const size_t per = recover_df_words(S);              // floats per warp
+    const size_t per = recover_df_words(m, n);           // floats per warp
     float* a = reinterpret_cast<float*>(shdf) + (size_t)warp * per;
-    float* b = a + S;
-    float2* A = reinterpret_cast<float2*>(b + S + (S & 1));
-    float2* B = A + S + 1;
-    const int nodes = S * S;
+    float* b = a + m;
+    float2* A = reinterpret_cast<float2*>(b + n + ((m + n) & 1));
+    float2* B = A + m + 1;
+    const int nodes = m * n;
     for (int node = blockIdx.x * nw + warp; node < nodes; node += gridDim.x * nw) {
-        const int k = node / S, j = node % S;    // k-major node order
-        load_node_df(x, S, k, j, a, b, A, B);
+        const int k = node / n, j = node % n;    // k-major node order
+        load_node_df(x, m, n, k, j, a, b, A, B);
         if (count_only) {
             int c = 0;
-            for (int i = lane; i < S; i += 32) c += node_source_df(S, i, A, B, b, nullptr, nullptr, nullptr, 0, 0, k);
+            for (int i = lane; i < m; i += 32) c += node_source_df(n, i, A, B, b, nullptr, nullptr, nullptr, 0, 0, k);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
             if (lane == 0) counts[node] = c;
-            const DF At = df_ld(A[S]), Bt = df_ld(B[S]);
-            for (int t = lane; t < S; t += 32) {
-                DF ra = df_sub(Bt, df_ld(A[t])), rb = df_sub(At, df_ld(B[t]));
+            const DF At = df_ld(A[m]), Bt = df_ld(B[n]);
+            for (int t = lane; t < m; t += 32) {
+                DF ra = df_sub(Bt, df_ld(A[t]));
                 if (!df_pos(ra)) ra = DF{0.f, 0.f};
+                const DF ga = df_min(DF{a[t], 0.f}, ra);
+                if (df_pos(ga)) atomicAdd(&marg1[(size_t)t * n + j], df_val(ga));
+            }
+            for (int t = lane; t < n; t += 32) {
+                DF rb = df_sub(At, df_ld(B[t]));
                 if (!df_pos(rb)) rb = DF{0.f, 0.f};
-                const DF ga = df_min(DF{a[t], 0.f}, ra), gb = df_min(DF{b[t], 0.f}, rb);
-                if (df_pos(ga)) atomicAdd(&marg1[(size_t)t * S + j], df_val(ga));
-                if (df_pos(gb)) atomicAdd(&marg2[(size_t)k * S + t], df_val(gb));
+                const DF gb = df_min(DF{b[t], 0.f}, rb);
+                if (df_pos(gb)) atomicAdd(&marg2[(size_t)k * n + t], df_val(gb));
             }
         } else {
             long long pos = offs[node];
-            for (int base = 0; base < S; base += 32) {
+            for (int base = 0; base < m; base += 32) {
                 const int i = base + lane;
                 int c = 0;
-                if (i < S) c = node_source_df(S, i, A, B, b, nullptr, nullptr, nullptr, 0, 0, k);
+                if (i < m) c = node_source_df(n, i, A, B, b, nullptr, nullptr, nullptr, 0, 0, k);
                 int incl = c;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
                     const int y = __shfl_up_sync(0xffffffffu, incl, o);
                     if (lane >= o) incl += y;
                 }
-                if (i < S && c > 0) node_source_df(S, i, A, B, b, src, dst, mass, (size_t)(pos + incl - c), i * S + j, k);
+                if (i < m && c > 0)
+                    node_source_df(n, i, A, B, b, src, dst, mass, (size_t)(pos + incl - c), i * n + j, k);
                 pos += __shfl_sync(0xffffffffu, incl, 31);
             }
         }
@@ -319,26 +332,26 @@ __global__ void k_marg_l1(const double* __restrict__ marg, const double* __restr
 }
 
 // x-bar from the slab layout into the paper's vec order (eq. 4-6):
-// f1_{i,k,j} at i + S k + S^2 j (same as slab j, row k, col i);
-// f2_{k,j,l} at S^3 + k + S j + S^2 l (slab S+k, row j, col l).
+// f1_{i,k,j} at i + m k + m^2 j (same as slab j, row k, col i);
+// f2_{k,j,l} at n m^2 + k + m j + m n l (slab n + k, row j, col l).
 template <typename T>
-__global__ void k_export(const T* __restrict__ x, int S, double* __restrict__ out) {
-    const size_t SS = (size_t)S * S;
-    const size_t half = SS * S;
-    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < 2 * half; q += (size_t)gridDim.x * blockDim.x) {
+__global__ void k_export(const T* __restrict__ x, int m, int n, double* __restrict__ out) {
+    const size_t half = (size_t)m * m * n, nn = (size_t)n * n;
+    const size_t V = half + (size_t)m * nn;
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < V; q += (size_t)gridDim.x * blockDim.x) {
         if (q < half) {
             out[q] = (double)x[q];
         } else {
-            const size_t p = q - half;            // internal f2 index: k*SS + j*S + l
-            const size_t k = p / SS, j = (p / S) % S, l = p % S;
-            out[half + k + S * j + SS * l] = (double)x[q];
+            const size_t p = q - half;            // internal f2 index: k n^2 + j n + l
+            const size_t k = p / nn, j = (p / n) % n, l = p % n;
+            out[half + k + (size_t)m * j + (size_t)m * n * l] = (double)x[q];
         }
     }
 }
 
 int export_flows(Inst* I, double* x, int space, cudaStream_t st) {
-    const int S = I->S;
-    const size_t V = 2ull * S * S * S;
+    const int m = I->m, n = I->n;
+    const size_t V = (size_t)m * n * (m + n);
     double* dst = x;
     double* tmp = nullptr;
     if (space == HOT_SPACE_HOST) {
@@ -346,8 +359,8 @@ int export_flows(Inst* I, double* x, int space, cudaStream_t st) {
         dst = tmp;
     }
     const int grid = 1024;
-    if (I->fp64) k_export<double><<<grid, 256, 0, st>>>((const double*)I->desc.xr, S, dst);
-    else k_export<float><<<grid, 256, 0, st>>>((const float*)I->desc.xr, S, dst);
+    if (I->fp64) k_export<double><<<grid, 256, 0, st>>>((const double*)I->desc.xr, m, n, dst);
+    else k_export<float><<<grid, 256, 0, st>>>((const float*)I->desc.xr, m, n, dst);
     HOT_CK(cudaGetLastError());
     if (tmp) {
         HOT_CK(cudaMemcpyAsync(x, tmp, V * 8, cudaMemcpyDeviceToHost, st));
@@ -360,8 +373,8 @@ int export_flows(Inst* I, double* x, int space, cudaStream_t st) {
 int recover_plan(Ctx* ctx, Inst* I, int32_t* src, int32_t* dst, double* mass, int space, size_t cap, size_t* nnz,
                  double* marg_l1, cudaStream_t st) {
     (void)ctx;
-    const int S = I->S;
-    const int nodes = S * S;
+    const int m = I->m, n = I->n;
+    const int nodes = m * n;
     int* counts = nullptr;
     long long* offs = nullptr;
     unsigned long long* dtot = nullptr;
@@ -373,9 +386,10 @@ int recover_plan(Ctx* ctx, Inst* I, int32_t* src, int32_t* dst, double* mass, in
     HOT_CK(cudaMallocAsync(&marg, sizeof(double) * 2 * nodes, st));
     HOT_CK(cudaMallocAsync(&l1, sizeof(double) * 2, st));
     HOT_CK(cudaMemsetAsync(marg, 0, sizeof(double) * 2 * nodes, st));
-    // warps per CTA: each holds a, b and their prefix sums (4S + 2 doubles;
-    // FP32 mode: 2S floats and 2(S + 1) float pairs)
-    const size_t per_warp = I->fp64 ? (4 * (size_t)S + 2) * sizeof(double) : recover_df_words(S) * sizeof(float);
+    // warps per CTA: each holds a, b and their prefix sums (2(m + n) + 2
+    // doubles; FP32 mode: m + n floats and m + n + 2 float pairs)
+    const size_t per_warp =
+        I->fp64 ? recover_words(m, n) * sizeof(double) : recover_df_words(m, n) * sizeof(float);
     const int nw = std::max(1, std::min(kRecWarps, (int)((200 * 1024) / per_warp)));
     const size_t shm = (size_t)nw * per_warp;
     static bool attr_set = false;
@@ -388,10 +402,10 @@ int recover_plan(Ctx* ctx, Inst* I, int32_t* src, int32_t* dst, double* mass, in
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
     const int grid = std::max(1, std::min((nodes + nw - 1) / nw, sms * 8));
     if (I->fp64)
-        k_recover<double><<<grid, nw * 32, shm, st>>>((const double*)I->desc.xr, S, 1, counts, nullptr,
+        k_recover<double><<<grid, nw * 32, shm, st>>>((const double*)I->desc.xr, m, n, 1, counts, nullptr,
                                                               nullptr, nullptr, nullptr, marg, marg + nodes);
     else
-        k_recover_df<<<grid, nw * 32, shm, st>>>((const float*)I->desc.xr, S, 1, counts, nullptr, nullptr, nullptr,
+        k_recover_df<<<grid, nw * 32, shm, st>>>((const float*)I->desc.xr, m, n, 1, counts, nullptr, nullptr, nullptr,
                                                  nullptr, marg, marg + nodes);
     HOT_CK(cudaGetLastError());
     k_scan<<<1, 1024, 0, st>>>(counts, offs, nodes, dtot);
@@ -419,10 +433,10 @@ int recover_plan(Ctx* ctx, Inst* I, int32_t* src, int32_t* dst, double* mass, in
                 HOT_CK(cudaMallocAsync(&dm, sizeof(double) * tot, st));
             }
             if (I->fp64)
-                k_recover<double><<<grid, nw * 32, shm, st>>>((const double*)I->desc.xr, S, 0, counts, offs,
+                k_recover<double><<<grid, nw * 32, shm, st>>>((const double*)I->desc.xr, m, n, 0, counts, offs,
                                                                       ds, dd, dm, nullptr, nullptr);
             else
-                k_recover_df<<<grid, nw * 32, shm, st>>>((const float*)I->desc.xr, S, 0, counts, offs, ds, dd, dm,
+                k_recover_df<<<grid, nw * 32, shm, st>>>((const float*)I->desc.xr, m, n, 0, counts, offs, ds, dd, dm,
                                                          nullptr, nullptr);
             HOT_CK(cudaGetLastError());
             if (space == HOT_SPACE_HOST) {

@@ -52,18 +52,21 @@ struct ServeState {
     std::vector<double> lat_ms, queue_ms;
 };
 
-static int serve_tile_rows(Ctx* ctx, int S, int fp64) {
-    const int t = tuned_tile_rows(ctx, S, fp64);
-    return t ? t : tile_rows(S, fp64, sweep_grid(fp64));
+static int serve_tile_rows(Ctx* ctx, int m, int n, int fp64) {
+    const int t = tuned_tile_rows(ctx, m, n, fp64);
+    return t ? t : tile_rows(m, n, fp64, sweep_grid(fp64));
 }
 
-static size_t inst_bytes_estimate(Ctx* ctx, int S, int fp64) {
-    const size_t V = 2ull * S * S * S;
+// Device bytes of one instance (an upper bound of inst_create's layout).
+static size_t inst_bytes_estimate(Ctx* ctx, int m, int n, int fp64) {
+    const size_t MN = (size_t)m * n;
+    const size_t V = MN * (size_t)(m + n);
     const size_t big = 5 * (V * (fp64 ? 8 : 4) + 256);
-    const int tr = serve_tile_rows(ctx, S, fp64);
-    const size_t nb = (S + tr - 1) / tr;
-    size_t small = (size_t)S * S * (8 * 4 + 8 * 4 + 8 * 6 * nb + 8 * 2 + 16) + 1024 * 64;
-    if (!fp64) small += (size_t)S * S * (112 + 8 * nb);       // double-float arrays of FP32 mode
+    const int tr = serve_tile_rows(ctx, m, n, fp64);
+    const size_t CP = (size_t)n * ((m + tr - 1) / tr) * m + (size_t)m * ((n + tr - 1) / tr) * n;
+    // pieces 3 x 32 MN, slab-row sums 5 x 16 MN, marginals 16 MN, column partials 28 CP
+    size_t small = MN * (96 + 80 + 16) + CP * 28 + 1024 * 64;
+    if (!fp64) small += MN * 192;       // double-float arrays of FP32 mode
     return big + small;
 }
 
@@ -111,7 +114,7 @@ static void serve_loop(Ctx* ctx) {
                     finish_req(ctx, s, r, HOT_ECANCELLED);
                     continue;
                 }
-                const size_t need = inst_bytes_estimate(ctx, r->pair.S, fp64);
+                const size_t need = inst_bytes_estimate(ctx, r->pair.m, r->pair.n, fp64);
                 if (s->in_use + need > s->budget) {
                     if (s->active.empty() && admit.empty() && s->in_use == 0) {
                         // can never fit
@@ -137,7 +140,7 @@ static void serve_loop(Ctx* ctx) {
         for (Req* r : admit) {
             Inst* I = nullptr;
             r->t_admit = Clock::now();
-            const int rc = inst_create(r->pair, fp64, ctx->cfg, r->tol, r->max_iter, tuned_tile_rows(ctx, r->pair.S, fp64), s->st, &I);
+            const int rc = inst_create(r->pair, fp64, ctx->cfg, r->tol, r->max_iter, tuned_tile_rows(ctx, r->pair.m, r->pair.n, fp64), s->st, &I);
             std::lock_guard<std::mutex> g(s->mu);
             if (rc != HOT_OK) {
                 s->in_use -= std::min(s->in_use, r->bytes);

@@ -164,6 +164,14 @@ def _ptr(a):
     return arr.ctypes.data, HOT_SPACE_HOST, arr
 
 
+def _grid(mu, nu):
+    """(m, n) of a histogram pair; both must be 2-D arrays of the same shape."""
+    if len(mu.shape) != 2 or tuple(nu.shape) != tuple(mu.shape):
+        raise HotError(HOT_EINVAL, "mu and nu must be 2-D arrays of the same shape, got %s and %s"
+                       % (tuple(mu.shape), tuple(nu.shape)))
+    return int(mu.shape[0]), int(mu.shape[1])
+
+
 # ----------------------------------------------------------- C-named calls --
 
 def hot_config_default():
@@ -233,7 +241,7 @@ def hot_solve(ctx, mu, nu, tol=1e-6, max_iter=100000):
     pn, sn, kn = _ptr(nu)
     if sm != sn:
         raise HotError(HOT_EINVAL, "mu and nu must live in the same space")
-    m, n = mu.shape
+    m, n = _grid(mu, nu)
     res = hot_result()
     rc = lib.hot_solve(ctx, pm, pn, m, n, sm, float(tol), int(max_iter), ctypes.byref(res))
     if rc not in (HOT_OK, HOT_NOT_CONVERGED):
@@ -248,7 +256,7 @@ def hot_solve_coords(ctx, mu, nu, xs, ys, tol=1e-6, max_iter=100000):
     pn, sn, kn = _ptr(nu)
     if sm != sn:
         raise HotError(HOT_EINVAL, "mu and nu must live in the same space")
-    m, n = mu.shape
+    m, n = _grid(mu, nu)
     ax = np.ascontiguousarray(xs, dtype=np.float64)
     ay = np.ascontiguousarray(ys, dtype=np.float64)
     if ax.shape != (m,) or ay.shape != (n,):
@@ -266,7 +274,7 @@ def hot_solve_profiled(ctx, mu, nu, tol=1e-6, max_iter=100000):
     lib = load_library()
     pm, sm, km = _ptr(mu)
     pn, sn, kn = _ptr(nu)
-    m, n = mu.shape
+    m, n = _grid(mu, nu)
     res = hot_result()
     kt = hot_kernel_times()
     rc = lib.hot_solve_profiled(ctx, pm, pn, m, n, sm, float(tol), int(max_iter), ctypes.byref(res),
@@ -293,7 +301,7 @@ def hot_solve_batch(ctx, mus, nus, tol=1e-6, max_iter=100000):
         if s1 != space or s2 != space:
             raise HotError(HOT_EINVAL, "all histograms must live in the same space")
         pm[q], pn[q] = p1, p2
-        ms[q], ns[q] = a.shape
+        ms[q], ns[q] = _grid(a, b)
     out = (hot_result * len(mus))()
     rc = lib.hot_solve_batch(ctx, len(mus), pm, pn, ms, ns, space or 0, float(tol), int(max_iter), out)
     if rc != HOT_OK:
@@ -368,6 +376,7 @@ def hot_submit(ctx, mu, nu, tol=1e-6, max_iter=100000, keep_solution=False):
     lib = load_library()
     a = np.ascontiguousarray(mu, dtype=np.float64)
     b = np.ascontiguousarray(nu, dtype=np.float64)
+    _grid(a, b)
     req = hot_request(a.ctypes.data, b.ctypes.data, a.shape[0], a.shape[1], float(tol), int(max_iter),
                       1 if keep_solution else 0)
     t = ctypes.c_ulonglong()

@@ -163,7 +163,8 @@ def test_invalid_inputs_are_rejected(lib, ctx32):
     bad /= bad.sum()
     nan = good1.copy()
     nan[3, 3] = np.nan
-    cases = [(bad, good2), (good1 * 1.01, good2), (nan, good2), (good1[:, :12] / good1[:, :12].sum(), good2[:, :12]),
+    cases = [(bad, good2), (good1 * 1.01, good2), (nan, good2), (good1, good2[:, :12] / good2[:, :12].sum()),
+             (good1[:, :10] / good1[:, :10].sum(), good2[:, :10] / good2[:, :10].sum()),
              (syn.make_pair("white", 6, 1)[0], syn.make_pair("white", 6, 1)[1]),
              (syn.make_pair("white", 10, 1)[0], syn.make_pair("white", 10, 1)[1])]
     for a, b in cases:
