@@ -40,10 +40,11 @@ SWEEP_TRAFFIC = {"kernels_sha256": None, "bytes_per_launch": None}
 
 # iterations of Algorithm 2 (with the restart rule) that the FP64 oracle takes
 # to rel-KKT tol on the default bench pair (synthetic.make_pair("white", 256,
-# 1000)): oracle.hot.hot_solve(mu1, mu2, tol=1e-6) -> 450 iterations, 12
-# restarts, rel-KKT 9.1177e-7, 1269 s on one x86 core.  Used to extrapolate
-# the oracle's per-iteration time to a full solve.
-ITERS_PER_SOLVE = {(256, "white", 1e-6): 450}
+# 1000)): oracle.hot.hot_solve(mu1, mu2, tol=1e-6) -> 440 iterations, 12
+# restarts, rel-KKT 9.7194e-7, 1028 s on one x86 core (sigma rounded to the
+# grid 2^(j/16) at restarts).  Used to extrapolate the oracle's per-iteration
+# time to a full solve.
+ITERS_PER_SOLVE = {(256, "white", 1e-6): 440}
 
 
 def parse():
