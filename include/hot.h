@@ -216,6 +216,21 @@ typedef struct hot_kernel_times {
 HOT_API int hot_solve_profiled(hot_ctx *ctx, const double *mu, const double *nu, int m, int n, int space,
                        double tol, long long max_iter, hot_result *out, hot_kernel_times *kt);
 
+/* Live timing of the dominant kernel, the fused Steps 2-4 sweep of a
+ * non-check iteration (the paper has no counterpart; it measures the kernel
+ * inside the production path, not in a separate profiled run).  enable = 1:
+ * later single-instance hot_solve calls on this context launch block graphs
+ * that carry a CUDA event pair around one non-check sweep per block of
+ * check_every iterations (check_every >= 2), and add each measured duration
+ * to the context's counters; enable = 0: plain graphs again; enable = -1:
+ * the mode is left as it is.  Every call returns the counters accumulated
+ * since the previous call, then resets them: *total_ms the summed durations,
+ * *launches the number of timed sweeps, *bytes their algorithmic bytes
+ * (12 B per flow variable in FP32 bulk mode, 24 B in FP64 mode).  Output
+ * pointers (host) may be NULL.  Batches, the serve loop and
+ * hot_solve_profiled are never timed this way. */
+HOT_API int hot_sweep_timing(hot_ctx *ctx, int enable, double *total_ms, long long *launches, double *bytes);
+
 /* Algorithm 1 without any device allocation (the paper has no counterpart;
  * this exists for callers that cannot let a library allocate device memory at
  * call time: code with a fixed, pre-accounted device-memory footprint, or a

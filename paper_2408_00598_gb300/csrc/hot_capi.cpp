@@ -227,6 +227,29 @@ int hot_solve_profiled(hot_ctx* ctx, const double* mu, const double* nu, int m, 
     HOT_GUARD_END
 }
 
+int hot_sweep_timing(hot_ctx* ctx, int enable, double* total_ms, long long* launches, double* bytes) {
+    HOT_GUARD_BEGIN
+    if (!ctx) {
+        set_error("ctx is NULL");
+        return HOT_EINVAL;
+    }
+    if (enable < -1 || enable > 1) {
+        set_error("enable must be -1, 0 or 1");
+        return HOT_EINVAL;
+    }
+    hot::Ctx& x = ctx->impl;
+    std::lock_guard<std::mutex> g(x.mu);
+    if (total_ms) *total_ms = x.st_ms;
+    if (launches) *launches = x.st_launches;
+    if (bytes) *bytes = x.st_bytes;
+    x.st_ms = 0.0;
+    x.st_bytes = 0.0;
+    x.st_launches = 0;
+    if (enable >= 0) x.sweep_timing = enable;
+    return HOT_OK;
+    HOT_GUARD_END
+}
+
 int hot_solve_batch(hot_ctx* ctx, int count, const double* const* mus, const double* const* nus, const int* ms,
                     const int* ns, int space, double tol, long long max_iter, hot_result* out) {
     HOT_GUARD_BEGIN

@@ -154,6 +154,8 @@ int inst_create(const PairHost& p, int fp64, const hot_config& cfg, double tol, 
     const int ntiles = n * I->nb1 + m * I->nb2;
     const size_t CP = (size_t)n * I->nb1 * m + (size_t)m * I->nb2 * n;   // column-partial entries
     const int NS = m + n;                                                  // slabs
+    const int n_achunk = (int)((4 * MN + kAlphaChunk - 1) / kAlphaChunk);   // k_alpha32 chunks
+    const size_t NPART = (size_t)std::max(NS, n_achunk);                   // <b, y> partials
     size_t off = 0;
     auto take = [&](size_t bytes) {
         size_t o = off;
@@ -199,9 +201,9 @@ int inst_create(const PairHost& p, int fp64, const hot_config& cfg, double tol, 
     const size_t o_cm = take(n * 8);
     const size_t o_rm = take(m * 8);
     const size_t o_k1 = take((size_t)I->n_k1 * 8);
-    const size_t o_dp = take((size_t)NS * 8);
+    const size_t o_dp = take(NPART * 8);
     const size_t o_cu = take((size_t)ntiles * 8);
-    const size_t o_cD = take((size_t)NS * 8);
+    const size_t o_cD = take(NPART * 8);
     const size_t o_ctl = take(sizeof(HotCtl));
     I->small_bytes = off;
 
@@ -223,6 +225,7 @@ int inst_create(const PairHost& p, int fp64, const hot_config& cfg, double tol, 
     d.nb1 = I->nb1;
     d.nb2 = I->nb2;
     d.n_k1 = I->n_k1;
+    d.n_achunk = n_achunk;
     d.fp64 = fp64;
     d.gadmm = cfg.method == HOT_METHOD_GADMM ? 1 : 0;
     d.stop_abs = cfg.stop_rule == HOT_STOP_ABSOLUTE ? 1 : 0;
@@ -397,6 +400,11 @@ void inst_destroy(Inst* I, cudaStream_t st) {
 
 Batch::~Batch() {
     if (graph) cudaGraphExecDestroy(graph);
+    for (int p = 0; p < 2; ++p) {
+        if (tgraph[p]) cudaGraphExecDestroy(tgraph[p]);
+        for (int q = 0; q < 2; ++q)
+            if (tev[p][q]) cudaEventDestroy(tev[p][q]);
+    }
     if (cap_stream) cudaStreamDestroy(cap_stream);
     cudaFree(d_work);
     cudaFree(d_inst);
@@ -413,11 +421,16 @@ Batch::~Batch() {
 int Batch::reserve(int n) {
     if (n <= cap && d_work) return HOT_OK;
     int ncap = std::max(n, std::max(16, cap * 2));
-    // the graph captured the old table pointers
+    // the graphs captured the old table pointers
     if (graph) {
         cudaGraphExecDestroy(graph);
         graph = nullptr;
     }
+    for (int p = 0; p < 2; ++p)
+        if (tgraph[p]) {
+            cudaGraphExecDestroy(tgraph[p]);
+            tgraph[p] = nullptr;
+        }
     cudaFree(d_work);
     cudaFree(d_inst);
     cudaFree(d_pre);
@@ -431,13 +444,13 @@ int Batch::reserve(int n) {
     d_work = nullptr;
     HOT_CK(cudaMalloc(&d_work, sizeof(WorkDev)));
     HOT_CK(cudaMalloc(&d_inst, sizeof(HotInst) * ncap));
-    HOT_CK(cudaMalloc(&d_pre, sizeof(int) * 4 * (ncap + 1)));
+    HOT_CK(cudaMalloc(&d_pre, sizeof(int) * kPreTables * (ncap + 1)));
     HOT_CK(cudaMalloc(&d_running, sizeof(int)));
     HOT_CK(cudaMalloc(&d_st, sizeof(int) * ncap));
     HOT_CK(cudaMallocHost(&h_st, sizeof(int) * ncap));
     HOT_CK(cudaMallocHost(&h_work, sizeof(WorkDev)));
     HOT_CK(cudaMallocHost(&h_inst, sizeof(HotInst) * ncap));
-    HOT_CK(cudaMallocHost(&h_pre, sizeof(int) * 4 * (ncap + 1)));
+    HOT_CK(cudaMallocHost(&h_pre, sizeof(int) * kPreTables * (ncap + 1)));
     HOT_CK(cudaMallocHost(&h_running, sizeof(int) * 4));
     cap = ncap;
     return HOT_OK;
@@ -453,7 +466,8 @@ int Batch::set_instances(const std::vector<Inst*>& v, cudaStream_t st) {
     int* ps = h_pre + (cap + 1);
     int* pv = h_pre + 2 * (cap + 1);
     int* pk = h_pre + 3 * (cap + 1);
-    pt[0] = ps[0] = pv[0] = pk[0] = 0;
+    int* pa = h_pre + 4 * (cap + 1);
+    pt[0] = ps[0] = pv[0] = pk[0] = pa[0] = 0;
     int running = 0;
     for (int i = 0; i < n; ++i) {
         h_inst[i] = v[i]->desc;
@@ -462,6 +476,7 @@ int Batch::set_instances(const std::vector<Inst*>& v, cudaStream_t st) {
         ps[i + 1] = ps[i] + m + nn;
         pv[i + 1] = pv[i] + (v[i]->fp64 ? 2 * (m + nn) : vec32_items(m, nn));
         pk[i + 1] = pk[i] + v[i]->n_k1;
+        pa[i + 1] = pa[i] + v[i]->desc.n_achunk;
         if (v[i]->ctl_host.status == ST_RUNNING) ++running;
     }
     h_work->ninst = n;
@@ -470,12 +485,13 @@ int Batch::set_instances(const std::vector<Inst*>& v, cudaStream_t st) {
     h_work->pre_slab = d_pre + (cap + 1);
     h_work->pre_vec = d_pre + 2 * (cap + 1);
     h_work->pre_k1 = d_pre + 3 * (cap + 1);
+    h_work->pre_achunk = d_pre + 4 * (cap + 1);
     h_work->n_running = d_running;
     h_work->st_out = d_st;
     for (int i = 0; i < n; ++i) h_st[i] = v[i]->ctl_host.status;
     h_running[0] = running;
     if (n > 0) HOT_CK(cudaMemcpyAsync(d_inst, h_inst, sizeof(HotInst) * n, cudaMemcpyHostToDevice, st));
-    HOT_CK(cudaMemcpyAsync(d_pre, h_pre, sizeof(int) * 4 * (cap + 1), cudaMemcpyHostToDevice, st));
+    HOT_CK(cudaMemcpyAsync(d_pre, h_pre, sizeof(int) * kPreTables * (cap + 1), cudaMemcpyHostToDevice, st));
     HOT_CK(cudaMemcpyAsync(d_work, h_work, sizeof(WorkDev), cudaMemcpyHostToDevice, st));
     HOT_CK(cudaMemcpyAsync(d_running, h_running, sizeof(int), cudaMemcpyHostToDevice, st));
     if (n > 0) HOT_CK(cudaMemcpyAsync(d_st, h_st, sizeof(int) * n, cudaMemcpyHostToDevice, st));
@@ -483,12 +499,17 @@ int Batch::set_instances(const std::vector<Inst*>& v, cudaStream_t st) {
     return HOT_OK;
 }
 
-int Batch::ensure_graph() {
-    if (graph) return HOT_OK;
-    if (!cap_stream) HOT_CK(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
-    ld = make_launch_dims(device, fp64);
+// One check block (K iterations plus the block end) captured into *out; with
+// ev, an event pair recorded around the sweep of iteration timed_iter().
+int Batch::capture(cudaGraphExec_t* out, cudaEvent_t* ev) {
     HOT_CK(cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal));
-    for (int j = 0; j < K; ++j) launch_iteration(d_work, ld, fp64, j, j == K - 1, cap_stream);
+    for (int j = 0; j < K; ++j) {
+        launch_solve_kernels(d_work, ld, fp64, j, j == K - 1, cap_stream);
+        const bool t = ev && j == timed_iter() && j < K - 1;
+        if (t) cudaEventRecordWithFlags(ev[0], cap_stream, cudaEventRecordExternal);
+        launch_sweep(d_work, ld, fp64, j, j == K - 1, cap_stream);
+        if (t) cudaEventRecordWithFlags(ev[1], cap_stream, cudaEventRecordExternal);
+    }
     launch_block_end(d_work, ld, fp64, K, a1, a2, a3, cap_stream);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(cap_stream, &g);
@@ -496,18 +517,35 @@ int Batch::ensure_graph() {
         set_error(std::string("graph capture failed: ") + cudaGetErrorString(e));
         return HOT_ECUDA;
     }
-    e = cudaGraphInstantiate(&graph, g, 0);
+    e = cudaGraphInstantiate(out, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
-        graph = nullptr;
+        *out = nullptr;
         set_error(std::string("graph instantiation failed: ") + cudaGetErrorString(e));
         return HOT_ECUDA;
     }
     return HOT_OK;
 }
 
-int Batch::launch_block(cudaStream_t st) const {
-    HOT_CK(cudaGraphLaunch(graph, st));
+int Batch::ensure_graph(int want_timing) {
+    timing = want_timing && K >= 2 ? 1 : 0;
+    if (timing ? (tgraph[0] && tgraph[1]) : graph != nullptr) return HOT_OK;
+    if (!cap_stream) HOT_CK(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
+    ld = make_launch_dims(device, fp64);
+    if (!timing) return capture(&graph, nullptr);
+    for (int p = 0; p < 2; ++p) {
+        for (int q = 0; q < 2; ++q)
+            if (!tev[p][q]) HOT_CK(cudaEventCreate(&tev[p][q]));
+        if (!tgraph[p]) {
+            const int rc = capture(&tgraph[p], tev[p]);
+            if (rc != HOT_OK) return rc;
+        }
+    }
+    return HOT_OK;
+}
+
+int Batch::launch_block(cudaStream_t st, long long block) const {
+    HOT_CK(cudaGraphLaunch(timing ? tgraph[block & 1] : graph, st));
     return HOT_OK;
 }
 
@@ -573,7 +611,10 @@ int run_solve(Ctx* ctx, const std::vector<PairHost>& pairs, double tol, long lon
         insts.push_back(I);
     }
     int rc = B.set_instances(insts, st);
-    if (rc == HOT_OK) rc = B.ensure_graph();      // also fixes the launch dimensions
+    // live sweep timing: single-instance graph solves only (the bytes of a
+    // timed launch are then those of the one instance)
+    const int timing = ctx->sweep_timing && insts.size() == 1 && !kt ? 1 : 0;
+    if (rc == HOT_OK) rc = B.ensure_graph(timing);   // also fixes the launch dimensions
     if (rc != HOT_OK) {
         cleanup();
         return rc;
@@ -597,7 +638,7 @@ int run_solve(Ctx* ctx, const std::vector<PairHost>& pairs, double tol, long lon
     cudaEventRecord(t0, st);
     for (;;) {
         if (!kt) {
-            if (B.launch_block(st) != HOT_OK) {
+            if (B.launch_block(st, nb) != HOT_OK) {
                 err = HOT_ECUDA;
                 break;
             }
@@ -605,6 +646,19 @@ int run_solve(Ctx* ctx, const std::vector<PairHost>& pairs, double tol, long lon
             cudaEventRecord(ev[nb & 1], st);
             if (nb >= 1) {
                 cudaEventSynchronize(ev[(nb - 1) & 1]);
+                if (timing) {
+                    // block nb - 1 has finished; block nb runs on the other graph instance
+                    float tms = 0.f;
+                    const int p = (int)((nb - 1) & 1);
+                    if (cudaEventElapsedTime(&tms, B.tev[p][0], B.tev[p][1]) == cudaSuccess) {
+                        const Inst* I0 = insts[0];
+                        ctx->st_ms += tms;
+                        ctx->st_launches += 1;
+                        ctx->st_bytes += (double)I0->m * I0->n * (I0->m + I0->n) * (fp64 ? 24.0 : 12.0);
+                    } else {
+                        cudaGetLastError();
+                    }
+                }
                 if (B.h_running[1 + ((nb - 1) & 1)] <= 0) {
                     ++nb;
                     break;

@@ -70,6 +70,8 @@ int inst_create(const PairHost& p, int fp64, const hot_config& cfg, double tol, 
 void inst_destroy(Inst* I, cudaStream_t st);
 
 // Device work tables plus the instantiated block graph that reads them.
+// Prefix tables (cap + 1 ints each): tiles, slabs, k_vec items, k_kkt1 chunks, k_alpha32 chunks.
+constexpr int kPreTables = 5;
 struct Batch {
     int device = 0;
     int cap = 0;
@@ -87,14 +89,23 @@ struct Batch {
     int* h_pre = nullptr;           // pinned
     int* h_running = nullptr;       // pinned, [4]
     cudaGraphExec_t graph = nullptr;
+    // sweep-timing mode: two instances of the block graph, launched
+    // alternately, each with a CUDA event pair around the sweep of iteration
+    // timed_iter; the host reads one block's pair while the next block runs
+    // on the other instance
+    cudaGraphExec_t tgraph[2] = {nullptr, nullptr};
+    cudaEvent_t tev[2][2] = {};
+    int timing = 0;
     cudaStream_t cap_stream = nullptr;
     LaunchDims ld{};
     int ninst = 0;
     ~Batch();
     int reserve(int n);
     int set_instances(const std::vector<Inst*>& v, cudaStream_t st);   // async H2D
-    int ensure_graph();
-    int launch_block(cudaStream_t st) const;
+    int ensure_graph(int timing = 0);
+    int launch_block(cudaStream_t st, long long block = 0) const;
+    int timed_iter() const { return (K - 1) / 2; }   // a non-check iteration when K >= 2
+    int capture(cudaGraphExec_t* out, cudaEvent_t* ev);
 };
 
 struct Solution {
@@ -117,6 +128,10 @@ struct Ctx {
     std::mutex tune_mu;                    // guards tuned (the serve thread reads it)
     std::map<int, std::pair<int, double>> tuned[2];   // [fp64][S] -> (TR, us per iteration)
     std::string tune_cache;                // hot_config.autotune_cache, copied
+    // live timing of the non-check sweep inside the block graph (hot_sweep_timing)
+    int sweep_timing = 0;
+    double st_ms = 0.0, st_bytes = 0.0;
+    long long st_launches = 0;
     Ctx();
     ~Ctx();
 };

@@ -36,6 +36,8 @@ constexpr int kThreads = 256;          // block size of the tile kernels
 constexpr int kNK = 5;                 // per-tile check partials: r^2, min^2, x^2, z^2, c.x
 constexpr int kRowSmemBytes = 16384;   // row-partial buffer of a sweep tile
 constexpr int kMaxS = 1024;
+constexpr int kAPT = 4;                // k_alpha32: pieces per thread and chunk
+constexpr int kAlphaChunk = kThreads * kAPT;
 constexpr int kMaxTR = 128;            // FP32 tiles: TR * max(m, n) <= kRowSmemBytes / 4
 
 enum : int {
@@ -96,6 +98,7 @@ struct HotInst {
     int TR;                // rows per sweep tile
     int nb1, nb2;          // bands (tiles) per f1 slab = ceil(m / TR), per f2 slab = ceil(n / TR)
     int n_k1;              // chunks of the A x - b kernel
+    int n_achunk;          // chunks of k_alpha32 (kAlphaChunk pieces each; FP32 mode)
     int fp64;              // 1: FP64 state, 0: FP32 anchor + delta
     int gadmm;             // 1: Step 4 of the generalized ADMM instead of Halpern's
     int stop_abs;          // 1: stop on the absolute KKT residual
@@ -134,9 +137,9 @@ struct HotInst {
     double* colmu1;        // [n] sum_i mu1(i, j)
     double* rowmu2;        // [m] sum_l mu2(k, l)
     double* k1_part;       // [n_k1] partial ||A x - b||^2
-    double* dobj_part;     // [m + n] partial <b, y> per slab
+    double* dobj_part;     // partial <b, y>: [m + n] per slab (FP64 mode), [n_achunk] per chunk (FP32 mode)
     double* cu_part;       // [tiles] <c, u> per tile (FP32 mode, set per cycle)
-    double* cD_part;       // [m + n] <c, A^T(y-bar - y0)> per slab (FP32 mode, check iterations)
+    double* cD_part;       // [n_achunk] <c, A^T(y-bar - y0)> per k_alpha32 chunk (FP32 mode, check iterations)
     // FP32 bulk mode only (null in FP64 mode): the per-iteration Prop. 3
     // arithmetic runs on double-float pairs (hi, lo) of FP32 values, whose
     // sum carries about 48 significant bits, instead of FP64
@@ -206,6 +209,7 @@ struct WorkDev {
     int* pre_slab;         // k_alpha: m + n slabs per instance
     int* pre_vec;          // k_vec: 2(m + n) per instance (one warp each); k_vec32: vec32_items(m, n) CTA items
     int* pre_k1;           // k_kkt1: n_k1 per instance
+    int* pre_achunk;       // k_alpha32: n_achunk per instance
     int* n_running;        // instances still running
     int* st_out;           // [ninst] status of each instance after its last check
 };
@@ -218,6 +222,7 @@ struct LaunchDims {
     int grid_tile_chk;     // sweep of check iterations
     int grid_rst;          // restart passes
     int grid_slab;
+    int grid_alpha;        // k_alpha32 (FP32 mode)
     int grid_vec;
     int grid_k1;
     int grid_inst;

@@ -6,8 +6,8 @@
 //                the marginals that Prop. 3 needs);
 //   k_alpha32 -- Prop. 3: the right-hand side R of eq. (update:y) from the
 //                slab sums, its closed-form solution y-bar, and the per-slab
-//                broadcast vectors alpha/beta of A^T y-bar; slabs in
-//                contiguous runs per CTA;
+//                broadcast vectors alpha/beta of A^T y-bar; elementwise over
+//                the pieces, in chunks;
 //   k_sweep   -- Steps 2-4 fused into one streaming pass over the flow state:
 //                x-bar, z-bar = Pi_+(...), the Halpern update, and the slab
 //                row/column sums of the new state (the A v products of the
@@ -604,31 +604,50 @@ __global__ void __launch_bounds__(kThreads) k_vec32(const WorkDev* __restrict__ 
     }
 }
 
-// Inputs of this thread's first entries of a slab (row entry e = tid and
-// column entry e = tid), loaded together with the instance-wide vectors so
-// that a slab costs one round trip of loads.
-struct AlphaIn {
-    float2 ra, rb;        // row sums of u + d: f2 slab k row j, f1 slab j row k
-    float2 a0r, a0c;      // anchor pieces of the row and the column entry
-    float2 k2, mu;        // column anchor constant and (check) the marginal
-    float kd;             // column total of the delta over the bands
+// Pieces of A^T(y-bar - y0) in FP32 mode: per slab its row pieces (alpha),
+// then its column pieces (beta), slab after slab as in ab32, 4mn per instance.
+// The inputs of one piece, loaded in one round before any is computed:
+//   row piece e of f1 slab j (k = e) or f2 slab k (j = e): the row sums of
+//     u + d of f2 slab k row j (x) and of f1 slab j row k (y);
+//   column piece e: the sigma-scaled anchor constant K2 (x), the column total
+//     of the delta over the slab's bands (y.x) and on check iterations the
+//     marginal entry (mu).
+struct PieceIn {
+    float2 a0;            // anchor piece (hi, lo)
+    float2 x, y, mu;
 };
-__device__ __forceinline__ AlphaIn alpha_in(const HotInst& I, int slab, int e, bool check) {
-    const int m = I.m, n = I.n, Ls = g_side(I, slab), nb = g_nb(I, slab);
-    AlphaIn a;
+__device__ __forceinline__ void piece_slab(const HotInst& I, int q, int& slab, int& idx) {
+    const int m = I.m, n = I.n;
+    const int h1 = 2 * m * n;                     // pieces of the f1 half: n slabs of 2m
+    if (q < h1) {
+        slab = q / (2 * m);
+        idx = q - slab * 2 * m;
+    } else {
+        const int r = q - h1, t = r / (2 * n);
+        slab = n + t;
+        idx = r - t * 2 * n;
+    }
+}
+__device__ __forceinline__ PieceIn piece_in(const HotInst& I, int slab, int idx, bool check) {
+    const int m = I.m, n = I.n;
     const bool f1 = slab < n;
-    const int j = f1 ? slab : e, k = f1 ? e : slab - n;
-    a.ra = I.rs2[(size_t)n * m + (size_t)k * n + j];
-    a.rb = I.rs2[(size_t)j * m + k];
-    const size_t o = 2 * g_row(I, slab);
-    a.a0r = I.ab0_32[o + e];
-    a.a0c = I.ab0_32[o + Ls + e];
-    a.k2 = I.K2[g_row(I, slab) + e];
-    a.mu = check ? (f1 ? I.mu1f[(size_t)e * n + slab] : I.mu2f[(size_t)(slab - n) * n + e]) : make_float2(0.f, 0.f);
-    float kd = 0.f;
-    for (int b = 0; b < nb; ++b) kd += I.cs32[g_colp(I, slab, b) + e];
-    a.kd = kd;
-    return a;
+    const int Ls = f1 ? m : n;
+    PieceIn p;
+    p.a0 = I.ab0_32[2 * g_row(I, slab) + idx];
+    p.mu = make_float2(0.f, 0.f);
+    if (idx < Ls) {
+        const int j = f1 ? slab : idx, k = f1 ? idx : slab - n;
+        p.x = I.rs2[(size_t)n * m + (size_t)k * n + j];
+        p.y = I.rs2[(size_t)j * m + k];
+    } else {
+        const int e = idx - Ls, nb = f1 ? I.nb1 : I.nb2;
+        p.x = I.K2[g_row(I, slab) + e];
+        float kd = 0.f;
+        for (int b = 0; b < nb; ++b) kd += I.cs32[g_colp(I, slab, b) + e];
+        p.y = make_float2(kd, 0.f);
+        if (check) p.mu = f1 ? I.mu1f[(size_t)e * n + slab] : I.mu2f[(size_t)(slab - n) * n + e];
+    }
+    return p;
 }
 
 // The instance-wide O(m + n) stage: from T1, T2, P1, P2 (k_vec32) the vectors
@@ -737,97 +756,111 @@ __device__ void alpha32_stage(const HotInst& I, const StageIn& pre, float2 (*sq)
     __syncthreads();
 }
 
-// k_alpha32: per slab, the entries of y-bar - y0 (pairs, kept for the
-// restart), their FP32 split for the sweep, and on check iterations <b, y>
-// and max |A^T y| pieces.  Slabs are taken in contiguous runs per CTA so that
-// the instance-wide stage is formed once per instance and CTA.
+// k_alpha32: the pieces of y-bar - y0 (pairs, kept for the restart), their
+// FP32 split for the sweep, and on check iterations the partial sums of
+// <b, y>, of <c, A^T(y-bar - y0)> and max |A^T y|.  An instance's 4mn pieces
+// are cut into chunks of kAlphaChunk (kAPT per thread, consecutive threads on
+// consecutive pieces); a CTA takes chunks in a grid-stride loop, loads the
+// inputs of all its pieces of the chunk, then forms the instance-wide stage
+// (once per instance it meets) while those loads are in flight, so a chunk
+// costs about one L2 round trip.  Per-chunk partial sums sit at the chunk's
+// index (dobj_part, cD_part; k_check adds them in order).
 template <bool CHECK>
-__global__ void __launch_bounds__(kThreads, 3) k_alpha32(const WorkDev* __restrict__ W, int j) {
+__global__ void __launch_bounds__(kThreads, 2) k_alpha32(const WorkDev* __restrict__ W, int j) {
     __shared__ float2 sq[4][kMaxS];
     __shared__ float2 s_red[4 * 32];
     __shared__ float s_max[32];
     const int ninst = W->ninst;
-    const int nslab = W->pre_slab[ninst];
-    const int chunk = (nslab + gridDim.x - 1) / gridDim.x;
-    const int t0 = blockIdx.x * chunk, t1 = min(nslab, t0 + chunk);
+    const int nchunk = W->pre_achunk[ninst];
     const int tid = threadIdx.x;
     int cached = -1;
-    for (int t = t0; t < t1; ++t) {
-        // every thread resolves the slab itself (uniform, no barrier)
-        const int inst = find_inst(W->pre_slab, ninst, t);
+    for (int c = blockIdx.x; c < nchunk; c += gridDim.x) {
+        // every thread resolves the chunk itself (uniform, no barrier)
+        const int inst = find_inst(W->pre_achunk, ninst, c);
         const HotInst& I = W->inst[inst];
         if (I.ctl->status != ST_RUNNING) continue;
-        const int slab = t - W->pre_slab[inst];
-        const int m = I.m, n = I.n, Ls = g_side(I, slab);
-        // one round of loads: this thread's first entries, the cycle
-        // constants and (for a new instance) the stage inputs
-        AlphaIn pin{};
-        if (tid < Ls) pin = alpha_in(I, slab, tid, CHECK);
-        const CycleK& C = *I.cyc;
+        const int m = I.m, n = I.n;
+        const int cl = c - W->pre_achunk[inst];
+        const int npieces = 4 * m * n;
+        int ps[kAPT], pi[kAPT];
+        PieceIn pin[kAPT];
+#pragma unroll
+        for (int u = 0; u < kAPT; ++u) {
+            const int q = cl * kAlphaChunk + u * kThreads + tid;
+            ps[u] = -1;
+            if (q < npieces) {
+                piece_slab(I, q, ps[u], pi[u]);
+                pin[u] = piece_in(I, ps[u], pi[u], CHECK);
+            }
+        }
         if (inst != cached) {
             const StageIn sin = stage_in(I, tid);
             alpha32_stage(I, sin, sq, s_red);
             cached = inst;
         }
-        if (slab == 0 && tid == 0) *I.p32 = make_p32(I.ctl->sigma, I.ctl->k + j, I.h, I.gadmm, I.relax);
+        if (cl == 0 && tid == 0) *I.p32 = make_p32(I.ctl->sigma, I.ctl->k + j, I.h, I.gadmm, I.relax);
+        const CycleK& C = *I.cyc;
         const DF is = df_ld(C.is), imn = df_ld(C.imn);
-        const size_t o = 2 * g_row(I, slab);
         const float igrid = (float)I.h, grid = 1.0f / igrid;       // powers of two: exact
         float ymax = 0.f;
         DF dob{0.f, 0.f};
-        // <c, A^T(y-bar - y0)> of the slab: the cost is separable, so it is
+        // <c, A^T(y-bar - y0)>: the cost is separable, so a slab contributes
         // sum_r dalpha_r C(r) + sum_c dbeta_c C(c), C(x) = sum_y (X_x - X_y)^2
         DF cdd{0.f, 0.f};
-        const float2* csum = I.csum2 + g_xbase(I, slab);
-        // idx < Ls: alpha (row) entries, idx >= Ls: beta (column) entries; returns the full piece on check iterations
-        auto put = [&](int idx, DF dv, float2 a0) -> DF {
-            I.dab2[o + idx] = df_st(dv);
+#pragma unroll
+        for (int u = 0; u < kAPT; ++u) {
+            if (ps[u] < 0) continue;
+            const int slab = ps[u], idx = pi[u];
+            const bool f1 = slab < n;
+            const int Ls = f1 ? m : n;
+            const PieceIn& a = pin[u];
+            DF dv;
+            bool col = idx >= Ls, zero = false;
+            if (!col) {
+                // y1(k, j) on f1 slab j row k, -y1(k, j) on f2 slab k row j, with
+                // R1(k, j) = -(rowsum f1 slab j - rowsum f2 slab k)/sigma
+                const DF R1 = df_mul(df_sub(df_ld(a.x), df_ld(a.y)), is);
+                const DF fixed_row = f1 ? df_ld(sq[0][slab]) : df_ld(sq[1][slab - n]);
+                const DF other = f1 ? df_ld(sq[1][idx]) : df_ld(sq[0][idx]);
+                const DF y1 = df_mul(df_add(df_add(R1, fixed_row), other), imn);
+                dv = f1 ? y1 : df_neg(y1);
+            } else {
+                // y2(i, j) on f1 slab j, y3(k, l) on f2 slab k (y3(m, n) = 0)
+                const int e = idx - Ls;
+                zero = !f1 && slab == n + m - 1 && e == n - 1;
+                if (zero) {
+                    dv = DF{0.f, 0.f};
+                } else {
+                    const DF colc = f1 ? df_mul(df_ld(sq[2][slab]), df_neg(df_ld(C.im)))
+                                       : df_mul(df_ld(sq[3][slab - n]), df_ld(C.in));
+                    const DF isc = f1 ? df_ld(C.isim) : df_ld(C.isin);
+                    dv = df_add(df_sub(df_ld(a.x), df_mul(isc, a.y.x)), colc);
+                }
+            }
+            const size_t o = 2 * g_row(I, slab) + idx;
+            I.dab2[o] = df_st(dv);
             const float df = df_f(dv);
             const float dh = rintf(df * grid) * igrid;          // on the grid 2^-E
-            I.ab32[o + idx] = make_float4(a0.x + dh, a0.y + (df - dh), df, 0.f);
-            DF full{0.f, 0.f};
+            I.ab32[o] = make_float4(a.a0.x + dh, a.a0.y + (df - dh), df, 0.f);
             if (CHECK) {
-                full = df_add(DF{a0.x, a0.y}, dv);
+                const DF full = df_add(DF{a.a0.x, a.a0.y}, dv);
                 ymax = fmaxf(ymax, fabsf(full.hi));
-                cdd = df_add(cdd, df_mul(dv, df_ld(csum[idx < Ls ? idx : idx - Ls])));
+                const float2* csum = I.csum2 + g_xbase(I, slab);
+                cdd = df_add(cdd, df_mul(dv, df_ld(csum[col ? idx - Ls : idx])));
+                if (col && !zero) dob = df_add(dob, df_mul(df_ld(a.mu), full));
             }
-            return full;
-        };
-        const bool f1 = slab < n;
-        // row entries: f1 slab j gives y1(k, j) for every k, f2 slab k gives -y1(k, j) for every j
-        const DF fixed_row = f1 ? df_ld(sq[0][slab]) : df_ld(sq[1][slab - n]);
-        for (int e = tid; e < Ls; e += kThreads) {
-            const AlphaIn a = e == tid ? pin : alpha_in(I, slab, e, CHECK);
-            // R1(k, j) = -(rowsum f1 slab j - rowsum f2 slab k)/sigma
-            const DF R1 = df_mul(df_sub(df_ld(a.ra), df_ld(a.rb)), is);
-            const DF other = f1 ? df_ld(sq[1][e]) : df_ld(sq[0][e]);
-            const DF y1 = df_mul(df_add(df_add(R1, fixed_row), other), imn);
-            put(e, f1 ? y1 : df_neg(y1), a.a0r);
-        }
-        // column entries: y2(i, j) on f1 slab j, y3(k, l) on f2 slab k (y3(m, n) = 0)
-        const DF colc = f1 ? df_mul(df_ld(sq[2][slab]), df_neg(df_ld(C.im))) : df_mul(df_ld(sq[3][slab - n]), df_ld(C.in));
-        const DF isc = f1 ? df_ld(C.isim) : df_ld(C.isin);
-        for (int e = tid; e < Ls; e += kThreads) {
-            const AlphaIn a = e == tid ? pin : alpha_in(I, slab, e, CHECK);
-            if (!f1 && slab == n + m - 1 && e == n - 1) {
-                put(Ls + e, DF{0.f, 0.f}, a.a0c);
-                continue;
-            }
-            const DF dv = df_add(df_sub(df_ld(a.k2), df_mul(isc, a.kd)), colc);
-            const DF full = put(Ls + e, dv, a.a0c);
-            if (CHECK) dob = df_add(dob, df_mul(df_ld(a.mu), full));
         }
         if (CHECK) {
             DF red[2] = {dob, cdd};
             block_sum_df<2>(red, s_red);
             const float bm = block_max(ymax, s_max);
             if (tid == 0) {
-                I.dobj_part[slab] = df_val(red[0]);
-                I.cD_part[slab] = df_val(red[1]);
+                I.dobj_part[cl] = df_val(red[0]);
+                I.cD_part[cl] = df_val(red[1]);
                 atomicMax(&I.ctl->ymax_bits, __float_as_uint(bm));
             }
         }
-        __syncthreads();           // sq may be rewritten for the next slab's instance
+        __syncthreads();           // sq may be rewritten for the next chunk's instance
     }
 }
 
@@ -1657,7 +1690,10 @@ __global__ void __launch_bounds__(kThreads) k_check(const WorkDev* __restrict__ 
             if (!I.fp64) v[7] += I.cu_part[q];
         }
         for (int q = threadIdx.x; q < I.n_k1; q += blockDim.x) v[5] += I.k1_part[q];
-        for (int q = threadIdx.x; q < nslab; q += blockDim.x) {
+        // partial sums of <b, y> (and FP32 mode: <c, A^T(y-bar - y0)>): one per
+        // slab in FP64 mode, one per k_alpha32 chunk in FP32 mode
+        const int npart = I.fp64 ? nslab : I.n_achunk;
+        for (int q = threadIdx.x; q < npart; q += blockDim.x) {
             v[6] += I.dobj_part[q];
             if (!I.fp64) v[4] += C->sigma * I.cD_part[q];
         }
@@ -1779,12 +1815,14 @@ LaunchDims make_launch_dims(int device, int fp64) {
         d.grid_tile_chk = d.grid_tile;
         d.grid_rst = std::min(occ_grid(k_restart<double, 0>, sms, 0, 8), occ_grid(k_restart<double, 1>, sms, 0, 8));
         d.grid_slab = occ_grid(k_alpha<true>, sms, 0, 4);
+        d.grid_alpha = d.grid_slab;
         d.grid_vec = occ_grid(k_vec, sms, 0, 4);
     } else {
         d.grid_tile = occ_grid(k_sweep32<false>, sms, kSweepSmem, 8);
         d.grid_tile_chk = occ_grid(k_sweep32<true>, sms, kSweepSmemChk, 8);
         d.grid_rst = std::min(occ_grid(k_restart<float, 0>, sms, 0, 8), occ_grid(k_restart<float, 1>, sms, 0, 8));
-        d.grid_slab = occ_grid(k_alpha32<true>, sms, 0, 4);
+        d.grid_slab = occ_grid(k_anchor, sms, 0, 4);
+        d.grid_alpha = occ_grid(k_alpha32<true>, sms, 0, 2);
         d.grid_vec = occ_grid(k_vec32, sms, 0, 4);
     }
     d.grid_k1 = sms * 2;
@@ -1840,7 +1878,7 @@ void launch_solve_kernels(const WorkDev* w, const LaunchDims& ld, int fp64, int 
         launch(ld, check ? k_alpha<true> : k_alpha<false>, ld.grid_slab, 0, st, w);
     } else {
         launch(ld, k_vec32, ld.grid_vec, 0, st, w);
-        launch(ld, check ? k_alpha32<true> : k_alpha32<false>, ld.grid_slab, 0, st, w, j);
+        launch(ld, check ? k_alpha32<true> : k_alpha32<false>, ld.grid_alpha, 0, st, w, j);
     }
 }
 

@@ -89,8 +89,11 @@ static void finish_req(Ctx* ctx, ServeState* s, Req* r, int status) {
         s->in_use -= std::min(s->in_use, r->bytes);
         r->inst = nullptr;
     }
-    if (status == HOT_ECANCELLED) ++s->cancelled;
-    else ++s->completed;
+    if (status == HOT_ECANCELLED) {
+        ++s->cancelled;                 // latency statistics cover served requests only
+        return;
+    }
+    ++s->completed;
     s->lat_ms.push_back(std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count());
     s->queue_ms.push_back(r->res.queue_ms);
 }
@@ -329,7 +332,19 @@ int serve_cancel(Ctx* ctx, unsigned long long ticket) {
         set_error("unknown or finished ticket");
         return HOT_ENOTFOUND;
     }
-    it->second->cancel = true;
+    Req* r = it->second.get();
+    r->cancel = true;
+    if (r->state == 0) {
+        // still queued: leave the queue now (an admitted request stops at its next check)
+        for (auto q = s->queue.begin(); q != s->queue.end(); ++q)
+            if (*q == r) {
+                s->queue.erase(q);
+                r->t_admit = Clock::now();
+                finish_req(ctx, s, r, HOT_ECANCELLED);
+                s->cv_done.notify_all();
+                break;
+            }
+    }
     s->cv_work.notify_all();
     return HOT_OK;
 }

@@ -126,6 +126,7 @@ def load_library(path=None):
         "hot_solve_batch": (i, [vp, i, P(vp), P(vp), P(i), P(i), i, d, ll, P(hot_result)]),
         "hot_solve_coords": (i, [vp, vp, vp, i, i, i, vp, vp, d, ll, P(hot_result)]),
         "hot_solve_profiled": (i, [vp, vp, vp, i, i, i, d, ll, P(hot_result), P(hot_kernel_times)]),
+        "hot_sweep_timing": (i, [vp, i, P(d), P(ll), P(d)]),
         "hot_get_flows": (i, [vp, ull, vp, i]),
         "hot_recover_plan": (i, [vp, ull, vp, vp, vp, i, sz, P(sz), P(d)]),
         "hot_release": (i, [vp, ull]),
@@ -282,6 +283,19 @@ def hot_solve_profiled(ctx, mu, nu, tol=1e-6, max_iter=100000):
     if rc not in (HOT_OK, HOT_NOT_CONVERGED):
         raise _err(lib, ctx, rc)
     return res.to_dict(), kt.to_dict()
+
+
+def hot_sweep_timing(ctx, enable):
+    """Switch the live in-graph sweep timing on (1), off (0) or leave it (-1);
+    returns the counters since the last call: {"ms", "launches", "bytes"}."""
+    lib = load_library()
+    ms = ctypes.c_double()
+    n = ctypes.c_longlong()
+    b = ctypes.c_double()
+    rc = lib.hot_sweep_timing(ctx, int(enable), ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b))
+    if rc != HOT_OK:
+        raise _err(lib, ctx, rc)
+    return {"ms": ms.value, "launches": n.value, "bytes": b.value}
 
 
 def hot_solve_batch(ctx, mus, nus, tol=1e-6, max_iter=100000):
@@ -483,6 +497,9 @@ class Context:
 
     def solve_batch(self, mus, nus, tol=1e-6, max_iter=100000):
         return hot_solve_batch(self.ctx, mus, nus, tol, max_iter)
+
+    def sweep_timing(self, enable=-1):
+        return hot_sweep_timing(self.ctx, enable)
 
     def flows(self, res, out=None):
         return hot_get_flows(self.ctx, res["solution_id"], res["m"], res["n"], out)

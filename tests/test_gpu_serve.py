@@ -71,6 +71,8 @@ def test_cancel_queued_and_running(lib):
         t1 = srv.submit(a, b, tol=0.0, max_iter=10 ** 9)    # never converges
         t2 = srv.submit(a, b, tol=1e-6)                      # waits for the only slot
         assert srv.cancel(t2) == lib.HOT_OK
+        st2, _ = srv.poll(t2)                                # a queued request leaves at once
+        assert st2 == lib.HOT_ECANCELLED
         time.sleep(0.05)
         assert srv.cancel(t1) == lib.HOT_OK
         st1, r1 = srv.wait(t1, timeout_ms=60000)

@@ -291,3 +291,29 @@ def test_batch_equals_single_solves(lib, ctx32):
         ctx32.release(rs)
         assert rb["status"] == 0
         assert rb["ot_value"] == rs["ot_value"] and rb["iters"] == rs["iters"]
+
+
+# ------------------------------------------------------- live sweep timing --
+
+def test_live_sweep_timing_leaves_the_solve_unchanged(lib):
+    """The event pair in the block graph times one non-check sweep per block
+    and changes nothing else: same iterates, same value."""
+    S = 64
+    mu1, mu2 = syn.make_pair("white", S, 3)
+    with lib.Context(precision="fp32") as ctx:
+        a = ctx.solve(mu1, mu2, tol=1e-6)
+        ctx.release(a)
+        ctx.sweep_timing(1)
+        b = ctx.solve(mu1, mu2, tol=1e-6)
+        ctx.release(b)
+        t = ctx.sweep_timing(0)
+        c = ctx.solve(mu1, mu2, tol=1e-6)
+        ctx.release(c)
+        t2 = ctx.sweep_timing(-1)
+    assert a["ot_value"] == b["ot_value"] == c["ot_value"]
+    assert a["iters"] == b["iters"] == c["iters"]
+    blocks = b["iters"] // 10
+    assert t["launches"] == blocks
+    assert t["bytes"] == blocks * 12.0 * 2 * S ** 3
+    assert 0.0 < t["ms"] / t["launches"] < 5.0
+    assert t2["launches"] == 0 and t2["ms"] == 0.0
