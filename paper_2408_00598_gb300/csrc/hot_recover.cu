@@ -206,28 +206,41 @@ __device__ __forceinline__ void load_node_df(const float* __restrict__ x, int m,
     __syncwarp();
 }
 
-__device__ __forceinline__ int node_source_df(int n, int i, const float2* A, const float2* B, const float* b,
-                                              int32_t* src, int32_t* dst, double* mass, size_t pos, int src_id,
-                                              int node_k) {
-    const DF lo = df_ld(A[i]);
-    const DF hi = df_min(df_ld(A[i + 1]), df_ld(B[n]));
-    if (!df_lt(lo, hi)) return 0;
-    int l0 = 0, l1 = n - 1;                               // first l with B[l+1] > lo
-    while (l0 < l1) {
-        const int mid = (l0 + l1) >> 1;
-        if (df_lt(lo, df_ld(B[mid + 1]))) l1 = mid; else l0 = mid + 1;
+// The node's coupling as a merge of the source ends A[1..m] with the sink
+// ends B[1..n] (ties: source first).  After the first d merged ends the walk
+// stands at source p, sink q = d - p; the step from there moves the overlap
+// min(A[p+1], B[q+1]) - max(A[p], B[q]) from source p to sink q (an entry
+// when positive) and passes the nearer end.  These are exactly the pairs and
+// masses of the north-west-corner loops, in (i, l) order.  A lane takes a
+// contiguous range of steps and finds its start by a binary search on the
+// merge diagonal (merge path), so a node costs about log2(m + n) +
+// (m + n)/32 steps per lane.
+__device__ __forceinline__ int merge_split(const float2* A, const float2* B, int m, int n, int d) {
+    int lo = d - n > 0 ? d - n : 0, hi = d < m ? d : m;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        // source end mid + 1 is among the first d ends iff it is <= sink end d - mid
+        if (!df_lt(df_ld(B[d - mid]), df_ld(A[mid + 1]))) lo = mid + 1;
+        else hi = mid;
     }
+    return lo;
+}
+__device__ __forceinline__ int merge_walk(const float2* A, const float2* B, int m, int n, int p, int q, int steps,
+                                          int32_t* src, int32_t* dst, double* mass, size_t pos, int j, int k) {
     int cnt = 0;
-    for (int l = l0; l < n && df_lt(df_ld(B[l]), hi); ++l) {
-        const DF p = df_sub(df_min(hi, df_ld(B[l + 1])), df_max(lo, df_ld(B[l])));
-        if (df_pos(p) && b[l] > 0.f) {
+    for (int t = 0; t < steps && p < m && q < n; ++t) {
+        const DF ae = df_ld(A[p + 1]), be = df_ld(B[q + 1]);
+        const DF ov = df_sub(df_min(ae, be), df_max(df_ld(A[p]), df_ld(B[q])));
+        if (df_pos(ov)) {
             if (src) {
-                src[pos + cnt] = src_id;
-                dst[pos + cnt] = node_k * n + l;
-                mass[pos + cnt] = df_val(p);
+                src[pos + cnt] = p * n + j;
+                dst[pos + cnt] = k * n + q;
+                mass[pos + cnt] = df_val(ov);
             }
             ++cnt;
         }
+        if (!df_lt(be, ae)) ++p;
+        else ++q;
     }
     return cnt;
 }
@@ -248,12 +261,15 @@ __global__ void __launch_bounds__(kRecWarps * 32) k_recover_df(const float* __re
     float2* A = reinterpret_cast<float2*>(b + n + ((m + n) & 1));
     float2* B = A + m + 1;
     const int nodes = m * n;
+    const int span = (m + n + 31) / 32;                  // merge steps per lane
+    const int d0 = lane * span < m + n ? lane * span : m + n;
+    const int d1 = d0 + span < m + n ? d0 + span : m + n;
     for (int node = blockIdx.x * nw + warp; node < nodes; node += gridDim.x * nw) {
         const int k = node / n, j = node % n;    // k-major node order
         load_node_df(x, m, n, k, j, a, b, A, B);
+        const int p0 = d0 < d1 ? merge_split(A, B, m, n, d0) : m;
+        int c = merge_walk(A, B, m, n, p0, d0 - p0, d1 - d0, nullptr, nullptr, nullptr, 0, j, k);
         if (count_only) {
-            int c = 0;
-            for (int i = lane; i < m; i += 32) c += node_source_df(n, i, A, B, b, nullptr, nullptr, nullptr, 0, 0, k);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
             if (lane == 0) counts[node] = c;
@@ -271,21 +287,14 @@ __global__ void __launch_bounds__(kRecWarps * 32) k_recover_df(const float* __re
                 if (df_pos(gb)) atomicAdd(&marg2[(size_t)k * n + t], df_val(gb));
             }
         } else {
-            long long pos = offs[node];
-            for (int base = 0; base < m; base += 32) {
-                const int i = base + lane;
-                int c = 0;
-                if (i < m) c = node_source_df(n, i, A, B, b, nullptr, nullptr, nullptr, 0, 0, k);
-                int incl = c;
+            int incl = c;
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int y = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= o) incl += y;
-                }
-                if (i < m && c > 0)
-                    node_source_df(n, i, A, B, b, src, dst, mass, (size_t)(pos + incl - c), i * n + j, k);
-                pos += __shfl_sync(0xffffffffu, incl, 31);
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
             }
+            if (c > 0)
+                merge_walk(A, B, m, n, p0, d0 - p0, d1 - d0, src, dst, mass, (size_t)(offs[node] + incl - c), j, k);
         }
         __syncwarp();
     }
