@@ -114,7 +114,7 @@ struct HotInst {
     void* d1;              // delta, pong             [V]
     void* xr;              // x-bar at the last restart (final x-bar after the solve)
     void* zr;              // z-bar at the last restart
-    float4* ab32;          // [4mn] pieces (hi, lo, delta, 0) of alpha then beta, FP32 mode
+    float4* ab32;          // [4mn] pieces (hi, lo, delta, x) of alpha then beta, x the row/column coordinate, FP32 mode
     float2* ab0_32;        // [4mn] (hi, lo) split of ab0, FP32 mode (fixed within a cycle)
     double* ab64;          // [4mn] alpha then beta = A^T y-bar pieces (FP64 mode)
     double* ab0;           // [4mn] the same pieces of A^T y0 at the anchor
@@ -157,6 +157,8 @@ struct HotInst {
     const double* X64;     // the same in FP64
     const float2* csum2;   // [m + n] C(x) = sum_y (X_x - X_y)^2 within each axis, as pairs
     struct CycleK* cyc;    // Prop. 3 constants of the current cycle
+    float2* stage2;        // [4][max(m, n)] Prop. 3 stage of the iteration (FP32 mode): mvA, mvS, sy, sp
+    int* vec_count;        // k_vec32 items finished in the current launch (0 between launches)
     HotCtl* ctl;
 };
 
@@ -234,9 +236,10 @@ constexpr int kLaunchesBlockEnd = 8;       // k_kkt1, k_check, 3 x k_restart, k_
 // work items of k_vec32 per instance: T1 (n outputs) and T2 (m outputs) in
 // items of 8, P1 (m columns over n rows) and P2 (n columns over m rows) in items
 // of 32 columns x 64 rows (one partial per 64-row block)
-inline int vec32_items(int m, int n) {
+__host__ __device__ inline int vec32_items_dev(int m, int n) {
     return (n + 7) / 8 + (m + 7) / 8 + ((m + 31) / 32) * ((n + 63) / 64) + ((n + 31) / 32) * ((m + 63) / 64);
 }
+inline int vec32_items(int m, int n) { return vec32_items_dev(m, n); }
 // float2 entries of vec2: T1, T2, then the (n + 63)/64 partials of P1 and the
 // (m + 63)/64 partials of P2, each a row of max(m, n)
 inline size_t vec2_entries(int m, int n) {

@@ -525,11 +525,189 @@ __global__ void __launch_bounds__(kThreads) k_alpha(const WorkDev* __restrict__ 
 // its loads before it adds, so an item costs about one L2 round trip.
 constexpr int kVecRows = 64;
 
+// Pieces of A^T(y-bar - y0) in FP32 mode: per slab its row pieces (alpha),
+// then its column pieces (beta), slab after slab as in ab32, 4mn per instance.
+// The inputs of one piece, loaded in one round before any is computed:
+//   row piece e of f1 slab j (k = e) or f2 slab k (j = e): the row sums of
+//     u + d of f2 slab k row j (x) and of f1 slab j row k (y);
+//   column piece e: the sigma-scaled anchor constant K2 (x), the column total
+//     of the delta over the slab's bands (y.x) and on check iterations the
+//     marginal entry (mu).
+struct PieceIn {
+    float2 a0;            // anchor piece (hi, lo)
+    float2 x, y, mu;
+    float2 s1, s2;        // stage entries: row piece mvA/mvS of its slab and of its row; column piece sy or sp
+    float xc;             // bin coordinate of the piece's row or column
+};
+__device__ __forceinline__ void piece_slab(const HotInst& I, int q, int& slab, int& idx) {
+    const int m = I.m, n = I.n;
+    const int h1 = 2 * m * n;                     // pieces of the f1 half: n slabs of 2m
+    if (q < h1) {
+        slab = q / (2 * m);
+        idx = q - slab * 2 * m;
+    } else {
+        const int r = q - h1, t = r / (2 * n);
+        slab = n + t;
+        idx = r - t * 2 * n;
+    }
+}
+__device__ __forceinline__ PieceIn piece_in(const HotInst& I, int slab, int idx, bool check) {
+    const int m = I.m, n = I.n;
+    const bool f1 = slab < n;
+    const int Ls = f1 ? m : n;
+    PieceIn p;
+    p.a0 = I.ab0_32[2 * g_row(I, slab) + idx];
+    p.mu = make_float2(0.f, 0.f);
+    p.xc = I.X32[g_xbase(I, slab) + (idx < Ls ? idx : idx - Ls)];
+    const int L = g_L(I);
+    const float2* __restrict__ sg = I.stage2;           // rows: mvA (j), mvS (k), sy (j), sp (k)
+    p.s2 = make_float2(0.f, 0.f);
+    if (idx < Ls) {
+        const int j = f1 ? slab : idx, k = f1 ? idx : slab - n;
+        p.x = I.rs2[(size_t)n * m + (size_t)k * n + j];
+        p.y = I.rs2[(size_t)j * m + k];
+        p.s1 = f1 ? sg[j] : sg[L + k];                    // the slab's own index
+        p.s2 = f1 ? sg[L + k] : sg[j];                    // the row's index
+    } else {
+        const int e = idx - Ls, nb = f1 ? I.nb1 : I.nb2;
+        p.s1 = f1 ? sg[2 * (size_t)L + slab] : sg[3 * (size_t)L + (slab - n)];
+        p.x = I.K2[g_row(I, slab) + e];
+        float kd = 0.f;
+        for (int b = 0; b < nb; ++b) kd += I.cs32[g_colp(I, slab, b) + e];
+        p.y = make_float2(kd, 0.f);
+        if (check) p.mu = f1 ? I.mu1f[(size_t)e * n + slab] : I.mu2f[(size_t)(slab - n) * n + e];
+    }
+    return p;
+}
+
+// The instance-wide O(m + n) stage: from T1, T2, P1, P2 (k_vec32) the vectors
+//   mvA_j = a_j/n - (1/m + 1/n) bb_j      (column part of y1-hat), j < n
+//   mvS_k = r3_k/n + T3/n^2 - (m+n) y1a_k (row part of y1, times m+n), k < m
+//   sy_j  = sum_k y1(k, j)                (for y2)
+//   sp_k  = sum_j y1(k, j)                (for y3)
+// into rows 0-3 of sq (mvA at j, mvS at k, sy at j, sp at k).  With e_k = rowR1_k + r3_k and d
+// the diagonal of W-hat, every global scalar follows from four sums: sum a,
+// sum bb, T3 = sum r3 and sum d_k e_k, since s_k = (e_k + cst)/(m+n) with
+// cst = sum a/n - (1/m+1/n) sum bb + T3/n.  Each thread forms the scalars
+// from the block sums itself (no single-thread section, no extra barrier).
+struct StageIn {
+    float2 T1, P2, cm;    // j = threadIdx.x < n (P2: first row-block partial)
+    float2 T2, P1, rm;    // k = threadIdx.x < m (P1: first row-block partial)
+    float kdl;            // thread m-1: delta column total at the dropped (m, n) entry
+};
+__device__ __forceinline__ StageIn stage_in(const HotInst& I, int q) {
+    const int m = I.m, n = I.n, L = g_L(I);
+    const float2* __restrict__ v = I.vec2;
+    const int r1 = (n + kVecRows - 1) / kVecRows;      // row blocks of P1
+    StageIn s{};
+    if (q < n) {
+        s.T1 = __ldcg(v + q);
+        s.P2 = __ldcg(v + (size_t)(2 + r1) * L + q);
+        s.cm = I.cm2[q];
+    }
+    if (q < m) {
+        s.T2 = __ldcg(v + L + q);
+        s.P1 = __ldcg(v + 2 * (size_t)L + q);
+        s.rm = I.rm2[q];
+    }
+    s.kdl = 0.f;
+    if (q == m - 1) {
+        const int sl = g_nslab(I) - 1;
+        for (int b = 0; b < I.nb2; ++b) s.kdl += I.cs32[g_colp(I, sl, b) + (n - 1)];
+    }
+    return s;
+}
+
+// The cycle constants are read where they are used (L1 broadcasts) rather
+// than held in registers.
+// The results go to sq[w * L + q] (global; every entry is written and read
+// back by the same thread).  The row-block partials of P1/P2 are loaded
+// before they are added, and with L1 bypassed: they come from other CTAs of
+// the same launch (k_vec32).
+__device__ void alpha32_stage(const HotInst& I, const StageIn& pre, float2* __restrict__ sq, float2* s_red) {
+    const int m = I.m, n = I.n, L = g_L(I);
+    const CycleK& C = *I.cyc;
+    const float2* __restrict__ v = I.vec2;
+    const int r1 = (n + kVecRows - 1) / kVecRows, r2 = (m + kVecRows - 1) / kVecRows;
+    const DF is = df_ld(C.is), im = df_ld(C.im), dl = df_ld(C.dl);
+    const DF mk = df_ld(C.mk);
+    DF red[4] = {DF{0.f, 0.f}, DF{0.f, 0.f}, DF{0.f, 0.f}, DF{0.f, 0.f}};
+    const int top = m > n ? m : n;
+    for (int q = threadIdx.x; q < top; q += blockDim.x) {
+        const StageIn s = q == (int)threadIdx.x ? pre : stage_in(I, q);
+        if (q < n) {                                               // column quantities, j = q
+            float2 pp[kMaxS / kVecRows];
+#pragma unroll
+            for (int b = 1; b < kMaxS / kVecRows; ++b)
+                pp[b] = b < r2 ? __ldcg(v + (size_t)(2 + r1 + b) * L + q) : make_float2(0.f, 0.f);
+            DF P2 = df_ld(s.P2);
+#pragma unroll
+            for (int b = 1; b < kMaxS / kVecRows; ++b)
+                if (b < r2) P2 = df_add(P2, df_ld(pp[b]));
+            const DF T1 = df_ld(s.T1);
+            const DF A = df_mul(df_sub(P2, T1), is);                 // a_j = -(T1 - P2)/sigma
+            const DF B = df_mul(df_sub(df_ld(s.cm), T1), is);         // bb_j
+            sq[0 * (size_t)L + q] = df_st(A);
+            sq[2 * (size_t)L + q] = df_st(B);
+            red[0] = df_add(red[0], A);
+            red[1] = df_add(red[1], B);
+        }
+        if (q < m) {                                               // row quantities, k = q
+            float2 pp[kMaxS / kVecRows];
+#pragma unroll
+            for (int b = 1; b < kMaxS / kVecRows; ++b)
+                pp[b] = b < r1 ? __ldcg(v + (size_t)(2 + b) * L + q) : make_float2(0.f, 0.f);
+            DF P1 = df_ld(s.P1);
+#pragma unroll
+            for (int b = 1; b < kMaxS / kVecRows; ++b)
+                if (b < r1) P1 = df_add(P1, df_ld(pp[b]));
+            const DF T2 = df_ld(s.T2);
+            DF R3 = df_mul(df_sub(df_ld(s.rm), T2), is);              // r3_k
+            // the dropped (m, n) row of eq. (7): column n-1 of the last f2 slab
+            if (q == m - 1) R3 = df_sub(R3, df_mul(df_add(mk, -s.kdl), is));
+            const DF e = df_add(df_mul(df_sub(T2, P1), is), R3);      // rowR1_k + r3_k
+            sq[1 * (size_t)L + q] = df_st(R3);
+            sq[3 * (size_t)L + q] = df_st(e);
+            red[2] = df_add(red[2], R3);
+            red[3] = df_add(red[3], df_mul(e, q == m - 1 ? dl : im));
+        }
+    }
+    block_sum_df<4>(red, s_red);
+    const DF in = df_ld(C.in), imn = df_ld(C.imn), imin = df_ld(C.imin);
+    const DF T3 = red[2];
+    const DF cst = df_add(df_sub(df_mul(red[0], in), df_mul(red[1], imin)), df_mul(T3, in));
+    const DF sumd = df_ld(C.sumd);
+    const DF ds = df_mul(df_add(red[3], df_mul(cst, sumd)), imn);          // sum d_k s_k
+    const DF dsiw = df_mul(ds, df_ld(C.iw));
+    const DF tsum = df_neg(df_add(ds, df_mul(dsiw, sumd)));                // 1^T W-hat s
+    const DF tin = df_mul(tsum, in);
+    const DF yasum = df_add(tsum, df_mul(tin, (float)m));                  // 1^T y1a over k < m
+    const DF T3in = df_mul(T3, in);
+    const DF T3in2 = df_mul(T3in, in);
+    const float mpn = (float)(m + n);
+    for (int q = threadIdx.x; q < top; q += blockDim.x) {
+        if (q < n) {
+            const DF A = df_ld(sq[0 * (size_t)L + q]), B = df_ld(sq[2 * (size_t)L + q]);
+            sq[0 * (size_t)L + q] = df_st(df_sub(df_mul(A, in), df_mul(B, imin)));                    // mvA_j
+            sq[2 * (size_t)L + q] = df_st(df_sub(df_mul(df_add(df_sub(A, B), T3in), in), yasum));     // sy_j
+        }
+        if (q < m) {
+            const DF R3 = df_ld(sq[1 * (size_t)L + q]), e = df_ld(sq[3 * (size_t)L + q]);
+            const DF sk = df_mul(df_add(e, cst), imn);                                 // s_k
+            const DF ya = df_add(df_neg(df_mul(df_add(sk, dsiw), q == m - 1 ? dl : im)), tin);   // y1a_k
+            sq[1 * (size_t)L + q] = df_st(df_sub(df_add(df_mul(R3, in), T3in2), df_mul(ya, mpn)));  // mvS_k
+            sq[3 * (size_t)L + q] = df_st(df_sub(sk, df_mul(ya, (float)n)));                        // sp_k
+        }
+    }
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(kThreads) k_vec32(const WorkDev* __restrict__ W) {
     constexpr int kW = kThreads / 32;
     constexpr int kRW = kVecRows / kW;               // rows per warp in a P item
     __shared__ float2 s_p[kThreads];
-    __shared__ int s_t[3];
+    __shared__ float2 s_red[4 * 32];
+    __shared__ int s_t[4];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ninst = W->ninst;
     const int nitems = W->pre_vec[ninst];
@@ -599,181 +777,43 @@ __global__ void __launch_bounds__(kThreads) k_vec32(const WorkDev* __restrict__ 
                     I.vec2[(size_t)(2 + (which ? r1 : 0) + part) * L + q] = df_st(tot);
                 }
             }
+            // the CTA that finishes the instance's last item forms its Prop. 3
+            // stage (threadfence reduction: every writer fences before the
+            // count, the last CTA reads the sums with L1 bypassed; no CTA waits)
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                const int prev = atomicAdd(I.vec_count, 1);
+                s_t[3] = prev == vec32_items_dev(m, n) - 1;
+            }
+            __syncthreads();
+            if (s_t[3]) {
+                __threadfence();
+                const StageIn sin = stage_in(I, threadIdx.x);
+                alpha32_stage(I, sin, I.stage2, s_red);
+                if (threadIdx.x == 0) *I.vec_count = 0;      // for the next iteration
+            }
         }
         __syncthreads();
     }
 }
 
-// Pieces of A^T(y-bar - y0) in FP32 mode: per slab its row pieces (alpha),
-// then its column pieces (beta), slab after slab as in ab32, 4mn per instance.
-// The inputs of one piece, loaded in one round before any is computed:
-//   row piece e of f1 slab j (k = e) or f2 slab k (j = e): the row sums of
-//     u + d of f2 slab k row j (x) and of f1 slab j row k (y);
-//   column piece e: the sigma-scaled anchor constant K2 (x), the column total
-//     of the delta over the slab's bands (y.x) and on check iterations the
-//     marginal entry (mu).
-struct PieceIn {
-    float2 a0;            // anchor piece (hi, lo)
-    float2 x, y, mu;
-};
-__device__ __forceinline__ void piece_slab(const HotInst& I, int q, int& slab, int& idx) {
-    const int m = I.m, n = I.n;
-    const int h1 = 2 * m * n;                     // pieces of the f1 half: n slabs of 2m
-    if (q < h1) {
-        slab = q / (2 * m);
-        idx = q - slab * 2 * m;
-    } else {
-        const int r = q - h1, t = r / (2 * n);
-        slab = n + t;
-        idx = r - t * 2 * n;
-    }
-}
-__device__ __forceinline__ PieceIn piece_in(const HotInst& I, int slab, int idx, bool check) {
-    const int m = I.m, n = I.n;
-    const bool f1 = slab < n;
-    const int Ls = f1 ? m : n;
-    PieceIn p;
-    p.a0 = I.ab0_32[2 * g_row(I, slab) + idx];
-    p.mu = make_float2(0.f, 0.f);
-    if (idx < Ls) {
-        const int j = f1 ? slab : idx, k = f1 ? idx : slab - n;
-        p.x = I.rs2[(size_t)n * m + (size_t)k * n + j];
-        p.y = I.rs2[(size_t)j * m + k];
-    } else {
-        const int e = idx - Ls, nb = f1 ? I.nb1 : I.nb2;
-        p.x = I.K2[g_row(I, slab) + e];
-        float kd = 0.f;
-        for (int b = 0; b < nb; ++b) kd += I.cs32[g_colp(I, slab, b) + e];
-        p.y = make_float2(kd, 0.f);
-        if (check) p.mu = f1 ? I.mu1f[(size_t)e * n + slab] : I.mu2f[(size_t)(slab - n) * n + e];
-    }
-    return p;
-}
-
-// The instance-wide O(m + n) stage: from T1, T2, P1, P2 (k_vec32) the vectors
-//   mvA_j = a_j/n - (1/m + 1/n) bb_j      (column part of y1-hat), j < n
-//   mvS_k = r3_k/n + T3/n^2 - (m+n) y1a_k (row part of y1, times m+n), k < m
-//   sy_j  = sum_k y1(k, j)                (for y2)
-//   sp_k  = sum_j y1(k, j)                (for y3)
-// into sq[0][j], sq[1][k], sq[2][j], sq[3][k].  With e_k = rowR1_k + r3_k and d
-// the diagonal of W-hat, every global scalar follows from four sums: sum a,
-// sum bb, T3 = sum r3 and sum d_k e_k, since s_k = (e_k + cst)/(m+n) with
-// cst = sum a/n - (1/m+1/n) sum bb + T3/n.  Each thread forms the scalars
-// from the block sums itself (no single-thread section, no extra barrier).
-struct StageIn {
-    float2 T1, P2, cm;    // j = threadIdx.x < n (P2: first row-block partial)
-    float2 T2, P1, rm;    // k = threadIdx.x < m (P1: first row-block partial)
-    float kdl;            // thread m-1: delta column total at the dropped (m, n) entry
-};
-__device__ __forceinline__ StageIn stage_in(const HotInst& I, int q) {
-    const int m = I.m, n = I.n, L = g_L(I);
-    const float2* __restrict__ v = I.vec2;
-    const int r1 = (n + kVecRows - 1) / kVecRows;      // row blocks of P1
-    StageIn s{};
-    if (q < n) {
-        s.T1 = v[q];
-        s.P2 = v[(size_t)(2 + r1) * L + q];
-        s.cm = I.cm2[q];
-    }
-    if (q < m) {
-        s.T2 = v[L + q];
-        s.P1 = v[2 * (size_t)L + q];
-        s.rm = I.rm2[q];
-    }
-    s.kdl = 0.f;
-    if (q == m - 1) {
-        const int sl = g_nslab(I) - 1;
-        for (int b = 0; b < I.nb2; ++b) s.kdl += I.cs32[g_colp(I, sl, b) + (n - 1)];
-    }
-    return s;
-}
-
-// The cycle constants are read where they are used (L1 broadcasts) rather
-// than held in registers.
-__device__ void alpha32_stage(const HotInst& I, const StageIn& pre, float2 (*sq)[kMaxS], float2* s_red) {
-    const int m = I.m, n = I.n, L = g_L(I);
-    const CycleK& C = *I.cyc;
-    const float2* __restrict__ v = I.vec2;
-    const int r1 = (n + kVecRows - 1) / kVecRows, r2 = (m + kVecRows - 1) / kVecRows;
-    const DF is = df_ld(C.is), im = df_ld(C.im), dl = df_ld(C.dl);
-    const DF mk = df_ld(C.mk);
-    DF red[4] = {DF{0.f, 0.f}, DF{0.f, 0.f}, DF{0.f, 0.f}, DF{0.f, 0.f}};
-    const int top = m > n ? m : n;
-    for (int q = threadIdx.x; q < top; q += blockDim.x) {
-        const StageIn s = q == (int)threadIdx.x ? pre : stage_in(I, q);
-        if (q < n) {                                               // column quantities, j = q
-            DF P2 = df_ld(s.P2);
-            for (int b = 1; b < r2; ++b) P2 = df_add(P2, df_ld(v[(size_t)(2 + r1 + b) * L + q]));
-            const DF T1 = df_ld(s.T1);
-            const DF A = df_mul(df_sub(P2, T1), is);                 // a_j = -(T1 - P2)/sigma
-            const DF B = df_mul(df_sub(df_ld(s.cm), T1), is);         // bb_j
-            sq[0][q] = df_st(A);
-            sq[2][q] = df_st(B);
-            red[0] = df_add(red[0], A);
-            red[1] = df_add(red[1], B);
-        }
-        if (q < m) {                                               // row quantities, k = q
-            DF P1 = df_ld(s.P1);
-            for (int b = 1; b < r1; ++b) P1 = df_add(P1, df_ld(v[(size_t)(2 + b) * L + q]));
-            const DF T2 = df_ld(s.T2);
-            DF R3 = df_mul(df_sub(df_ld(s.rm), T2), is);              // r3_k
-            // the dropped (m, n) row of eq. (7): column n-1 of the last f2 slab
-            if (q == m - 1) R3 = df_sub(R3, df_mul(df_add(mk, -s.kdl), is));
-            const DF e = df_add(df_mul(df_sub(T2, P1), is), R3);      // rowR1_k + r3_k
-            sq[1][q] = df_st(R3);
-            sq[3][q] = df_st(e);
-            red[2] = df_add(red[2], R3);
-            red[3] = df_add(red[3], df_mul(e, q == m - 1 ? dl : im));
-        }
-    }
-    block_sum_df<4>(red, s_red);                 // ends with a barrier: sq is published too
-    const DF in = df_ld(C.in), imn = df_ld(C.imn), imin = df_ld(C.imin);
-    const DF T3 = red[2];
-    const DF cst = df_add(df_sub(df_mul(red[0], in), df_mul(red[1], imin)), df_mul(T3, in));
-    const DF sumd = df_ld(C.sumd);
-    const DF ds = df_mul(df_add(red[3], df_mul(cst, sumd)), imn);          // sum d_k s_k
-    const DF dsiw = df_mul(ds, df_ld(C.iw));
-    const DF tsum = df_neg(df_add(ds, df_mul(dsiw, sumd)));                // 1^T W-hat s
-    const DF tin = df_mul(tsum, in);
-    const DF yasum = df_add(tsum, df_mul(tin, (float)m));                  // 1^T y1a over k < m
-    const DF T3in = df_mul(T3, in);
-    const DF T3in2 = df_mul(T3in, in);
-    const float mpn = (float)(m + n);
-    for (int q = threadIdx.x; q < top; q += blockDim.x) {
-        if (q < n) {
-            const DF A = df_ld(sq[0][q]), B = df_ld(sq[2][q]);
-            sq[0][q] = df_st(df_sub(df_mul(A, in), df_mul(B, imin)));                    // mvA_j
-            sq[2][q] = df_st(df_sub(df_mul(df_add(df_sub(A, B), T3in), in), yasum));     // sy_j
-        }
-        if (q < m) {
-            const DF R3 = df_ld(sq[1][q]), e = df_ld(sq[3][q]);
-            const DF sk = df_mul(df_add(e, cst), imn);                                 // s_k
-            const DF ya = df_add(df_neg(df_mul(df_add(sk, dsiw), q == m - 1 ? dl : im)), tin);   // y1a_k
-            sq[1][q] = df_st(df_sub(df_add(df_mul(R3, in), T3in2), df_mul(ya, mpn)));  // mvS_k
-            sq[3][q] = df_st(df_sub(sk, df_mul(ya, (float)n)));                        // sp_k
-        }
-    }
-    __syncthreads();
-}
-
 // k_alpha32: the pieces of y-bar - y0 (pairs, kept for the restart), their
 // FP32 split for the sweep, and on check iterations the partial sums of
-// <b, y>, of <c, A^T(y-bar - y0)> and max |A^T y|.  An instance's 4mn pieces
-// are cut into chunks of kAlphaChunk (kAPT per thread, consecutive threads on
-// consecutive pieces); a CTA takes chunks in a grid-stride loop, loads the
-// inputs of all its pieces of the chunk, then forms the instance-wide stage
-// (once per instance it meets) while those loads are in flight, so a chunk
-// costs about one L2 round trip.  Per-chunk partial sums sit at the chunk's
-// index (dobj_part, cD_part; k_check adds them in order).
+// <b, y>, of <c, A^T(y-bar - y0)> and max |A^T y|, from the instance-wide
+// stage that k_vec32 left in stage2.  An instance's 4mn pieces are cut into
+// chunks of kAlphaChunk (kAPT per thread, consecutive threads on consecutive
+// pieces); a CTA takes chunks in a grid-stride loop and loads the inputs of
+// all its pieces of a chunk before it computes any, so a chunk costs about
+// one L2 round trip.  Per-chunk partial sums sit at the chunk's index
+// (dobj_part, cD_part; k_check adds them in order).
 template <bool CHECK>
 __global__ void __launch_bounds__(kThreads, 2) k_alpha32(const WorkDev* __restrict__ W, int j) {
-    __shared__ float2 sq[4][kMaxS];
     __shared__ float2 s_red[4 * 32];
     __shared__ float s_max[32];
     const int ninst = W->ninst;
     const int nchunk = W->pre_achunk[ninst];
     const int tid = threadIdx.x;
-    int cached = -1;
     for (int c = blockIdx.x; c < nchunk; c += gridDim.x) {
         // every thread resolves the chunk itself (uniform, no barrier)
         const int inst = find_inst(W->pre_achunk, ninst, c);
@@ -792,11 +832,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_alpha32(const WorkDev* __restri
                 piece_slab(I, q, ps[u], pi[u]);
                 pin[u] = piece_in(I, ps[u], pi[u], CHECK);
             }
-        }
-        if (inst != cached) {
-            const StageIn sin = stage_in(I, tid);
-            alpha32_stage(I, sin, sq, s_red);
-            cached = inst;
         }
         if (cl == 0 && tid == 0) *I.p32 = make_p32(I.ctl->sigma, I.ctl->k + j, I.h, I.gadmm, I.relax);
         const CycleK& C = *I.cyc;
@@ -820,9 +855,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_alpha32(const WorkDev* __restri
                 // y1(k, j) on f1 slab j row k, -y1(k, j) on f2 slab k row j, with
                 // R1(k, j) = -(rowsum f1 slab j - rowsum f2 slab k)/sigma
                 const DF R1 = df_mul(df_sub(df_ld(a.x), df_ld(a.y)), is);
-                const DF fixed_row = f1 ? df_ld(sq[0][slab]) : df_ld(sq[1][slab - n]);
-                const DF other = f1 ? df_ld(sq[1][idx]) : df_ld(sq[0][idx]);
-                const DF y1 = df_mul(df_add(df_add(R1, fixed_row), other), imn);
+                const DF y1 = df_mul(df_add(df_add(R1, df_ld(a.s1)), df_ld(a.s2)), imn);
                 dv = f1 ? y1 : df_neg(y1);
             } else {
                 // y2(i, j) on f1 slab j, y3(k, l) on f2 slab k (y3(m, n) = 0)
@@ -831,8 +864,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_alpha32(const WorkDev* __restri
                 if (zero) {
                     dv = DF{0.f, 0.f};
                 } else {
-                    const DF colc = f1 ? df_mul(df_ld(sq[2][slab]), df_neg(df_ld(C.im)))
-                                       : df_mul(df_ld(sq[3][slab - n]), df_ld(C.in));
+                    const DF colc = f1 ? df_mul(df_ld(a.s1), df_neg(df_ld(C.im))) : df_mul(df_ld(a.s1), df_ld(C.in));
                     const DF isc = f1 ? df_ld(C.isim) : df_ld(C.isin);
                     dv = df_add(df_sub(df_ld(a.x), df_mul(isc, a.y.x)), colc);
                 }
@@ -841,7 +873,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_alpha32(const WorkDev* __restri
             I.dab2[o] = df_st(dv);
             const float df = df_f(dv);
             const float dh = rintf(df * grid) * igrid;          // on the grid 2^-E
-            I.ab32[o] = make_float4(a.a0.x + dh, a.a0.y + (df - dh), df, 0.f);
+            // w: the bin coordinate of the piece's row or column, for the sweep
+            I.ab32[o] = make_float4(a.a0.x + dh, a.a0.y + (df - dh), df, a.xc);
             if (CHECK) {
                 const DF full = df_add(DF{a.a0.x, a.a0.y}, dv);
                 ymax = fmaxf(ymax, fabsf(full.hi));
@@ -1068,9 +1101,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep64(const WorkDev* __restri
 // (x the bin coordinates of the slab's half, integers in FP32 mode), so the
 // grid part of the reduced cost is Gh = (A_r + B_c) - 2 h x_r x_c with
 // A_r = h x_r^2 - alpha_hi (per row) and B_c = h x_c^2 - beta_hi (per column):
-// every term is an integer multiple of 2^-E, so Gh is exact in FP32.
+// every term is an integer multiple of 2^-E, so Gh is exact in FP32.  The
+// coordinates travel in the w component of the alpha/beta pieces (k_alpha32),
+// so the sweep reads no coordinate array.  A tile's offsets in the per-slab
+// arrays are resolved once, by the issue side, into its descriptor.
 struct TileD {
     int inst, slab, band, S, NC, P, r0, r1, npass;
+    int row;          // g_row: first row entry of the slab
+    int tile;         // g_tile: index of the tile within its instance
+    int colp;         // g_colp: first column-partial entry of (slab, band)
+    long long elem;   // g_elem: first flow variable of the slab
 };
 
 // Resolve tile t; npass = 0 marks a tile of an instance that is not running,
@@ -1088,6 +1128,10 @@ __device__ __forceinline__ TileD tile_desc(const WorkDev* __restrict__ W, int t,
     d.P = kThreads / d.NC;
     d.r0 = d.band * I.TR;
     d.r1 = min(d.S, d.r0 + I.TR);
+    d.row = (int)g_row(I, d.slab);
+    d.tile = g_tile(I, d.slab, d.band);
+    d.colp = (int)g_colp(I, d.slab, d.band);
+    d.elem = (long long)g_elem(I, d.slab);
     if (I.ctl->status == ST_RUNNING) d.npass = (d.r1 - d.r0 + d.P - 1) / d.P;
     return d;
 }
@@ -1118,11 +1162,11 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkD
     struct Cur {
         const float* u;            // this thread's source of the next pass (u)
         const float* d;            // and of the delta
-        const float4* a;           // alpha pieces of the tile's rows
+        const float4* a;           // alpha piece of this thread's row of the tile (tid < tile rows)
         int step;                  // P rows, in floats
-        int row;                   // this thread's row (relative) in the next pass
-        int P, nr, left, it, ik;   // rows/pass, tile rows, passes left, tile, tiles started
-        bool first;                // next pass is the tile's first (carries the alpha pieces)
+        int mine;                  // passes of the tile left in which this thread copies a row
+        int left, it, ik;          // passes left, tile, tiles started
+        bool acopy;                // the next pass is the tile's first and this thread copies an alpha piece
     } c;
     auto set_tile = [&](int t) {
         TileD d = tile_desc(W, t, ntiles);
@@ -1134,16 +1178,16 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkD
         if (t < ntiles) {
             const HotInst& I = W->inst[d.inst];
             const int ro = tid / d.NC, cg = tid - ro * d.NC;
-            const size_t base = g_elem(I, d.slab) + ((size_t)d.r0 + ro) * d.S + (size_t)cg * NV;
+            const size_t base = (size_t)d.elem + ((size_t)d.r0 + ro) * d.S + (size_t)cg * NV;
             c.u = (const float*)I.u + base;
             c.d = (const float*)((j & 1) ? I.d1 : I.d0) + base;
-            c.a = I.ab32 + 2 * g_row(I, d.slab) + d.r0;
+            const int nr = d.r1 - d.r0;
+            c.a = I.ab32 + 2 * (size_t)d.row + d.r0 + tid;
             c.step = d.P * d.S;
-            c.row = ro < d.P ? ro : kMaxS;           // threads past P rows copy nothing
-            c.P = d.P;
-            c.nr = d.r1 - d.r0;
+            // rows ro, ro + P, ... below nr (threads past P rows copy nothing)
+            c.mine = ro < d.P && ro < nr ? (nr - ro + d.P - 1) / d.P : 0;
             c.left = d.npass;
-            c.first = true;
+            c.acopy = tid < nr;
             if (tid == 0) s_td[c.ik % kStages] = d;
         }
     };
@@ -1152,18 +1196,18 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkD
     // one commit group per call: the copies of global pass n (ring slot n % kStages)
     auto issue = [&](int n) {
         if (c.it < ntiles) {
-            if (c.row < c.nr) {
+            if (c.mine > 0) {
                 float4* su = s_stage + (size_t)(n % kStages) * 2 * kThreads + tid;
                 cp_async16(su, c.u);
                 cp_async16(su + kThreads, c.d);
+                --c.mine;
             }
-            if (c.first) {
-                if (tid < c.nr) cp_async16(&s_alpha[c.ik % kStages][tid], c.a + tid);
-                c.first = false;
+            if (c.acopy) {
+                cp_async16(&s_alpha[c.ik % kStages][tid], c.a);
+                c.acopy = false;
             }
             c.u += c.step;
             c.d += c.step;
-            c.row += c.P;
             if (--c.left == 0) {
                 ++c.ik;
                 set_tile(c.it + G);
@@ -1183,7 +1227,7 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkD
         const HotInst& I = W->inst[d.inst];
         const int ro = tid / d.NC, c0 = (tid - ro * d.NC) * NV;
         p = *I.p32;
-        const float4* ab = I.ab32 + 2 * g_row(I, d.slab) + d.S;
+        const float4* ab = I.ab32 + 2 * (size_t)d.row + d.S;
 #pragma unroll
         for (int e = 0; e < NV; ++e)
             bq[e] = ro < d.P ? ab[c0 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1206,14 +1250,13 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkD
         const bool active = ro < P;
         const int c0 = cg * NV;
         const float h = p.h;
-        const float* X = I.X32 + g_xbase(I, slab);             // bin coordinates of this half
 #pragma unroll
         for (int e = 0; e < NV; ++e) {
-            const float cf = active ? X[c0 + e] : 0.f;
+            const float cf = bq[e].w;                          // column coordinate x_c
             bq[e] = make_float4(fmaf(cf * cf, h, -bq[e].x), bq[e].y, bq[e].z, cf);
         }
         const float4* sa = s_alpha[ck % kStages];
-        float* __restrict__ dout = (float*)((j & 1) ? I.d0 : I.d1) + g_elem(I, slab) + ((size_t)r0 + ro) * S + c0;
+        float* __restrict__ dout = (float*)((j & 1) ? I.d0 : I.d1) + dc.elem + ((size_t)r0 + ro) * S + c0;
         const int ostep = P * S;
         float* srow = s_row + ro * (NC + 1) + cg;
         float* sxrow = s_xrow + (CHECK ? ro * (NC + 1) + cg : 0);
@@ -1237,7 +1280,7 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkD
                 const float uu[NV] = {U.x, U.y, U.z, U.w};
                 const float dd[NV] = {D.x, D.y, D.z, D.w};
                 const float4 a = sa[rr];
-                const float rf = X[r0 + rr];
+                const float rf = a.w;                         // row coordinate x_r
                 const float Ar = fmaf(rf * rf, h, -a.x);      // h x_r^2 - alpha_hi (exact)
                 const float m2hr = -2.f * h * rf;             // exact
                 float out[NV], xo[NV];
@@ -1289,7 +1332,7 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkD
         // under the reductions below
         have = !(c.it >= ntiles && ck + 1 >= c.ik);
         if (have) load_cols(s_td[(ck + 1) % kStages]);
-        const size_t cbase = g_colp(I, slab, band);
+        const size_t cbase = dc.colp;
         for (int cc = tid; cc < S; cc += kThreads) {
             DF a{0.f, 0.f}, x{0.f, 0.f};
             for (int qq = 0; qq < P; ++qq) {
@@ -1321,7 +1364,7 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkD
             kd[kNK - 1] = cd;
             block_sum_df<kNK>(kd, s_red);        // its barriers also publish s_rdf
             if (tid == 0) {
-                double* o = I.tile_kkt + (size_t)g_tile(I, slab, band) * kNK;
+                double* o = I.tile_kkt + (size_t)dc.tile * kNK;
 #pragma unroll
                 for (int qq = 0; qq < kNK; ++qq) o[qq] = df_val(kd[qq]);
             }
@@ -1336,9 +1379,9 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkD
                 a = df_add(a, df_ld(s_rdf[w][r]));
                 if constexpr (CHECK) x = df_add(x, df_ld(s_xdf[w][r]));
             }
-            a = df_add(a, df_ld(I.rs02[g_row(I, slab) + r0 + r]));      // + row sum of u
-            I.rs2[g_row(I, slab) + r0 + r] = df_st(a);
-            if constexpr (CHECK) I.xrs[g_row(I, slab) + r0 + r] = df_val(x);
+            a = df_add(a, df_ld(I.rs02[dc.row + r0 + r]));      // + row sum of u
+            I.rs2[dc.row + r0 + r] = df_st(a);
+            if constexpr (CHECK) I.xrs[dc.row + r0 + r] = df_val(x);
         }
     }
     cp_async_wait<0>();

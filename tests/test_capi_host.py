@@ -58,6 +58,7 @@ def test_library_loads_and_calls_host_only_entry_points(libpath):
     h = ctypes.c_void_p()
     assert lib.hot_create(ctypes.byref(h), ctypes.byref(bad)) == hot.HOT_EINVAL
     assert lib.hot_create(None, ctypes.byref(cfg)) == hot.HOT_EINVAL
+    assert lib.hot_sweep_timing(None, 1, None, None, None) == hot.HOT_EINVAL
 
 
 C_PROBE = r"""
