@@ -186,9 +186,7 @@ int inst_create(const PairHost& p, int fp64, const hot_config& cfg, double tol, 
     const size_t o_K2 = take(2 * MN * F2);
     const size_t o_vec2 = take(vec2_entries(m, n) * F2);
     const size_t o_dab2 = take(4 * MN * F2);
-    const size_t o_vcnt = take(sizeof(int));
     const size_t o_zero_end = off;                 // everything above starts at 0
-    const size_t o_stage2 = take(4 * (size_t)L * F2);
     const size_t o_mu1f = take(MN * F2);
     const size_t o_mu2f = take(MN * F2);
     const size_t o_cm2 = take(n * F2);
@@ -320,8 +318,6 @@ int inst_create(const PairHost& p, int fp64, const hot_config& cfg, double tol, 
     d.X64 = (double*)(sm + o_X64);
     d.csum2 = (float2*)(sm + o_cs2);
     d.cyc = (CycleK*)(sm + o_cyc);
-    d.stage2 = fp64 ? nullptr : (float2*)(sm + o_stage2);
-    d.vec_count = (int*)(sm + o_vcnt);
     d.ctl = (HotCtl*)(sm + o_ctl);
 
     // host-side constants uploaded once

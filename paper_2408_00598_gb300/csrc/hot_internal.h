@@ -157,8 +157,6 @@ struct HotInst {
     const double* X64;     // the same in FP64
     const float2* csum2;   // [m + n] C(x) = sum_y (X_x - X_y)^2 within each axis, as pairs
     struct CycleK* cyc;    // Prop. 3 constants of the current cycle
-    float2* stage2;        // [4][max(m, n)] Prop. 3 stage of the iteration (FP32 mode): mvA, mvS, sy, sp
-    int* vec_count;        // k_vec32 items finished in the current launch (0 between launches)
     HotCtl* ctl;
 };
 

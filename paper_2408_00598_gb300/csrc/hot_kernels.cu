@@ -536,7 +536,6 @@ constexpr int kVecRows = 64;
 struct PieceIn {
     float2 a0;            // anchor piece (hi, lo)
     float2 x, y, mu;
-    float2 s1, s2;        // stage entries: row piece mvA/mvS of its slab and of its row; column piece sy or sp
     float xc;             // bin coordinate of the piece's row or column
 };
 __device__ __forceinline__ void piece_slab(const HotInst& I, int q, int& slab, int& idx) {
@@ -559,18 +558,12 @@ __device__ __forceinline__ PieceIn piece_in(const HotInst& I, int slab, int idx,
     p.a0 = I.ab0_32[2 * g_row(I, slab) + idx];
     p.mu = make_float2(0.f, 0.f);
     p.xc = I.X32[g_xbase(I, slab) + (idx < Ls ? idx : idx - Ls)];
-    const int L = g_L(I);
-    const float2* __restrict__ sg = I.stage2;           // rows: mvA (j), mvS (k), sy (j), sp (k)
-    p.s2 = make_float2(0.f, 0.f);
     if (idx < Ls) {
         const int j = f1 ? slab : idx, k = f1 ? idx : slab - n;
         p.x = I.rs2[(size_t)n * m + (size_t)k * n + j];
         p.y = I.rs2[(size_t)j * m + k];
-        p.s1 = f1 ? sg[j] : sg[L + k];                    // the slab's own index
-        p.s2 = f1 ? sg[L + k] : sg[j];                    // the row's index
     } else {
         const int e = idx - Ls, nb = f1 ? I.nb1 : I.nb2;
-        p.s1 = f1 ? sg[2 * (size_t)L + slab] : sg[3 * (size_t)L + (slab - n)];
         p.x = I.K2[g_row(I, slab) + e];
         float kd = 0.f;
         for (int b = 0; b < nb; ++b) kd += I.cs32[g_colp(I, slab, b) + e];
@@ -620,10 +613,10 @@ __device__ __forceinline__ StageIn stage_in(const HotInst& I, int q) {
 
 // The cycle constants are read where they are used (L1 broadcasts) rather
 // than held in registers.
-// The results go to sq[w * L + q] (global; every entry is written and read
-// back by the same thread).  The row-block partials of P1/P2 are loaded
-// before they are added, and with L1 bypassed: they come from other CTAs of
-// the same launch (k_vec32).
+// The results go to sq[w * L + q] (every entry is written and read back by
+// the same thread; the final barrier publishes them to the CTA).  The
+// row-block partials of P1/P2 are loaded four at a time before they are
+// added (a zero pair adds nothing).
 __device__ void alpha32_stage(const HotInst& I, const StageIn& pre, float2* __restrict__ sq, float2* s_red) {
     const int m = I.m, n = I.n, L = g_L(I);
     const CycleK& C = *I.cyc;
@@ -636,14 +629,15 @@ __device__ void alpha32_stage(const HotInst& I, const StageIn& pre, float2* __re
     for (int q = threadIdx.x; q < top; q += blockDim.x) {
         const StageIn s = q == (int)threadIdx.x ? pre : stage_in(I, q);
         if (q < n) {                                               // column quantities, j = q
-            float2 pp[kMaxS / kVecRows];
-#pragma unroll
-            for (int b = 1; b < kMaxS / kVecRows; ++b)
-                pp[b] = b < r2 ? __ldcg(v + (size_t)(2 + r1 + b) * L + q) : make_float2(0.f, 0.f);
             DF P2 = df_ld(s.P2);
+            for (int b0 = 1; b0 < r2; b0 += 4) {                   // partials four at a time
+                float2 pp[4];
 #pragma unroll
-            for (int b = 1; b < kMaxS / kVecRows; ++b)
-                if (b < r2) P2 = df_add(P2, df_ld(pp[b]));
+                for (int u = 0; u < 4; ++u)
+                    pp[u] = b0 + u < r2 ? __ldcg(v + (size_t)(2 + r1 + b0 + u) * L + q) : make_float2(0.f, 0.f);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) P2 = df_add(P2, df_ld(pp[u]));
+            }
             const DF T1 = df_ld(s.T1);
             const DF A = df_mul(df_sub(P2, T1), is);                 // a_j = -(T1 - P2)/sigma
             const DF B = df_mul(df_sub(df_ld(s.cm), T1), is);         // bb_j
@@ -653,14 +647,15 @@ __device__ void alpha32_stage(const HotInst& I, const StageIn& pre, float2* __re
             red[1] = df_add(red[1], B);
         }
         if (q < m) {                                               // row quantities, k = q
-            float2 pp[kMaxS / kVecRows];
-#pragma unroll
-            for (int b = 1; b < kMaxS / kVecRows; ++b)
-                pp[b] = b < r1 ? __ldcg(v + (size_t)(2 + b) * L + q) : make_float2(0.f, 0.f);
             DF P1 = df_ld(s.P1);
+            for (int b0 = 1; b0 < r1; b0 += 4) {
+                float2 pp[4];
 #pragma unroll
-            for (int b = 1; b < kMaxS / kVecRows; ++b)
-                if (b < r1) P1 = df_add(P1, df_ld(pp[b]));
+                for (int u = 0; u < 4; ++u)
+                    pp[u] = b0 + u < r1 ? __ldcg(v + (size_t)(2 + b0 + u) * L + q) : make_float2(0.f, 0.f);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) P1 = df_add(P1, df_ld(pp[u]));
+            }
             const DF T2 = df_ld(s.T2);
             DF R3 = df_mul(df_sub(df_ld(s.rm), T2), is);              // r3_k
             // the dropped (m, n) row of eq. (7): column n-1 of the last f2 slab
@@ -706,8 +701,7 @@ __global__ void __launch_bounds__(kThreads) k_vec32(const WorkDev* __restrict__ 
     constexpr int kW = kThreads / 32;
     constexpr int kRW = kVecRows / kW;               // rows per warp in a P item
     __shared__ float2 s_p[kThreads];
-    __shared__ float2 s_red[4 * 32];
-    __shared__ int s_t[4];
+    __shared__ int s_t[3];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ninst = W->ninst;
     const int nitems = W->pre_vec[ninst];
@@ -777,22 +771,6 @@ __global__ void __launch_bounds__(kThreads) k_vec32(const WorkDev* __restrict__ 
                     I.vec2[(size_t)(2 + (which ? r1 : 0) + part) * L + q] = df_st(tot);
                 }
             }
-            // the CTA that finishes the instance's last item forms its Prop. 3
-            // stage (threadfence reduction: every writer fences before the
-            // count, the last CTA reads the sums with L1 bypassed; no CTA waits)
-            __threadfence();
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                const int prev = atomicAdd(I.vec_count, 1);
-                s_t[3] = prev == vec32_items_dev(m, n) - 1;
-            }
-            __syncthreads();
-            if (s_t[3]) {
-                __threadfence();
-                const StageIn sin = stage_in(I, threadIdx.x);
-                alpha32_stage(I, sin, I.stage2, s_red);
-                if (threadIdx.x == 0) *I.vec_count = 0;      // for the next iteration
-            }
         }
         __syncthreads();
     }
@@ -800,20 +778,25 @@ __global__ void __launch_bounds__(kThreads) k_vec32(const WorkDev* __restrict__ 
 
 // k_alpha32: the pieces of y-bar - y0 (pairs, kept for the restart), their
 // FP32 split for the sweep, and on check iterations the partial sums of
-// <b, y>, of <c, A^T(y-bar - y0)> and max |A^T y|, from the instance-wide
-// stage that k_vec32 left in stage2.  An instance's 4mn pieces are cut into
-// chunks of kAlphaChunk (kAPT per thread, consecutive threads on consecutive
-// pieces); a CTA takes chunks in a grid-stride loop and loads the inputs of
-// all its pieces of a chunk before it computes any, so a chunk costs about
-// one L2 round trip.  Per-chunk partial sums sit at the chunk's index
-// (dobj_part, cD_part; k_check adds them in order).
+// <b, y>, of <c, A^T(y-bar - y0)> and max |A^T y|.  An instance's 4mn pieces
+// are cut into chunks of kAlphaChunk (kAPT per thread, consecutive threads on
+// consecutive pieces); a CTA takes chunks in a grid-stride loop, loads the
+// inputs of all its pieces of a chunk, then forms the instance-wide stage
+// (once per instance it meets, in shared memory) while those loads are in
+// flight, so a chunk costs about one L2 round trip plus the stage.  (Forming
+// the stage once, in the CTA that finishes k_vec32's last item, measured
+// slower: the rest of the GPU idles while that one CTA works.)  Per-chunk
+// partial sums sit at the chunk's index (dobj_part, cD_part; k_check adds
+// them in order).
 template <bool CHECK>
 __global__ void __launch_bounds__(kThreads, 2) k_alpha32(const WorkDev* __restrict__ W, int j) {
+    __shared__ float2 sq[4 * kMaxS];
     __shared__ float2 s_red[4 * 32];
     __shared__ float s_max[32];
     const int ninst = W->ninst;
     const int nchunk = W->pre_achunk[ninst];
     const int tid = threadIdx.x;
+    int cached = -1;
     for (int c = blockIdx.x; c < nchunk; c += gridDim.x) {
         // every thread resolves the chunk itself (uniform, no barrier)
         const int inst = find_inst(W->pre_achunk, ninst, c);
@@ -833,6 +816,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_alpha32(const WorkDev* __restri
                 pin[u] = piece_in(I, ps[u], pi[u], CHECK);
             }
         }
+        if (inst != cached) {
+            const StageIn sin = stage_in(I, tid);
+            alpha32_stage(I, sin, sq, s_red);
+            cached = inst;
+        }
+        const int L = g_L(I);
         if (cl == 0 && tid == 0) *I.p32 = make_p32(I.ctl->sigma, I.ctl->k + j, I.h, I.gadmm, I.relax);
         const CycleK& C = *I.cyc;
         const DF is = df_ld(C.is), imn = df_ld(C.imn);
@@ -855,7 +844,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_alpha32(const WorkDev* __restri
                 // y1(k, j) on f1 slab j row k, -y1(k, j) on f2 slab k row j, with
                 // R1(k, j) = -(rowsum f1 slab j - rowsum f2 slab k)/sigma
                 const DF R1 = df_mul(df_sub(df_ld(a.x), df_ld(a.y)), is);
-                const DF y1 = df_mul(df_add(df_add(R1, df_ld(a.s1)), df_ld(a.s2)), imn);
+                const DF fixed_row = f1 ? df_ld(sq[slab]) : df_ld(sq[L + slab - n]);    // mvA_j / mvS_k
+                const DF other = f1 ? df_ld(sq[L + idx]) : df_ld(sq[idx]);              // mvS_k / mvA_j
+                const DF y1 = df_mul(df_add(df_add(R1, fixed_row), other), imn);
                 dv = f1 ? y1 : df_neg(y1);
             } else {
                 // y2(i, j) on f1 slab j, y3(k, l) on f2 slab k (y3(m, n) = 0)
@@ -864,7 +855,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_alpha32(const WorkDev* __restri
                 if (zero) {
                     dv = DF{0.f, 0.f};
                 } else {
-                    const DF colc = f1 ? df_mul(df_ld(a.s1), df_neg(df_ld(C.im))) : df_mul(df_ld(a.s1), df_ld(C.in));
+                    const DF colc = f1 ? df_mul(df_ld(sq[2 * L + slab]), df_neg(df_ld(C.im)))
+                                       : df_mul(df_ld(sq[3 * L + slab - n]), df_ld(C.in));
                     const DF isc = f1 ? df_ld(C.isim) : df_ld(C.isin);
                     dv = df_add(df_sub(df_ld(a.x), df_mul(isc, a.y.x)), colc);
                 }

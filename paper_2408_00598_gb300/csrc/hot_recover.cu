@@ -179,7 +179,11 @@ __device__ __forceinline__ void load_node_df(const float* __restrict__ x, int m,
     for (int t = lane; t < m; t += 32) a[t] = fmaxf(ra[t], 0.f);
     for (int t = lane; t < n; t += 32) b[t] = fmaxf(rb[t], 0.f);
     __syncwarp();
-    DF ca{0.f, 0.f}, cb{0.f, 0.f};
+    // prefix sums of non-negative entries never decrease, but the rounding of
+    // sums formed in different orders (the scan tree) can make a later one
+    // smaller by an ulp; a running maximum restores the order the merge walk
+    // relies on (ma, mb: maxima of the chunks done so far)
+    DF ca{0.f, 0.f}, cb{0.f, 0.f}, ma{0.f, 0.f}, mb{0.f, 0.f};
     const int L = m > n ? m : n;
     for (int base = 0; base < L; base += 32) {
         const int t = base + lane;
@@ -194,14 +198,25 @@ __device__ __forceinline__ void load_node_df(const float* __restrict__ x, int m,
         }
         DF ea = df_shfl_up(sa, 1), eb = df_shfl_up(sb, 1);       // exclusive within the chunk
         if (lane == 0) ea = eb = DF{0.f, 0.f};
-        if (t < m) A[t] = df_st(df_add(ca, ea));
-        if (t < n) B[t] = df_st(df_add(cb, eb));
+        DF pa = df_max(df_add(ca, ea), ma), pb = df_max(df_add(cb, eb), mb);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const DF ya = df_shfl_up(pa, o), yb = df_shfl_up(pb, o);
+            if (lane >= o) {
+                pa = df_max(pa, ya);
+                pb = df_max(pb, yb);
+            }
+        }
+        if (t < m) A[t] = df_st(pa);
+        if (t < n) B[t] = df_st(pb);
+        ma = df_shfl(pa, 31);
+        mb = df_shfl(pb, 31);
         ca = df_add(ca, df_shfl(sa, 31));
         cb = df_add(cb, df_shfl(sb, 31));
     }
     if (lane == 0) {
-        A[m] = df_st(ca);
-        B[n] = df_st(cb);
+        A[m] = df_st(df_max(ca, ma));
+        B[n] = df_st(df_max(cb, mb));
     }
     __syncwarp();
 }
@@ -210,8 +225,9 @@ __device__ __forceinline__ void load_node_df(const float* __restrict__ x, int m,
 // ends B[1..n] (ties: source first).  After the first d merged ends the walk
 // stands at source p, sink q = d - p; the step from there moves the overlap
 // min(A[p+1], B[q+1]) - max(A[p], B[q]) from source p to sink q (an entry
-// when positive) and passes the nearer end.  These are exactly the pairs and
-// masses of the north-west-corner loops, in (i, l) order.  A lane takes a
+// when positive and both the source and the sink hold mass) and passes the
+// nearer end.  These are the pairs and masses of the north-west-corner loops
+// of Algorithm 1, in (i, l) order.  A lane takes a
 // contiguous range of steps and finds its start by a binary search on the
 // merge diagonal (merge path), so a node costs about log2(m + n) +
 // (m + n)/32 steps per lane.
@@ -225,13 +241,14 @@ __device__ __forceinline__ int merge_split(const float2* A, const float2* B, int
     }
     return lo;
 }
-__device__ __forceinline__ int merge_walk(const float2* A, const float2* B, int m, int n, int p, int q, int steps,
-                                          int32_t* src, int32_t* dst, double* mass, size_t pos, int j, int k) {
+__device__ __forceinline__ int merge_walk(const float2* A, const float2* B, const float* a, const float* b, int m,
+                                          int n, int p, int q, int steps, int32_t* src, int32_t* dst, double* mass,
+                                          size_t pos, int j, int k) {
     int cnt = 0;
     for (int t = 0; t < steps && p < m && q < n; ++t) {
         const DF ae = df_ld(A[p + 1]), be = df_ld(B[q + 1]);
         const DF ov = df_sub(df_min(ae, be), df_max(df_ld(A[p]), df_ld(B[q])));
-        if (df_pos(ov)) {
+        if (df_pos(ov) && a[p] > 0.f && b[q] > 0.f) {
             if (src) {
                 src[pos + cnt] = p * n + j;
                 dst[pos + cnt] = k * n + q;
@@ -268,7 +285,7 @@ __global__ void __launch_bounds__(kRecWarps * 32) k_recover_df(const float* __re
         const int k = node / n, j = node % n;    // k-major node order
         load_node_df(x, m, n, k, j, a, b, A, B);
         const int p0 = d0 < d1 ? merge_split(A, B, m, n, d0) : m;
-        int c = merge_walk(A, B, m, n, p0, d0 - p0, d1 - d0, nullptr, nullptr, nullptr, 0, j, k);
+        int c = merge_walk(A, B, a, b, m, n, p0, d0 - p0, d1 - d0, nullptr, nullptr, nullptr, 0, j, k);
         if (count_only) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
@@ -294,7 +311,8 @@ __global__ void __launch_bounds__(kRecWarps * 32) k_recover_df(const float* __re
                 if (lane >= o) incl += y;
             }
             if (c > 0)
-                merge_walk(A, B, m, n, p0, d0 - p0, d1 - d0, src, dst, mass, (size_t)(offs[node] + incl - c), j, k);
+                merge_walk(A, B, a, b, m, n, p0, d0 - p0, d1 - d0, src, dst, mass, (size_t)(offs[node] + incl - c), j,
+                           k);
         }
         __syncwarp();
     }
