@@ -246,7 +246,6 @@ inline size_t vec2_entries(int m, int n) {
 }
 void launch_solve_kernels(const WorkDev* w, const LaunchDims& ld, int fp64, int j, bool check, cudaStream_t st);
 void launch_sweep(const WorkDev* w, const LaunchDims& ld, int fp64, int j, bool check, cudaStream_t st);
-void launch_iteration(const WorkDev* w, const LaunchDims& ld, int fp64, int j, bool check, cudaStream_t st);
 void launch_block_end(const WorkDev* w, const LaunchDims& ld, int fp64, int K, double a1, double a2, double a3,
                       cudaStream_t st);
 LaunchDims make_launch_dims(int device, int fp64);

@@ -96,17 +96,6 @@ __device__ __forceinline__ float block_max(float v, float* sh) {
     return r;  // valid in thread 0
 }
 
-// FP32 sums of up to 8 terms, accumulated in FP64 (fixed order).
-__device__ __forceinline__ double sum_f32_strided(const float* p, int count, int stride) {
-    double acc = 0.0;
-    for (int q0 = 0; q0 < count; q0 += 8) {
-        float g = 0.f;
-        const int q1 = min(count, q0 + 8);
-        for (int q = q0; q < q1; ++q) g += p[q * stride];
-        acc += (double)g;
-    }
-    return acc;
-}
 __device__ __forceinline__ double sum_f64_strided(const double* p, int count, int stride) {
     double acc = 0.0;
     for (int q = 0; q < count; ++q) acc += p[q * stride];
@@ -1924,11 +1913,6 @@ void launch_sweep(const WorkDev* w, const LaunchDims& ld, int fp64, int j, bool 
         launch(ld, k_sweep32<true>, ld.grid_tile_chk, kSweepSmemChk, st, w, j);
     else
         launch(ld, k_sweep32<false>, ld.grid_tile, kSweepSmem, st, w, j);
-}
-
-void launch_iteration(const WorkDev* w, const LaunchDims& ld, int fp64, int j, bool check, cudaStream_t st) {
-    launch_solve_kernels(w, ld, fp64, j, check, st);
-    launch_sweep(w, ld, fp64, j, check, st);
 }
 
 void launch_block_end(const WorkDev* w, const LaunchDims& ld, int fp64, int K, double a1, double a2, double a3,
