@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--size", type=int, default=256)
     ap.add_argument("--kind", default="white")
     ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32",
+                    help="solve mode: FP32 bulk (the default) or the plain FP64 form")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=512)
     ap.add_argument("--rate", type=float, default=200.0)
@@ -212,7 +214,7 @@ def bench_solve(args, dist):
     # a dedicated stream: the library enqueues all its work on it, so CUDA
     # events recorded on it bracket exactly the solver's device work
     stream = torch.cuda.Stream(device=dist.local_rank)
-    ctx = hot.Context(device=dist.local_rank, precision="fp32", stream=stream.cuda_stream)
+    ctx = hot.Context(device=dist.local_rank, precision=args.precision, stream=stream.cuda_stream)
     S = args.size
     mu1, mu2 = syn.make_pair(args.kind, S, 1000 + dist.rank)
     d1 = torch.from_numpy(mu1).cuda()
@@ -298,12 +300,13 @@ def bench_solve(args, dist):
         timing = "CUDA event pairs around every sweep of a separate profiled solve (no graph)"
     peak, peak_kind = measured_peak()
     traffic = None
-    if SWEEP_TRAFFIC["kernels_sha256"] == kernels_sha() and S == 256:
+    if SWEEP_TRAFFIC["kernels_sha256"] == kernels_sha() and S == 256 and args.precision == "fp32":
         traffic = SWEEP_TRAFFIC["bytes_per_launch"]
     total_ms = kt["sweep_ms"] + kt["sweep_check_ms"] + kt["solve_ms"] + kt["block_end_ms"]
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
-                "kernel": "k_sweep32<false> (Steps 2-4 fused, non-check iterations)",
+                "kernel": ("k_sweep32<false>" if args.precision == "fp32" else "k_sweep64")
+                          + " (Steps 2-4 fused, non-check iterations)",
                 "bytes_per_launch": kt["sweep_bytes"], "avg_launch_us": round(sweep_s * 1e6, 2),
                 "timed_launches": live["launches"],
                 "timing": timing,
@@ -317,15 +320,18 @@ def bench_solve(args, dist):
     out = {"metric": "solves/s (ms-to-1e-6 KKT) at N=256", "value": round(value, 4), "unit": "solves/s",
            "n_gpus": dist.world, "steps": args.steps, "warmup": max(3, args.warmup),
            "ms_per_step": round(1000.0 * t / args.steps, 3), "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": "single %dx%d pair (%s, seed 1000+rank), FP32-bulk Algorithm 2 to rel-KKT %g "
-                                  "+ Algorithm 1 plan recovery on the device" % (S, S, args.kind, args.tol),
+           "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+           "config": {"workload": "single %dx%d pair (%s, seed 1000+rank), %s Algorithm 2 to rel-KKT %g "
+                                  "+ Algorithm 1 plan recovery on the device"
+                                  % (S, S, args.kind, "FP32-bulk" if args.precision == "fp32" else "FP64",
+                                     args.tol),
                       "S": S, "flow_variables": 2 * S ** 3, "tol": args.tol,
                       "l2": "state %.0f MB > 129 MB L2 every iteration (no flush needed)" % (20 * S ** 3 / 1e6),
                       "parallelism": "replicas" if dist.world > 1 else "single"},
            "iterations_per_solve": iters, "restarts": r["restarts"],
            "ms_per_iteration": round(1000.0 * t / args.steps / iters, 4),
-           "hbm_gbs_per_iteration": round(12.0 * 2 * S ** 3 / (t / args.steps / iters) / 1e9, 1),
+           "hbm_gbs_per_iteration": round((12.0 if args.precision == "fp32" else 24.0) * 2 * S ** 3
+                                          / (t / args.steps / iters) / 1e9, 1),
            "plan_nnz": rec["n"], "plan_marginal_l1": rec["l1"], "rel_kkt": r["rel_kkt"],
            "roofline": roofline, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
            "clocks": clocks}
