@@ -32,12 +32,14 @@ int tile_rows(int m, int n, int fp64, int grid) {
     }
     // TR * L <= 16384 (row-partial buffer).  Tiles as tall as that allows
     // (the per-tile set-up and reductions cost more than a ragged last round
-    // of the persistent grid), halved while a slab-set this small leaves the
-    // grid's CTAs under two tiles each and a tile keeps at least 4 passes
+    // of the persistent grid), halved while a slab-set this small leaves some
+    // of the grid's CTAs without a tile and a tile keeps at least 4 passes
+    // (measured with the autotuner on GB300: TR = 64 at 64^2, 128^2 and 256^2,
+    // 32 at 512^2)
     int tr = std::min(std::min(L, 16384 / L), kMaxTR);
     auto tiles = [&](int t) { return (long long)n * ((m + t - 1) / t) + (long long)m * ((n + t - 1) / t); };
     if (grid > 0)
-        while (tiles(tr) < 2LL * grid && (long long)(tr / 2) * L >= 4096) tr /= 2;
+        while (tiles(tr) < (long long)grid && (long long)(tr / 2) * L >= 4096) tr /= 2;
     return tr;
 }
 
