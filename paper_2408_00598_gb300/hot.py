@@ -8,6 +8,15 @@ The functions keep the C names (``hot_create``, ``hot_solve``,
 ``hot_recover_plan``, ``hot_submit``, ``hot_poll``, ...); ``Context`` wraps
 them for convenience.  Histograms are row-major (m, n) float64 arrays (numpy
 on the host, or torch CUDA tensors on the context's device).
+
+Example::
+
+    from paper_2408_00598_gb300 import hot
+    with hot.Context(precision="fp32") as ctx:        # or "fp64"
+        r = ctx.solve(mu, nu, tol=1e-6)                 # mu, nu: (m, n), each summing to 1
+        src, dst, mass, l1 = ctx.recover_plan(r)        # entries src = i*n + j -> dst = k*n + l
+        ctx.release(r)
+    # r["ot_value"], r["dual_value"], r["rel_kkt"], r["iters"], ...
 """
 import ctypes
 import os
