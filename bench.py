@@ -317,7 +317,7 @@ def bench_solve(args, dist):
                     "prop3_solve": round(1000 * kt["solve_ms"] / max(1, kt["sweep_launches"] + kt["sweep_check_launches"]), 2),
                     "block_end_per_block": round(1000 * kt["block_end_ms"] / max(1, kt["sweep_check_launches"]), 2)}}
 
-    out = {"metric": "solves/s (ms-to-1e-6 KKT) at N=256", "value": round(value, 4), "unit": "solves/s",
+    out = {"metric": "solves/s (ms-to-1e-6 KKT) at N=%d" % S, "value": round(value, 4), "unit": "solves/s",
            "n_gpus": dist.world, "steps": args.steps, "warmup": max(3, args.warmup),
            "ms_per_step": round(1000.0 * t / args.steps, 3), "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
@@ -363,7 +363,7 @@ def bench_reference(args, dist):
         times.append(per_solve)
     per = statistics.median(times)
     v = 1.0 / per
-    return {"impl": "reference", "metric": "solves/s (ms-to-1e-6 KKT) at N=256", "value": round(v, 8),
+    return {"impl": "reference", "metric": "solves/s (ms-to-1e-6 KKT) at N=%d" % S, "value": round(v, 8),
             "unit": "solves/s", "n_gpus": dist.world, "steps": len(times), "warmup": args.warmup,
             "ms_per_step": round(per * 1000.0, 1), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",

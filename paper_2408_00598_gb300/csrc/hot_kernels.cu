@@ -102,6 +102,23 @@ __device__ __forceinline__ double sum_f64_strided(const double* p, int count, in
     return acc;
 }
 
+// Column total over a slab's bands: init + p[0] + p[stride] + ... (nb terms,
+// added left to right in band order), the loads issued four at a time so that
+// nb bands cost about nb / 4 round trips instead of nb.
+template <typename T>
+__device__ __forceinline__ T sum_bands(const T* p, size_t stride, int nb, T init = T(0)) {
+    T acc = init;
+    for (int b0 = 0; b0 < nb; b0 += 4) {
+        T v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = b0 + u < nb ? p[(size_t)(b0 + u) * stride] : T(0);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (b0 + u < nb) acc += v[u];
+    }
+    return acc;
+}
+
 // deterministic block sum of NV pairs; every thread receives the totals
 template <int NV>
 __device__ __forceinline__ void block_sum_df(DF (&v)[NV], float2* sh) {
@@ -351,8 +368,8 @@ __global__ void __launch_bounds__(kThreads) k_marg(const WorkDev* __restrict__ W
         for (int q = threadIdx.x; q < mi; q += blockDim.x) rm[q] = I.rowmu2[q];
         // the dropped (m, n) row of eq. (7): column n-1 of the last f2 slab
         const int sl = g_nslab(I) - 1;
-        double kap_last = I.kapa[g_row(I, sl) + (ni - 1)];
-        for (int b = 0; b < I.nb2; ++b) kap_last += I.cs_part[g_colp(I, sl, b) + (ni - 1)];
+        const double kap_last =
+            sum_bands(I.cs_part + g_colp(I, sl, 0) + (ni - 1), (size_t)ni, I.nb2, I.kapa[g_row(I, sl) + (ni - 1)]);
         const double mu_last = I.mu2[(size_t)(mi - 1) * ni + (ni - 1)];
         __syncthreads();
         auto A_ = [&](int j) { return -(T1[j] - P2[j]) * is; };
@@ -451,7 +468,7 @@ __global__ void __launch_bounds__(kThreads) k_alpha(const WorkDev* __restrict__ 
         };
         auto kap_delta = [&](int c) -> double {           // column total of the delta over the bands
             double k = 0.0;
-            for (int b = 0; b < nb; ++b) k += I.cs_part[g_colp(I, slab, b) + c];
+            k += sum_bands(I.cs_part + g_colp(I, slab, 0) + c, (size_t)Ls, nb);
             return k;
         };
         if (slab < ni) {
@@ -555,7 +572,7 @@ __device__ __forceinline__ PieceIn piece_in(const HotInst& I, int slab, int idx,
         const int e = idx - Ls, nb = f1 ? I.nb1 : I.nb2;
         p.x = I.K2[g_row(I, slab) + e];
         float kd = 0.f;
-        for (int b = 0; b < nb; ++b) kd += I.cs32[g_colp(I, slab, b) + e];
+        kd += sum_bands(I.cs32 + g_colp(I, slab, 0) + e, (size_t)Ls, nb);
         p.y = make_float2(kd, 0.f);
         if (check) p.mu = f1 ? I.mu1f[(size_t)e * n + slab] : I.mu2f[(size_t)(slab - n) * n + e];
     }
@@ -595,7 +612,7 @@ __device__ __forceinline__ StageIn stage_in(const HotInst& I, int q) {
     s.kdl = 0.f;
     if (q == m - 1) {
         const int sl = g_nslab(I) - 1;
-        for (int b = 0; b < I.nb2; ++b) s.kdl += I.cs32[g_colp(I, sl, b) + (n - 1)];
+        s.kdl += sum_bands(I.cs32 + g_colp(I, sl, 0) + (n - 1), (size_t)n, I.nb2);
     }
     return s;
 }
@@ -908,7 +925,7 @@ __device__ __forceinline__ void anchor_slab(const HotInst& I, int slab, double s
         const int k = slab < ni ? q : slab - ni;
         I.R1a[ro + q] = -(I.rs0[(size_t)j * mi + k] - I.rs0[f2 + (size_t)k * ni + j]) * is;
         double kap = 0.0;
-        for (int b = 0; b < nb; ++b) kap += I.cs0_part[g_colp(I, slab, b) + q];
+        kap += sum_bands(I.cs0_part + g_colp(I, slab, 0) + q, (size_t)Ls, nb);
         I.kapa[ro + q] = kap;
         if (!I.fp64) {
             // pairs for the FP32-mode solve: the row sums of u (also those of
@@ -1681,12 +1698,12 @@ __global__ void __launch_bounds__(kThreads) k_kkt1(const WorkDev* __restrict__ W
             } else if (q < 2 * MN) {                       // mu1 rows (i, j)
                 const int j = (q - MN) / m, i = (q - MN) % m;
                 double kap = 0.0;
-                for (int b = 0; b < I.nb1; ++b) kap += I.xcs_part[g_colp(I, j, b) + i];
+                kap += sum_bands(I.xcs_part + g_colp(I, j, 0) + i, (size_t)m, I.nb1);
                 res = kap - I.mu1[(size_t)i * n + j];
             } else {                                       // mu2 rows (k, l), the last one dropped
                 const int k = (q - 2 * MN) / n, l = (q - 2 * MN) % n;
                 double kap = 0.0;
-                for (int b = 0; b < I.nb2; ++b) kap += I.xcs_part[g_colp(I, n + k, b) + l];
+                kap += sum_bands(I.xcs_part + g_colp(I, n + k, 0) + l, (size_t)n, I.nb2);
                 res = kap - I.mu2[(size_t)k * n + l];
             }
             v[0] = res * res;
