@@ -36,8 +36,8 @@ sys.path.insert(0, ROOT)
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the FP32 sweep
 # (k_sweep32<false>) on the 256^3 x 2 state, and the hash of the kernel
 # source it was taken on (traffic is reported only while the source matches).
-SWEEP_TRAFFIC = {"kernels_sha256": "e8882982894a772e8793b7953b1554b0c5a2ac14b7b01fab9a963d7b4c038422",
-                 "bytes_per_launch": 273727488 + 104828672}
+SWEEP_TRAFFIC = {"kernels_sha256": "38e2a9a6699e44bae4f9410457a19c5e9401a3a5340db257fd0e57ad323a1370",
+                 "bytes_per_launch": 273729024 + 104790528}
 
 # iterations of Algorithm 2 (with the restart rule) that the FP64 oracle takes
 # to rel-KKT tol on the default bench pair (synthetic.make_pair("white", 256,
