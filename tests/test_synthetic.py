@@ -35,3 +35,12 @@ def test_mixed_batch():
     batch = syn.mixed_batch([32, 48, 64], 20, 1)
     assert len(batch) == 20
     assert {b[1] for b in batch} <= {32, 48, 64}
+
+
+@pytest.mark.parametrize("kind", syn.KINDS)
+@pytest.mark.parametrize("m,n", [(8, 12), (20, 8), (24, 72)])
+def test_rectangular_pairs(kind, m, n):
+    a, b = syn.make_pair(kind, m, 3, n=n)
+    for h in (a, b):
+        assert h.shape == (m, n) and h.min() >= 0.0
+        assert abs(h.sum() - 1.0) < 1e-12
