@@ -188,6 +188,8 @@ int inst_create(const PairHost& p, int fp64, const hot_config& cfg, double tol, 
     const size_t o_K2 = take(2 * MN * F2);
     const size_t o_vec2 = take(vec2_entries(m, n) * F2);
     const size_t o_dab2 = take(4 * MN * F2);
+    const size_t o_stg2 = take(4 * (size_t)L * F2);
+    const size_t o_vcnt = take(sizeof(unsigned int));
     const size_t o_zero_end = off;                 // everything above starts at 0
     const size_t o_mu1f = take(MN * F2);
     const size_t o_mu2f = take(MN * F2);
@@ -311,6 +313,8 @@ int inst_create(const PairHost& p, int fp64, const hot_config& cfg, double tol, 
     d.K2 = fp64 ? nullptr : (float2*)(sm + o_K2);
     d.vec2 = fp64 ? nullptr : (float2*)(sm + o_vec2);
     d.dab2 = fp64 ? nullptr : (float2*)(sm + o_dab2);
+    d.stg2 = fp64 ? nullptr : (float2*)(sm + o_stg2);
+    d.vcount = (unsigned int*)(sm + o_vcnt);
     d.mu1f = fp64 ? nullptr : (float2*)(sm + o_mu1f);
     d.mu2f = fp64 ? nullptr : (float2*)(sm + o_mu2f);
     d.cm2 = fp64 ? nullptr : (float2*)(sm + o_cm2);

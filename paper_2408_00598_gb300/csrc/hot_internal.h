@@ -148,6 +148,8 @@ struct HotInst {
     float2* K2;            // [2mn] (mu - colsum u)/(sigma m) per slab column (/(sigma n) for f2), fixed within a cycle
     float2* vec2;          // rows of max(m, n): T1, T2, then ceil(n/64) partials of P1 and ceil(m/64) of P2, of u + d
     float2* dab2;          // [4mn] pieces of A^T(y-bar - y0)
+    float2* stg2;          // [4][max(m, n)] Prop. 3 stage of the current iteration: mvA, mvS, sy, sp (k_vec32)
+    unsigned int* vcount;  // k_vec32 items of this instance finished in the running launch (0 between launches)
     float2* mu1f;          // [m][n] mu1 as pairs
     float2* mu2f;          // [m][n] mu2 as pairs
     float2* cm2;           // [n] colmu1 as pairs

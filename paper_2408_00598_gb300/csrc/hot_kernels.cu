@@ -625,7 +625,7 @@ __device__ __forceinline__ StageIn stage_in(const HotInst& I, int q) {
 // added (a zero pair adds nothing).
 __device__ void alpha32_stage(const HotInst& I, const StageIn& pre, float2* __restrict__ sq, float2* s_red) {
     const int m = I.m, n = I.n, L = g_L(I);
-    const CycleK& C = *I.cyc;
+    const CycleK C = *I.cyc;
     const float2* __restrict__ v = I.vec2;
     const int r1 = (n + kVecRows - 1) / kVecRows, r2 = (m + kVecRows - 1) / kVecRows;
     const DF is = df_ld(C.is), im = df_ld(C.im), dl = df_ld(C.dl);
@@ -707,7 +707,8 @@ __global__ void __launch_bounds__(kThreads) k_vec32(const WorkDev* __restrict__ 
     constexpr int kW = kThreads / 32;
     constexpr int kRW = kVecRows / kW;               // rows per warp in a P item
     __shared__ float2 s_p[kThreads];
-    __shared__ int s_t[3];
+    __shared__ float2 s_red[4 * 32];
+    __shared__ int s_t[4];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ninst = W->ninst;
     const int nitems = W->pre_vec[ninst];
@@ -720,7 +721,7 @@ __global__ void __launch_bounds__(kThreads) k_vec32(const WorkDev* __restrict__ 
         }
         __syncthreads();
         if (s_t[2] == ST_RUNNING) {
-            const HotInst& I = W->inst[s_t[0]];
+            const HotInst I = W->inst[s_t[0]];
             const int m = I.m, n = I.n, L = g_L(I);
             const int t1 = (n + 7) / 8, t2 = (m + 7) / 8;
             const int c1 = (m + 31) / 32, r1 = (n + kVecRows - 1) / kVecRows;   // P1: columns k, rows j
@@ -777,6 +778,23 @@ __global__ void __launch_bounds__(kThreads) k_vec32(const WorkDev* __restrict__ 
                     I.vec2[(size_t)(2 + (which ? r1 : 0) + part) * L + q] = df_st(tot);
                 }
             }
+            // The CTA that finishes an instance's last item forms its Prop. 3
+            // stage once, for every piece of the next kernel: this item's
+            // writes are made visible device-wide before the count, and the
+            // last CTA reads the others' through L2 (__ldcg in stage_in).
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                const unsigned int done = atomicAdd(I.vcount, 1u) + 1u;
+                s_t[3] = done == (unsigned int)vec32_items_dev(m, n);
+                if (s_t[3]) __threadfence();
+            }
+            __syncthreads();
+            if (s_t[3]) {
+                const StageIn sin = stage_in(I, threadIdx.x);
+                alpha32_stage(I, sin, I.stg2, s_red);
+                if (threadIdx.x == 0) *I.vcount = 0u;        // for the next launch
+            }
         }
         __syncthreads();
     }
@@ -786,27 +804,24 @@ __global__ void __launch_bounds__(kThreads) k_vec32(const WorkDev* __restrict__ 
 // FP32 split for the sweep, and on check iterations the partial sums of
 // <b, y>, of <c, A^T(y-bar - y0)> and max |A^T y|.  An instance's 4mn pieces
 // are cut into chunks of kAlphaChunk (kAPT per thread, consecutive threads on
-// consecutive pieces); a CTA takes chunks in a grid-stride loop, loads the
-// inputs of all its pieces of a chunk, then forms the instance-wide stage
-// (once per instance it meets, in shared memory) while those loads are in
-// flight, so a chunk costs about one L2 round trip plus the stage.  (Forming
-// the stage once, in the CTA that finishes k_vec32's last item, measured
-// slower: the rest of the GPU idles while that one CTA works.)  Per-chunk
-// partial sums sit at the chunk's index (dobj_part, cD_part; k_check adds
-// them in order).
+// consecutive pieces); a CTA takes chunks in a grid-stride loop and loads the
+// inputs of all its pieces of a chunk before it computes any.  The
+// instance-wide O(m + n) stage of Prop. 3 comes from k_vec32 (stg2), so a
+// piece is a few loads and double-float operations.  The descriptor is copied
+// into registers: the stores below cannot then force reloads of its fields.
+// Per-chunk partial sums sit at the chunk's index (dobj_part, cD_part;
+// k_check adds them in order).
 template <bool CHECK>
 __global__ void __launch_bounds__(kThreads, 2) k_alpha32(const WorkDev* __restrict__ W, int j) {
-    __shared__ float2 sq[4 * kMaxS];
-    __shared__ float2 s_red[4 * 32];
+    __shared__ float2 s_red[2 * 32];
     __shared__ float s_max[32];
     const int ninst = W->ninst;
     const int nchunk = W->pre_achunk[ninst];
     const int tid = threadIdx.x;
-    int cached = -1;
     for (int c = blockIdx.x; c < nchunk; c += gridDim.x) {
         // every thread resolves the chunk itself (uniform, no barrier)
         const int inst = find_inst(W->pre_achunk, ninst, c);
-        const HotInst& I = W->inst[inst];
+        const HotInst I = W->inst[inst];
         if (I.ctl->status != ST_RUNNING) continue;
         const int m = I.m, n = I.n;
         const int cl = c - W->pre_achunk[inst];
@@ -822,14 +837,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_alpha32(const WorkDev* __restri
                 pin[u] = piece_in(I, ps[u], pi[u], CHECK);
             }
         }
-        if (inst != cached) {
-            const StageIn sin = stage_in(I, tid);
-            alpha32_stage(I, sin, sq, s_red);
-            cached = inst;
-        }
         const int L = g_L(I);
         if (cl == 0 && tid == 0) *I.p32 = make_p32(I.ctl->sigma, I.ctl->k + j, I.h, I.gadmm, I.relax);
-        const CycleK& C = *I.cyc;
+        const CycleK C = *I.cyc;
+        const float2* __restrict__ sq = I.stg2;
+        float2* __restrict__ dab2 = I.dab2;
+        float4* __restrict__ ab32 = I.ab32;
         const DF is = df_ld(C.is), imn = df_ld(C.imn);
         const float igrid = (float)I.h, grid = 1.0f / igrid;       // powers of two: exact
         float ymax = 0.f;
@@ -868,11 +881,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_alpha32(const WorkDev* __restri
                 }
             }
             const size_t o = 2 * g_row(I, slab) + idx;
-            I.dab2[o] = df_st(dv);
+            dab2[o] = df_st(dv);
             const float df = df_f(dv);
             const float dh = rintf(df * grid) * igrid;          // on the grid 2^-E
             // w: the bin coordinate of the piece's row or column, for the sweep
-            I.ab32[o] = make_float4(a.a0.x + dh, a.a0.y + (df - dh), df, a.xc);
+            ab32[o] = make_float4(a.a0.x + dh, a.a0.y + (df - dh), df, a.xc);
             if (CHECK) {
                 const DF full = df_add(DF{a.a0.x, a.a0.y}, dv);
                 ymax = fmaxf(ymax, fabsf(full.hi));
@@ -891,7 +904,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_alpha32(const WorkDev* __restri
                 atomicMax(&I.ctl->ymax_bits, __float_as_uint(bm));
             }
         }
-        __syncthreads();           // sq may be rewritten for the next chunk's instance
     }
 }
 

@@ -19,15 +19,21 @@ def digest(mu1, mu2):
     return h.hexdigest()
 
 
-def oracle_case(name):
+def oracle_case(name, live=True):
     """(mu1, mu2, record) for a stored case; the record is recomputed by the
-    oracle when this machine's generator output differs from the stored one."""
+    oracle when this machine's generator output differs from the stored one
+    (live=False: the test is skipped instead, for cases the oracle takes many
+    minutes on)."""
     with open(GOLDEN) as f:
         rec = json.load(f)["cases"][name]
     mu1, mu2 = syn.make_pair(rec["kind"], rec["S"], rec["seed"])
     if digest(mu1, mu2) != rec["sha256"]:
+        if not live:
+            import pytest
+            pytest.skip("the seeded generator gives other histograms on this machine")
         from oracle import hot
-        r = hot.hot_solve(mu1, mu2, tol=rec["tol"], max_iter=rec["max_iter"])
+        p = hot.HotParams(stop=rec.get("stop", "relative"))
+        r = hot.hot_solve(mu1, mu2, tol=rec["tol"], max_iter=rec["max_iter"], params=p)
         rec = dict(rec, ot_value=r.ot_value, dual_value=r.dual_value, rel_kkt=r.rel_kkt, iters=r.iters,
                    restarts=r.restarts, live=True)
     return mu1, mu2, rec
@@ -38,3 +44,11 @@ def case_names(prefix):
         return []
     with open(GOLDEN) as f:
         return sorted(k for k in json.load(f)["cases"] if k.startswith(prefix))
+
+
+def rec_is_cheap(name):
+    """True when the oracle reruns a stored case in under a minute or so (S <= 64
+    at a relative stopping rule), so a test may recompute it live."""
+    with open(GOLDEN) as f:
+        rec = json.load(f)["cases"][name]
+    return rec["S"] <= 64 and rec.get("stop", "relative") == "relative"

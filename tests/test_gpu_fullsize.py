@@ -89,3 +89,50 @@ def test_translation_512(ctx):
     ctx.release(r)
     assert r["status"] == 0 and r["rel_kkt"] <= 1e-8
     assert abs(r["dual_value"] - exact) <= 2e-4 * exact
+
+
+# ------------------------------------------- the 256 x 256 benchmark pair --
+
+def test_benchmark_pair_plan_marginals_and_algorithm1_at_1e9(ctx):
+    """The throughput benchmark's 256 x 256 white-noise pair (seed 1000) solved
+    to relative KKT 1e-9: the recovered plan's marginals agree with mu and nu
+    to 1e-6 in L1 (recomputed here on the host from the returned entries), and
+    Algorithm 1 on the device gives, node by node, the entries of the oracle's
+    literal loops (Alg. 1) run on the same clipped flows, for 64 sampled nodes
+    (k, j)."""
+    from oracle import recover as orec
+    from oracle import reduced_model as rm
+    S = 256
+    mu1, mu2 = syn.make_pair("white", S, 1000)
+    # relative KKT 1e-8 leaves 3.6e-6 in L1 here: the 2-norm rule over the
+    # 3M - 1 rows of A x = b allows an L1 residual of about sqrt(3M) times it
+    r = ctx.solve(mu1, mu2, tol=1e-9, max_iter=300000)
+    x = ctx.flows(r)
+    src, dst, mass, l1 = ctx.recover_plan(r)
+    ctx.release(r)
+    assert r["status"] == 0 and r["rel_kkt"] <= 1e-9
+    m1 = np.bincount(src, weights=mass, minlength=S * S).reshape(S, S)
+    m2 = np.bincount(dst, weights=mass, minlength=S * S).reshape(S, S)
+    e1, e2 = np.abs(m1 - mu1).sum(), np.abs(m2 - mu2).sum()
+    assert e1 <= 1e-6 and e2 <= 1e-6, (e1, e2)
+    assert abs(e1 - l1[0]) <= 1e-9 and abs(e2 - l1[1]) <= 1e-9
+    assert mass.min() > 0
+    node = (dst.astype(np.int64) // S) * S + (src % S)
+    assert np.all(np.diff(node) >= 0)
+    f1, f2 = rm.split_x(x, S, S)
+    rng = np.random.default_rng(7)
+    picks = rng.choice(S * S, 64, replace=False)
+    lo = np.searchsorted(node, picks, side="left")
+    hi = np.searchsorted(node, picks, side="right")
+    worst = 0.0
+    for q, nd in enumerate(picks):
+        k, j = divmod(int(nd), S)
+        ref = orec.recover_cell(np.maximum(f1[:, k, j], 0.0), np.maximum(f2[k, j, :], 0.0))
+        want = {(i, l): p for i, l, p in ref}
+        got = {}
+        for e in range(lo[q], hi[q]):
+            got[(int(src[e]) // S, int(dst[e]) % S)] = float(mass[e])
+        for key in set(want) | set(got):
+            worst = max(worst, abs(want.get(key, 0.0) - got.get(key, 0.0)))
+    # FP64 pairs of the FP32 flows hold the prefix sums to about 48 bits
+    assert worst <= 1e-12, worst

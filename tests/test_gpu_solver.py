@@ -15,7 +15,7 @@ from oracle import hot as ohot
 from oracle import recover as orec
 from oracle import reduced_model as rm
 from paper_2408_00598_gb300 import synthetic as syn
-from tests.gpu_helpers import case_names, oracle_case
+from tests.gpu_helpers import case_names, oracle_case, rec_is_cheap
 
 pytestmark = pytest.mark.gpu
 
@@ -84,7 +84,8 @@ def test_config1_fp64_16x16_against_oracle_and_exact(ctx64):
     assert r["status"] == 0 and r["rel_kkt"] <= 1e-8
     assert r["iters"] == rec["iters"]
     assert abs(r["ot_value"] - rec["ot_value"]) <= 1e-9 * rec["ot_value"]
-    assert abs(r["ot_value"] - rec["exact"]) <= 1e-5 * rec["exact"]
+    # the oracle stops 9.3e-7 (relative) from the exact optimum on this pair
+    assert abs(r["ot_value"] - rec["exact"]) <= 1e-6 * rec["exact"]
 
 
 def test_config1_fp32_16x16(ctx32):
@@ -92,18 +93,65 @@ def test_config1_fp32_16x16(ctx32):
     r = ctx32.solve(mu1, mu2, tol=1e-8, max_iter=100000)
     ctx32.release(r)
     assert r["status"] == 0 and r["rel_kkt"] <= 1e-8
+    assert r["iters"] == rec["iters"] and r["restarts"] == rec["restarts"]
     assert abs(r["ot_value"] - rec["ot_value"]) <= 1e-6 * rec["ot_value"]
-    assert abs(r["ot_value"] - rec["exact"]) <= 1e-5 * rec["exact"]
+    assert abs(r["dual_value"] - rec["dual_value"]) <= 1e-6 * rec["dual_value"]
 
 
-@pytest.mark.parametrize("name", case_names("c2_") + case_names("s16_"))
-def test_fp32_value_parity_at_paper_stopping_rule(ctx32, name):
-    """Relative KKT 1e-6 (eq. kkt_res): FP32 bulk value within 1e-6 of the oracle."""
-    mu1, mu2, rec = oracle_case(name)
-    r = ctx32.solve(mu1, mu2, tol=rec["tol"], max_iter=rec["max_iter"])
-    ctx32.release(r)
-    assert r["status"] == 0 and r["rel_kkt"] <= rec["tol"]
-    assert abs(r["ot_value"] - rec["ot_value"]) <= 1e-6 * abs(rec["ot_value"]), (r["iters"], rec["iters"])
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_config1_accuracy_parity(lib, precision):
+    """Accuracy parity: at relative KKT 1e-9 both objectives are within 1e-7 of
+    the exact min-cost-flow optimum of eq. (1) (the oracle's primal reaches
+    4.8e-8, its dual 2.4e-9 there), so the GPU's value must be within 1e-6 of
+    the exact value without depending on the trajectory."""
+    mu1, mu2, rec = oracle_case("c1_white16")
+    with lib.Context(precision=precision) as ctx:
+        r = ctx.solve(mu1, mu2, tol=1e-9, max_iter=200000)
+        ctx.release(r)
+    ex = rec["exact"]
+    assert r["status"] == 0 and r["rel_kkt"] <= 1e-9
+    assert abs(r["ot_value"] - ex) <= 1e-6 * ex
+    assert abs(r["dual_value"] - ex) <= 1e-6 * ex
+    # the certificate the large grids rely on: the primal-dual gap bounds the error
+    assert abs(r["ot_value"] - r["dual_value"]) <= 1e-6 * ex
+
+
+@pytest.mark.parametrize("name", case_names("c2_") + case_names("s16_") + case_names("c3_")
+                         + case_names("f3_"))
+def test_fp32_value_parity_at_paper_stopping_rule(lib, ctx32, name):
+    """FP32 bulk against the FP64 oracle on the same pair, both stopped by the
+    paper's rule (relative KKT eq. kkt_res at 1e-6; the c3_ cases are the
+    128 x 128 pairs and the 256 x 256 benchmark pair, also at 1e-8; the f3_
+    cases stop on the absolute KKT residual of Table VI at 1e-6).
+
+    * The dual objective <b, y-bar> agrees to 1e-6 relative.
+    * The primal objective <c, x-bar> agrees to 1e-6 of the OT value's size
+      wherever it is within 10 % of the dual.  Where it is not -- white noise
+      on 128 x 128 and larger grids at 1e-6, whose x-bar carries negative
+      parts that make <c, x-bar> a difference of nearly equal sums (-0.088
+      against an OT value of 0.715 on the 128 x 128 pair) -- FP32 storage of
+      the state moves it by up to 6e-6 of the OT value, and 2e-5 is asserted.
+    * Same restart decisions: the iteration counts agree to 1 % (the oracle
+      and the FP32 path stop at the same check, or one or two checks apart
+      when rel-KKT crosses the tolerance within rounding), 10 % for the
+      absolute rule's 1e4-iteration runs."""
+    mu1, mu2, rec = oracle_case(name, live=rec_is_cheap(name))
+    stop = rec.get("stop", "relative")
+    if stop == "relative":
+        r = ctx32.solve(mu1, mu2, tol=rec["tol"], max_iter=rec["max_iter"])
+        ctx32.release(r)
+    else:
+        with lib.Context(precision="fp32", stop=stop) as ctx:
+            r = ctx.solve(mu1, mu2, tol=rec["tol"], max_iter=rec["max_iter"])
+            ctx.release(r)
+    assert r["status"] == 0
+    assert (r["abs_kkt"] if stop == "absolute" else r["rel_kkt"]) <= rec["tol"]
+    band = 0.01 if stop == "relative" else 0.1
+    assert abs(r["iters"] - rec["iters"]) <= max(20, band * rec["iters"]), (r["iters"], rec["iters"])
+    assert abs(r["dual_value"] - rec["dual_value"]) <= 1e-6 * abs(rec["dual_value"])
+    scale = max(abs(rec["dual_value"]), abs(rec["ot_value"]))
+    cancelling = abs(rec["ot_value"] - rec["dual_value"]) > 0.1 * abs(rec["dual_value"])
+    assert abs(r["ot_value"] - rec["ot_value"]) <= (2e-5 if cancelling else 1e-6) * scale, (r["iters"], rec["iters"])
     if "exact" in rec:
         assert abs(r["ot_value"] - rec["exact"]) <= 5e-3 * rec["exact"]
 
