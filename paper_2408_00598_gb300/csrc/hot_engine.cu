@@ -274,6 +274,11 @@ int inst_create(const PairHost& p, int fp64, const hot_config& cfg, double tol, 
     for (double x : p.mu2) b2 += x * x;
     b2 -= p.mu2[MN - 1] * p.mu2[MN - 1];
     d.norm_b = std::sqrt(b2);
+    double s1 = 0.0, s2 = 0.0;
+    for (double x : p.mu1) s1 += x;
+    for (double x : p.mu2) s2 += x;
+    d.sum_mu1 = s1;
+    d.sum_mu2 = s2;
     char* big = I->big;
     const size_t VB = align256(V * es);
     d.u = big;
@@ -690,7 +695,7 @@ int run_solve(Ctx* ctx, const std::vector<PairHost>& pairs, double tol, long lon
                 cudaEventElapsedTime(&a, pev[3 * j], pev[3 * j + 1]);
                 cudaEventElapsedTime(&b, pev[3 * j + 1], pev[3 * j + 2]);
                 kt->solve_ms += a;
-                kt->solve_launches += launches_per_iteration(fp64) - 1;
+                kt->solve_launches += launches_per_iteration(fp64, j == K - 1) - 1;
                 if (j == K - 1) {
                     kt->sweep_check_ms += b;
                     kt->sweep_check_launches += 1;
@@ -730,7 +735,7 @@ int run_solve(Ctx* ctx, const std::vector<PairHost>& pairs, double tol, long lon
         cleanup();
         return HOT_ECUDA;
     }
-    const long long launches = nb * (K * launches_per_iteration(fp64) + kLaunchesBlockEnd);
+    const long long launches = nb * (launches_per_block(fp64, (int)K) + kLaunchesBlockEnd);
     for (size_t q = 0; q < insts.size(); ++q) {
         Inst* I = insts[q];
         cudaMemcpy(&I->ctl_host, I->desc.ctl, sizeof(HotCtl), cudaMemcpyDeviceToHost);

@@ -106,6 +106,8 @@ struct HotInst {
     double h;              // 2^-E
     double norm_b;         // ||b||
     double norm_c;         // ||c|| of the scaled problem
+    double sum_mu1;        // sum of mu1 (1 within 1e-9), the column totals' sum
+    double sum_mu2;        // sum of mu2 over every entry (the dropped one included)
     // per-instance arrays, sized for the slab layout: V = mn(m + n) flow
     // variables; "per slab row" arrays hold 2mn entries (g_row), "pieces" 4mn
     // (alpha then beta of each slab), column partials one row per band (g_colp)
@@ -230,8 +232,10 @@ struct LaunchDims {
     int grid_inst;
 };
 
-// FP64: k_vec, k_marg, k_alpha, k_sweep; FP32 bulk: k_vec32, k_alpha32, k_sweep
-inline int launches_per_iteration(int fp64) { return fp64 ? 4 : 3; }
+// launches of one iteration: FP64 k_vec, k_marg, k_alpha, k_sweep64; FP32
+// k_vec32, k_alpha32, k_sweep32
+inline int launches_per_iteration(int fp64, bool) { return fp64 ? 4 : 3; }
+inline int launches_per_block(int fp64, int K) { return K * launches_per_iteration(fp64, false); }
 constexpr int kLaunchesBlockEnd = 8;       // k_kkt1, k_check, 3 x k_restart, k_restart_sigma, k_anchor, k_block_end
 // work items of k_vec32 per instance: T1 (n outputs) and T2 (m outputs) in
 // items of 8, P1 (m columns over n rows) and P2 (n columns over m rows) in items
@@ -241,10 +245,11 @@ __host__ __device__ inline int vec32_items_dev(int m, int n) {
 }
 inline int vec32_items(int m, int n) { return vec32_items_dev(m, n); }
 // float2 entries of vec2: T1, T2, then the (n + 63)/64 partials of P1 and the
-// (m + 63)/64 partials of P2, each a row of max(m, n)
+// (m + 63)/64 partials of P2, then one row of per-item totals of the T1 and T2
+// items ((n + 7)/8 + (m + 7)/8 <= max(m, n) entries), each a row of max(m, n)
 inline size_t vec2_entries(int m, int n) {
     const int L = m > n ? m : n;
-    return (size_t)(2 + (n + 63) / 64 + (m + 63) / 64) * L;
+    return (size_t)(3 + (n + 63) / 64 + (m + 63) / 64) * L;
 }
 void launch_solve_kernels(const WorkDev* w, const LaunchDims& ld, int fp64, int j, bool check, cudaStream_t st);
 void launch_sweep(const WorkDev* w, const LaunchDims& ld, int fp64, int j, bool check, cudaStream_t st);

@@ -145,6 +145,7 @@ __device__ __forceinline__ void block_sum_df(DF (&v)[NV], float2* sh) {
     __syncthreads();
 }
 
+
 // ------------------------------------------------------ per-tile parameters --
 
 struct P64 {
@@ -542,6 +543,7 @@ constexpr int kVecRows = 64;
 struct PieceIn {
     float2 a0;            // anchor piece (hi, lo)
     float2 x, y, mu;
+    float2 s0, s1;        // the stage entries the piece uses (k_vec32): row pieces mvA_j, mvS_k; column pieces sy_j or sp_k
     float xc;             // bin coordinate of the piece's row or column
 };
 __device__ __forceinline__ void piece_slab(const HotInst& I, int q, int& slab, int& idx) {
@@ -564,11 +566,18 @@ __device__ __forceinline__ PieceIn piece_in(const HotInst& I, int slab, int idx,
     p.a0 = I.ab0_32[2 * g_row(I, slab) + idx];
     p.mu = make_float2(0.f, 0.f);
     p.xc = I.X32[g_xbase(I, slab) + (idx < Ls ? idx : idx - Ls)];
+    const int L = g_L(I);
+    const float2* __restrict__ sq = I.stg2;
     if (idx < Ls) {
+        const float2* __restrict__ rs = I.rs2;
         const int j = f1 ? slab : idx, k = f1 ? idx : slab - n;
-        p.x = I.rs2[(size_t)n * m + (size_t)k * n + j];
-        p.y = I.rs2[(size_t)j * m + k];
+        p.x = rs[(size_t)n * m + (size_t)k * n + j];
+        p.y = rs[(size_t)j * m + k];
+        p.s0 = sq[j];                 // mvA_j
+        p.s1 = sq[L + k];             // mvS_k
     } else {
+        p.s0 = f1 ? sq[2 * L + slab] : sq[3 * L + slab - n];   // sy_j / sp_k
+        p.s1 = make_float2(0.f, 0.f);
         const int e = idx - Ls, nb = f1 ? I.nb1 : I.nb2;
         p.x = I.K2[g_row(I, slab) + e];
         float kd = 0.f;
@@ -579,135 +588,185 @@ __device__ __forceinline__ PieceIn piece_in(const HotInst& I, int slab, int idx,
     return p;
 }
 
-// The instance-wide O(m + n) stage: from T1, T2, P1, P2 (k_vec32) the vectors
+// Constants of the piece formula for the current cycle (from CycleK) and the
+// cost grid 2^-E.
+struct PieceK {
+    DF is, imn, im, in, isim, isin;
+    float grid, igrid;
+};
+__device__ __forceinline__ PieceK piece_consts(const HotInst& I) {
+    const CycleK C = *I.cyc;
+    PieceK K;
+    K.is = df_ld(C.is);
+    K.imn = df_ld(C.imn);
+    K.im = df_ld(C.im);
+    K.in = df_ld(C.in);
+    K.isim = df_ld(C.isim);
+    K.isin = df_ld(C.isin);
+    K.igrid = (float)I.h;
+    K.grid = 1.0f / K.igrid;                 // powers of two: exact
+    return K;
+}
+
+// Piece idx of slab s of A^T(y-bar - y0) from its inputs and the stage sq of
+// k_vec32 (Prop. 3): row pieces (idx < side) are y1(k, j) on f1 slab j row k
+// and -y1(k, j) on f2 slab k row j, with
+//   y1(k, j) = (R1(k, j) + mvA_j + mvS_k) / (m + n),
+//   R1(k, j) = -(rowsum f1 slab j [k] - rowsum f2 slab k [j]) / sigma;
+// column pieces are y2(i, j) on f1 slab j and y3(k, l) on f2 slab k (y3(m, n) = 0,
+// the row dropped by eq. 7-8).  *zero is set for that last piece.
+__device__ __forceinline__ DF piece_dv(const HotInst& I, const PieceK& K, int slab, int idx, const PieceIn& a,
+                                      bool& zero) {
+    const int m = I.m, n = I.n;
+    const bool f1 = slab < n;
+    const int Ls = f1 ? m : n;
+    zero = false;
+    if (idx < Ls) {
+        const DF R1 = df_mul(df_sub(df_ld(a.x), df_ld(a.y)), K.is);
+        const DF y1 = df_mul(df_add(df_add(R1, df_ld(a.s0)), df_ld(a.s1)), K.imn);
+        return f1 ? y1 : df_neg(y1);
+    }
+    const int e = idx - Ls;
+    zero = !f1 && slab == n + m - 1 && e == n - 1;
+    if (zero) return DF{0.f, 0.f};
+    const DF colc = f1 ? df_mul(df_ld(a.s0), df_neg(K.im)) : df_mul(df_ld(a.s0), K.in);
+    const DF isc = f1 ? K.isim : K.isin;
+    return df_add(df_sub(df_ld(a.x), df_mul(isc, a.y.x)), colc);
+}
+
+// The float4 the sweep reads for a piece: the full piece A^T y-bar = anchor +
+// dv split into a part on the cost grid 2^-E (hi, so that c - hi_r - hi_c is
+// exact in FP32) and an FP32 remainder, then dv itself, then the bin
+// coordinate of the piece's row or column.
+__device__ __forceinline__ float4 piece_pack(const PieceIn& a, DF dv, const PieceK& K) {
+    const float df = df_f(dv);
+    const float dh = rintf(df * K.grid) * K.igrid;
+    return make_float4(a.a0.x + dh, a.a0.y + (df - dh), df, a.xc);
+}
+
+// The instance-wide O(m + n) stage of Prop. 3: from T1, T2, P1, P2 (k_vec32)
+// the vectors
 //   mvA_j = a_j/n - (1/m + 1/n) bb_j      (column part of y1-hat), j < n
 //   mvS_k = r3_k/n + T3/n^2 - (m+n) y1a_k (row part of y1, times m+n), k < m
 //   sy_j  = sum_k y1(k, j)                (for y2)
 //   sp_k  = sum_j y1(k, j)                (for y3)
-// into rows 0-3 of sq (mvA at j, mvS at k, sy at j, sp at k).  With e_k = rowR1_k + r3_k and d
-// the diagonal of W-hat, every global scalar follows from four sums: sum a,
-// sum bb, T3 = sum r3 and sum d_k e_k, since s_k = (e_k + cst)/(m+n) with
-// cst = sum a/n - (1/m+1/n) sum bb + T3/n.  Each thread forms the scalars
-// from the block sums itself (no single-thread section, no extra barrier).
+// into rows 0-3 of sq (mvA at j, mvS at k, sy at j, sp at k), with
+//   a_j = (P2_j - T1_j)/sigma, bb_j = (colmu1_j - T1_j)/sigma,
+//   r3_k = (rowmu2_k - T2_k)/sigma (less the dropped (m, n) entry's share at k = m-1),
+//   e_k = (T2_k - P1_k)/sigma + r3_k,  s_k = (e_k + cst)/(m+n).
+// Every global scalar is fixed by the two half totals F1 = sum_j T1_j = sum_k P1_k
+// and F2 = sum_k T2_k = sum_j P2_j (the state summed over the f1 and f2 slabs)
+// and the k = m-1 entries:
+//   sum a = (F2 - F1)/sigma,  sum bb = (sum mu1 - F1)/sigma,
+//   T3 = sum r3 = (sum mu2 - F2)/sigma - (dropped entry),
+//   sum d_k e_k = (1/m) ((F2 - F1)/sigma + T3) + (d_last - 1/m) e_{m-1}
+// (d the diagonal of W-hat: 1/m, ..., 1/m, d_last).  F1 and F2 come from the
+// per-item totals of k_vec32's T items (one block reduction); every thread
+// loads the k = m-1 entries itself, so the only barrier is that reduction's.
 struct StageIn {
-    float2 T1, P2, cm;    // j = threadIdx.x < n (P2: first row-block partial)
-    float2 T2, P1, rm;    // k = threadIdx.x < m (P1: first row-block partial)
-    float kdl;            // thread m-1: delta column total at the dropped (m, n) entry
+    DF T1, P2, cm;        // column quantities at j = q < n (P2 summed over its row blocks)
+    DF T2, P1, rm;        // row quantities at k = q < m (P1 summed over its row blocks)
 };
+// sum of the row-block partials at column q of rows first, first + 1, ...
+__device__ __forceinline__ DF sum_partials(const float2* __restrict__ v, int L, int first, int count, int q) {
+    DF acc{0.f, 0.f};
+    for (int b0 = 0; b0 < count; b0 += 4) {
+        float2 pp[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            pp[u] = b0 + u < count ? __ldcg(v + (size_t)(first + b0 + u) * L + q) : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc = df_add(acc, df_ld(pp[u]));
+    }
+    return acc;
+}
 __device__ __forceinline__ StageIn stage_in(const HotInst& I, int q) {
     const int m = I.m, n = I.n, L = g_L(I);
     const float2* __restrict__ v = I.vec2;
-    const int r1 = (n + kVecRows - 1) / kVecRows;      // row blocks of P1
+    const int r1 = (n + kVecRows - 1) / kVecRows, r2 = (m + kVecRows - 1) / kVecRows;
     StageIn s{};
     if (q < n) {
-        s.T1 = __ldcg(v + q);
-        s.P2 = __ldcg(v + (size_t)(2 + r1) * L + q);
-        s.cm = I.cm2[q];
+        s.T1 = df_ld(__ldcg(v + q));
+        s.P2 = sum_partials(v, L, 2 + r1, r2, q);
+        s.cm = df_ld(I.cm2[q]);
     }
     if (q < m) {
-        s.T2 = __ldcg(v + L + q);
-        s.P1 = __ldcg(v + 2 * (size_t)L + q);
-        s.rm = I.rm2[q];
-    }
-    s.kdl = 0.f;
-    if (q == m - 1) {
-        const int sl = g_nslab(I) - 1;
-        s.kdl += sum_bands(I.cs32 + g_colp(I, sl, 0) + (n - 1), (size_t)n, I.nb2);
+        s.T2 = df_ld(__ldcg(v + L + q));
+        s.P1 = sum_partials(v, L, 2, r1, q);
+        s.rm = df_ld(I.rm2[q]);
     }
     return s;
 }
 
-// The cycle constants are read where they are used (L1 broadcasts) rather
-// than held in registers.
-// The results go to sq[w * L + q] (every entry is written and read back by
-// the same thread; the final barrier publishes them to the CTA).  The
-// row-block partials of P1/P2 are loaded four at a time before they are
-// added (a zero pair adds nothing).
-__device__ void alpha32_stage(const HotInst& I, const StageIn& pre, float2* __restrict__ sq, float2* s_red) {
+// Every thread of the calling CTA takes part; the results are stored to sq
+// (global) by the thread of each index.
+__device__ void alpha32_stage(const HotInst& I, float2* __restrict__ sq, float2* s_red) {
     const int m = I.m, n = I.n, L = g_L(I);
     const CycleK C = *I.cyc;
     const float2* __restrict__ v = I.vec2;
     const int r1 = (n + kVecRows - 1) / kVecRows, r2 = (m + kVecRows - 1) / kVecRows;
-    const DF is = df_ld(C.is), im = df_ld(C.im), dl = df_ld(C.dl);
-    const DF mk = df_ld(C.mk);
-    DF red[4] = {DF{0.f, 0.f}, DF{0.f, 0.f}, DF{0.f, 0.f}, DF{0.f, 0.f}};
-    const int top = m > n ? m : n;
-    for (int q = threadIdx.x; q < top; q += blockDim.x) {
-        const StageIn s = q == (int)threadIdx.x ? pre : stage_in(I, q);
-        if (q < n) {                                               // column quantities, j = q
-            DF P2 = df_ld(s.P2);
-            for (int b0 = 1; b0 < r2; b0 += 4) {                   // partials four at a time
-                float2 pp[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    pp[u] = b0 + u < r2 ? __ldcg(v + (size_t)(2 + r1 + b0 + u) * L + q) : make_float2(0.f, 0.f);
-#pragma unroll
-                for (int u = 0; u < 4; ++u) P2 = df_add(P2, df_ld(pp[u]));
-            }
-            const DF T1 = df_ld(s.T1);
-            const DF A = df_mul(df_sub(P2, T1), is);                 // a_j = -(T1 - P2)/sigma
-            const DF B = df_mul(df_sub(df_ld(s.cm), T1), is);         // bb_j
-            sq[0 * (size_t)L + q] = df_st(A);
-            sq[2 * (size_t)L + q] = df_st(B);
-            red[0] = df_add(red[0], A);
-            red[1] = df_add(red[1], B);
-        }
-        if (q < m) {                                               // row quantities, k = q
-            DF P1 = df_ld(s.P1);
-            for (int b0 = 1; b0 < r1; b0 += 4) {
-                float2 pp[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    pp[u] = b0 + u < r1 ? __ldcg(v + (size_t)(2 + b0 + u) * L + q) : make_float2(0.f, 0.f);
-#pragma unroll
-                for (int u = 0; u < 4; ++u) P1 = df_add(P1, df_ld(pp[u]));
-            }
-            const DF T2 = df_ld(s.T2);
-            DF R3 = df_mul(df_sub(df_ld(s.rm), T2), is);              // r3_k
-            // the dropped (m, n) row of eq. (7): column n-1 of the last f2 slab
-            if (q == m - 1) R3 = df_sub(R3, df_mul(df_add(mk, -s.kdl), is));
-            const DF e = df_add(df_mul(df_sub(T2, P1), is), R3);      // rowR1_k + r3_k
-            sq[1 * (size_t)L + q] = df_st(R3);
-            sq[3 * (size_t)L + q] = df_st(e);
-            red[2] = df_add(red[2], R3);
-            red[3] = df_add(red[3], df_mul(e, q == m - 1 ? dl : im));
-        }
+    const int t1 = (n + 7) / 8, t2 = (m + 7) / 8;        // T items of k_vec32
+    const float2* __restrict__ tp = v + (size_t)(2 + r1 + r2) * L;
+    // F1, F2 from the T items' totals (t1 + t2 <= L <= 4 * kThreads)
+    DF red[2] = {DF{0.f, 0.f}, DF{0.f, 0.f}};
+    for (int q = threadIdx.x; q < t1 + t2; q += blockDim.x) {
+        const DF x = df_ld(__ldcg(tp + q));
+        if (q < t1) red[0] = df_add(red[0], x);
+        else red[1] = df_add(red[1], x);
     }
-    block_sum_df<4>(red, s_red);
-    const DF in = df_ld(C.in), imn = df_ld(C.imn), imin = df_ld(C.imin);
-    const DF T3 = red[2];
-    const DF cst = df_add(df_sub(df_mul(red[0], in), df_mul(red[1], imin)), df_mul(T3, in));
-    const DF sumd = df_ld(C.sumd);
-    const DF ds = df_mul(df_add(red[3], df_mul(cst, sumd)), imn);          // sum d_k s_k
-    const DF dsiw = df_mul(ds, df_ld(C.iw));
-    const DF tsum = df_neg(df_add(ds, df_mul(dsiw, sumd)));                // 1^T W-hat s
+    // the k = m-1 entries (every thread), and the entries of this thread's first index
+    const StageIn last = stage_in(I, m - 1);
+    const int sl = g_nslab(I) - 1;
+    const float kdl = sum_bands(I.cs32 + g_colp(I, sl, 0) + (n - 1), (size_t)n, I.nb2);
+    const StageIn own = stage_in(I, threadIdx.x);
+    block_sum_df<2>(red, s_red);
+    const DF F1 = red[0], F2 = red[1];
+    const DF is = df_ld(C.is), im = df_ld(C.im), in = df_ld(C.in), imn = df_ld(C.imn), imin = df_ld(C.imin);
+    const DF dl = df_ld(C.dl), sumd = df_ld(C.sumd), iw = df_ld(C.iw);
+    // the dropped (m, n) row of eq. (7): column n-1 of the last f2 slab
+    const DF drop = df_mul(df_add(df_ld(C.mk), -kdl), is);
+    const DF dF = df_mul(df_sub(F2, F1), is);
+    const DF suma = dF;
+    const DF sumbb = df_mul(df_sub(df_from(I.sum_mu1), F1), is);
+    const DF T3 = df_sub(df_mul(df_sub(df_from(I.sum_mu2), F2), is), drop);
+    const DF R3l = df_sub(df_mul(df_sub(last.rm, last.T2), is), drop);
+    const DF el = df_add(df_mul(df_sub(last.T2, last.P1), is), R3l);
+    const DF sde = df_add(df_mul(df_add(dF, T3), im), df_mul(el, df_sub(dl, im)));     // sum d_k e_k
+    const DF cst = df_add(df_sub(df_mul(suma, in), df_mul(sumbb, imin)), df_mul(T3, in));
+    const DF ds = df_mul(df_add(sde, df_mul(cst, sumd)), imn);                          // sum d_k s_k
+    const DF dsiw = df_mul(ds, iw);
+    const DF tsum = df_neg(df_add(ds, df_mul(dsiw, sumd)));                            // 1^T W-hat s
     const DF tin = df_mul(tsum, in);
-    const DF yasum = df_add(tsum, df_mul(tin, (float)m));                  // 1^T y1a over k < m
+    const DF yasum = df_add(tsum, df_mul(tin, (float)m));                              // 1^T y1a over k < m
     const DF T3in = df_mul(T3, in);
     const DF T3in2 = df_mul(T3in, in);
     const float mpn = (float)(m + n);
+    const int top = m > n ? m : n;
     for (int q = threadIdx.x; q < top; q += blockDim.x) {
+        const StageIn s = q == (int)threadIdx.x ? own : stage_in(I, q);
         if (q < n) {
-            const DF A = df_ld(sq[0 * (size_t)L + q]), B = df_ld(sq[2 * (size_t)L + q]);
-            sq[0 * (size_t)L + q] = df_st(df_sub(df_mul(A, in), df_mul(B, imin)));                    // mvA_j
-            sq[2 * (size_t)L + q] = df_st(df_sub(df_mul(df_add(df_sub(A, B), T3in), in), yasum));     // sy_j
+            const DF A = df_mul(df_sub(s.P2, s.T1), is);                                 // a_j
+            const DF B = df_mul(df_sub(s.cm, s.T1), is);                                 // bb_j
+            sq[0 * (size_t)L + q] = df_st(df_sub(df_mul(A, in), df_mul(B, imin)));                   // mvA_j
+            sq[2 * (size_t)L + q] = df_st(df_sub(df_mul(df_add(df_sub(A, B), T3in), in), yasum));    // sy_j
         }
         if (q < m) {
-            const DF R3 = df_ld(sq[1 * (size_t)L + q]), e = df_ld(sq[3 * (size_t)L + q]);
-            const DF sk = df_mul(df_add(e, cst), imn);                                 // s_k
+            DF R3 = df_mul(df_sub(s.rm, s.T2), is);                                      // r3_k
+            if (q == m - 1) R3 = df_sub(R3, drop);
+            const DF e = df_add(df_mul(df_sub(s.T2, s.P1), is), R3);
+            const DF sk = df_mul(df_add(e, cst), imn);                                   // s_k
             const DF ya = df_add(df_neg(df_mul(df_add(sk, dsiw), q == m - 1 ? dl : im)), tin);   // y1a_k
             sq[1 * (size_t)L + q] = df_st(df_sub(df_add(df_mul(R3, in), T3in2), df_mul(ya, mpn)));  // mvS_k
             sq[3 * (size_t)L + q] = df_st(df_sub(sk, df_mul(ya, (float)n)));                        // sp_k
         }
     }
-    __syncthreads();
 }
 
-__global__ void __launch_bounds__(kThreads) k_vec32(const WorkDev* __restrict__ W) {
+__global__ void __launch_bounds__(kThreads) k_vec32(const WorkDev* __restrict__ W, int j) {
     constexpr int kW = kThreads / 32;
     constexpr int kRW = kVecRows / kW;               // rows per warp in a P item
     __shared__ float2 s_p[kThreads];
-    __shared__ float2 s_red[4 * 32];
+    __shared__ float2 s_red[2 * 32];
     __shared__ int s_t[4];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ninst = W->ninst;
@@ -749,6 +808,16 @@ __global__ void __launch_bounds__(kThreads) k_vec32(const WorkDev* __restrict__ 
                     }
                     acc = warp_sum_df(acc);
                     if (lane == 0) I.vec2[which * L + q] = df_st(acc);
+                    if (lane == 0) s_p[warp] = df_st(acc);
+                } else if (lane == 0) {
+                    s_p[warp] = make_float2(0.f, 0.f);
+                }
+                // the item's total, for the half totals F1, F2 of the stage
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    DF tot = df_ld(s_p[0]);
+                    for (int w = 1; w < kW; ++w) tot = df_add(tot, df_ld(s_p[w]));
+                    I.vec2[(size_t)(2 + r1 + r2) * L + item] = df_st(tot);
                 }
             } else {
                 item -= t1 + t2;
@@ -779,21 +848,25 @@ __global__ void __launch_bounds__(kThreads) k_vec32(const WorkDev* __restrict__ 
                 }
             }
             // The CTA that finishes an instance's last item forms its Prop. 3
-            // stage once, for every piece of the next kernel: this item's
-            // writes are made visible device-wide before the count, and the
-            // last CTA reads the others' through L2 (__ldcg in stage_in).
-            __threadfence();
+            // stage once, for every piece of the next kernel.  The barrier
+            // orders this CTA's writes of the item before thread 0's fence,
+            // which makes them visible device-wide before the count (the
+            // pattern of a grid-wide barrier); the last CTA reads the others'
+            // through L2 (__ldcg in stage_in).
             __syncthreads();
             if (threadIdx.x == 0) {
+                __threadfence();
                 const unsigned int done = atomicAdd(I.vcount, 1u) + 1u;
                 s_t[3] = done == (unsigned int)vec32_items_dev(m, n);
                 if (s_t[3]) __threadfence();
             }
             __syncthreads();
             if (s_t[3]) {
-                const StageIn sin = stage_in(I, threadIdx.x);
-                alpha32_stage(I, sin, I.stg2, s_red);
-                if (threadIdx.x == 0) *I.vcount = 0u;        // for the next launch
+                alpha32_stage(I, I.stg2, s_red);
+                if (threadIdx.x == 0) {
+                    *I.vcount = 0u;                           // for the next launch
+                    *I.p32 = make_p32(I.ctl->sigma, I.ctl->k + j, I.h, I.gadmm, I.relax);
+                }
             }
         }
         __syncthreads();
@@ -822,10 +895,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_alpha32(const WorkDev* __restri
         // every thread resolves the chunk itself (uniform, no barrier)
         const int inst = find_inst(W->pre_achunk, ninst, c);
         const HotInst I = W->inst[inst];
-        if (I.ctl->status != ST_RUNNING) continue;
         const int m = I.m, n = I.n;
         const int cl = c - W->pre_achunk[inst];
         const int npieces = 4 * m * n;
+        // every input is loaded before the status is known (the instance's
+        // memory is valid either way), so the chunk costs one round trip less
         int ps[kAPT], pi[kAPT];
         PieceIn pin[kAPT];
 #pragma unroll
@@ -837,14 +911,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_alpha32(const WorkDev* __restri
                 pin[u] = piece_in(I, ps[u], pi[u], CHECK);
             }
         }
-        const int L = g_L(I);
-        if (cl == 0 && tid == 0) *I.p32 = make_p32(I.ctl->sigma, I.ctl->k + j, I.h, I.gadmm, I.relax);
-        const CycleK C = *I.cyc;
-        const float2* __restrict__ sq = I.stg2;
+        const PieceK K = piece_consts(I);
+        if (I.ctl->status != ST_RUNNING) continue;
         float2* __restrict__ dab2 = I.dab2;
         float4* __restrict__ ab32 = I.ab32;
-        const DF is = df_ld(C.is), imn = df_ld(C.imn);
-        const float igrid = (float)I.h, grid = 1.0f / igrid;       // powers of two: exact
         float ymax = 0.f;
         DF dob{0.f, 0.f};
         // <c, A^T(y-bar - y0)>: the cost is separable, so a slab contributes
@@ -854,38 +924,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_alpha32(const WorkDev* __restri
         for (int u = 0; u < kAPT; ++u) {
             if (ps[u] < 0) continue;
             const int slab = ps[u], idx = pi[u];
-            const bool f1 = slab < n;
-            const int Ls = f1 ? m : n;
+            const int Ls = slab < n ? m : n;
             const PieceIn& a = pin[u];
-            DF dv;
-            bool col = idx >= Ls, zero = false;
-            if (!col) {
-                // y1(k, j) on f1 slab j row k, -y1(k, j) on f2 slab k row j, with
-                // R1(k, j) = -(rowsum f1 slab j - rowsum f2 slab k)/sigma
-                const DF R1 = df_mul(df_sub(df_ld(a.x), df_ld(a.y)), is);
-                const DF fixed_row = f1 ? df_ld(sq[slab]) : df_ld(sq[L + slab - n]);    // mvA_j / mvS_k
-                const DF other = f1 ? df_ld(sq[L + idx]) : df_ld(sq[idx]);              // mvS_k / mvA_j
-                const DF y1 = df_mul(df_add(df_add(R1, fixed_row), other), imn);
-                dv = f1 ? y1 : df_neg(y1);
-            } else {
-                // y2(i, j) on f1 slab j, y3(k, l) on f2 slab k (y3(m, n) = 0)
-                const int e = idx - Ls;
-                zero = !f1 && slab == n + m - 1 && e == n - 1;
-                if (zero) {
-                    dv = DF{0.f, 0.f};
-                } else {
-                    const DF colc = f1 ? df_mul(df_ld(sq[2 * L + slab]), df_neg(df_ld(C.im)))
-                                       : df_mul(df_ld(sq[3 * L + slab - n]), df_ld(C.in));
-                    const DF isc = f1 ? df_ld(C.isim) : df_ld(C.isin);
-                    dv = df_add(df_sub(df_ld(a.x), df_mul(isc, a.y.x)), colc);
-                }
-            }
+            bool zero;
+            const DF dv = piece_dv(I, K, slab, idx, a, zero);
+            const bool col = idx >= Ls;
             const size_t o = 2 * g_row(I, slab) + idx;
             dab2[o] = df_st(dv);
-            const float df = df_f(dv);
-            const float dh = rintf(df * grid) * igrid;          // on the grid 2^-E
-            // w: the bin coordinate of the piece's row or column, for the sweep
-            ab32[o] = make_float4(a.a0.x + dh, a.a0.y + (df - dh), df, a.xc);
+            ab32[o] = piece_pack(a, dv, K);
             if (CHECK) {
                 const DF full = df_add(DF{a.a0.x, a.a0.y}, dv);
                 ymax = fmaxf(ymax, fabsf(full.hi));
@@ -899,8 +945,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_alpha32(const WorkDev* __restri
             block_sum_df<2>(red, s_red);
             const float bm = block_max(ymax, s_max);
             if (tid == 0) {
-                I.dobj_part[cl] = df_val(red[0]);
-                I.cD_part[cl] = df_val(red[1]);
+                reinterpret_cast<float2*>(I.dobj_part)[cl] = df_st(red[0]);
+                reinterpret_cast<float2*>(I.cD_part)[cl] = df_st(red[1]);
                 atomicMax(&I.ctl->ymax_bits, __float_as_uint(bm));
             }
         }
@@ -1255,7 +1301,7 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkD
         if (!have) load_cols(dc);
         const HotInst& I = W->inst[dc.inst];
         const int S = dc.S, NC = dc.NC, P = dc.P;
-        const int slab = dc.slab, band = dc.band, r0 = dc.r0, nr = dc.r1 - dc.r0;
+        const int r0 = dc.r0, nr = dc.r1 - dc.r0;
         const int ro = tid / NC, cg = tid - ro * NC;
         const bool active = ro < P;
         const int c0 = cg * NV;
@@ -1374,9 +1420,9 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkD
             kd[kNK - 1] = cd;
             block_sum_df<kNK>(kd, s_red);        // its barriers also publish s_rdf
             if (tid == 0) {
-                double* o = I.tile_kkt + (size_t)dc.tile * kNK;
+                float2* o = reinterpret_cast<float2*>(I.tile_kkt) + (size_t)dc.tile * kNK;
 #pragma unroll
-                for (int qq = 0; qq < kNK; ++qq) o[qq] = df_val(kd[qq]);
+                for (int qq = 0; qq < kNK; ++qq) o[qq] = df_st(kd[qq]);
             }
         } else {
             __syncthreads();
@@ -1441,31 +1487,56 @@ __device__ __forceinline__ void restart_tile(const HotInst& I, int slab, int ban
         fcol[e] = DF{0.f, 0.f};
     }
     if (active) {
+        // loop invariants of the tile, read once: the check iteration's
+        // constants, this thread's column pieces and column coordinates, and
+        // the arrays behind restrict-qualified locals (the stores below then
+        // force no reloads of the descriptor)
+        const P32 p32 = make_p32(sig_old, 0, I.h);
+        const P64 p64 = make_p64(sig_old, 0, I.h);
+        const float4* __restrict__ ab32 = F32 ? I.ab32 + 2 * g_row(I, slab) : nullptr;
+        const double* __restrict__ ab64 = F32 ? nullptr : I.ab64 + 2 * g_row(I, slab);
+        const double* __restrict__ dab64 = F32 ? nullptr : I.dab64 + 2 * g_row(I, slab);
+        const float* __restrict__ X32 = I.X32 + xb0;
+        const double* __restrict__ X64 = I.X64 + xb0;
+        float4 bq[NV];
+        T xc[NV], bb[NV], db[NV];
+#pragma unroll
+        for (int e = 0; e < NV; ++e) {
+            if constexpr (F32) {
+                bq[e] = ab32[S + c0 + e];
+                xc[e] = X32[c0 + e];
+            } else {
+                bb[e] = ab64[S + c0 + e];
+                db[e] = dab64[S + c0 + e];
+                xc[e] = X64[c0 + e];
+            }
+        }
+        const float fsig = (float)sig_new;
+        // two rows in flight per thread: the pass streams 16-24 B per variable
+        // and needs the loads of several rows outstanding to reach HBM speed
+#pragma unroll 2
         for (int r = r0 + ro; r < r1; r += P) {
             T uu[NV], dd[NV], xbv[NV], zbv[NV], rv[NV];
             V::ld(u + (size_t)r * S + c0, uu);
             V::ld(d1 + (size_t)r * S + c0, dd);
             if constexpr (F32) {
-                const P32 p = make_p32(sig_old, 0, I.h);
-                const float4* ab = I.ab32 + 2 * g_row(I, slab);
-                const float4 a = ab[r];
+                const float4 a = ab32[r];
+                const float xrow = X32[r];
 #pragma unroll
                 for (int e = 0; e < NV; ++e) {
-                    const float dc = I.X32[xb0 + r] - I.X32[xb0 + c0 + e];
-                    const E32 el = elem32(uu[e], dd[e], dc * dc, a, ab[S + c0 + e], p);
-                    xz32(el, p, xbv[e], zbv[e]);
+                    const float dc = xrow - xc[e];
+                    const E32 el = elem32(uu[e], dd[e], dc * dc, a, bq[e], p32);
+                    xz32(el, p32, xbv[e], zbv[e]);
                     rv[e] = el.r;
                 }
             } else {
-                const P64 p = make_p64(sig_old, 0, I.h);
-                const double* ab = I.ab64 + 2 * g_row(I, slab);
-                const double* dab = I.dab64 + 2 * g_row(I, slab);
-                const double a = ab[r], da = dab[r];
+                const double a = ab64[r], da = dab64[r];
+                const double xrow = X64[r];
 #pragma unroll
                 for (int e = 0; e < NV; ++e) {
-                    const double dc = I.X64[xb0 + r] - I.X64[xb0 + c0 + e];
-                    const E64 el = elem64(uu[e], dd[e], dc * dc, a, ab[S + c0 + e], da, dab[S + c0 + e], p);
-                    xz64(el, p, xbv[e], zbv[e]);
+                    const double dc = xrow - xc[e];
+                    const E64 el = elem64(uu[e], dd[e], dc * dc, a, bb[e], da, db[e], p64);
+                    xz64(el, p64, xbv[e], zbv[e]);
                     rv[e] = el.r;
                 }
             }
@@ -1494,16 +1565,17 @@ __device__ __forceinline__ void restart_tile(const HotInst& I, int slab, int ban
                 T nu_[NV], zero[NV];
                 DF rsf{0.f, 0.f};
                 double rsd = 0.0;
+                (void)rsd;
 #pragma unroll
                 for (int e = 0; e < NV; ++e) {
-                    if constexpr (F32) nu_[e] = fmaf((float)sig_new, rv[e], xbv[e]);
+                    if constexpr (F32) nu_[e] = fmaf(fsig, rv[e], xbv[e]);
                     else nu_[e] = xbv[e] + sig_new * rv[e];
                     zero[e] = T(0);
                     if constexpr (F32) {
                         rsf = df_add(rsf, (float)nu_[e]);
                         fcol[e] = df_add(fcol[e], (float)nu_[e]);
                         // <c, u>: (r-c)^2 u exactly as a pair (the integer cost is exact in FP32)
-                        const float dc = I.X32[xb0 + r] - I.X32[xb0 + c0 + e], cq = dc * dc;
+                        const float dc = X32[r] - xc[e], cq = dc * dc;
                         const float p = cq * (float)nu_[e];
                         fr[0] = df_add(fr[0], DF{p, fmaf(cq, (float)nu_[e], -p)});
                     } else {
@@ -1515,54 +1587,78 @@ __device__ __forceinline__ void restart_tile(const HotInst& I, int slab, int ban
                 V::st(xr + (size_t)r * S + c0, xbv);
                 V::st(zr + (size_t)r * S + c0, zbv);
                 V::st(d0 + (size_t)r * S + c0, zero);
-                s_row[(r - r0) * NC + cg] = F32 ? df_val(rsf) : rsd;
+                if constexpr (F32) reinterpret_cast<float2*>(s_row)[(r - r0) * NC + cg] = df_st(rsf);
+                else s_row[(r - r0) * NC + cg] = rsd;
             } else {
                 V::st(xr + (size_t)r * S + c0, xbv);
             }
         }
     }
-    if constexpr (F32) {
-        racc[0] = df_val(fr[0]);
-        racc[1] = df_val(fr[1]);
-#pragma unroll
-        for (int e = 0; e < NV; ++e) ccol[e] = df_val(fcol[e]);
-    }
+    // FP32 mode: the tile's sums as double-float pairs (GB300 runs FP64 at a
+    // small fraction of the FP32 rate); FP64 mode: FP64
     if constexpr (MODE == 0) {
-        block_sum<2>(racc, s_red);
-        if (threadIdx.x == 0) {
-            double* o = I.rst_part + (size_t)g_tile(I, slab, band) * 2;
-            o[0] = racc[0];
-            o[1] = racc[1];
+        if constexpr (F32) {
+            block_sum_df<2>(fr, reinterpret_cast<float2*>(s_red));
+            if (threadIdx.x == 0) {
+                float2* o = reinterpret_cast<float2*>(I.rst_part) + (size_t)g_tile(I, slab, band) * 2;
+                o[0] = df_st(fr[0]);
+                o[1] = df_st(fr[1]);
+            }
+        } else {
+            block_sum<2>(racc, s_red);
+            if (threadIdx.x == 0) {
+                double* o = I.rst_part + (size_t)g_tile(I, slab, band) * 2;
+                o[0] = racc[0];
+                o[1] = racc[1];
+            }
         }
     } else if constexpr (MODE == 1) {
         if constexpr (F32) {
-            double cu[1] = {racc[0]};                     // df_val(fr[0]): <c, u> of this thread's share
-            block_sum<1>(cu, s_red);
-            if (threadIdx.x == 0) I.cu_part[g_tile(I, slab, band)] = cu[0];
+            DF cu[1] = {fr[0]};                           // <c, u> of this thread's share
+            block_sum_df<1>(cu, reinterpret_cast<float2*>(s_red));
+            if (threadIdx.x == 0) reinterpret_cast<float2*>(I.cu_part)[g_tile(I, slab, band)] = df_st(cu[0]);
         }
         __syncthreads();
         if (active)
 #pragma unroll
-            for (int e = 0; e < NV; ++e) s_col[ro * S + c0 + e] = ccol[e];
+            for (int e = 0; e < NV; ++e) {
+                if constexpr (F32) reinterpret_cast<float2*>(s_col)[ro * S + c0 + e] = df_st(fcol[e]);
+                else s_col[ro * S + c0 + e] = ccol[e];
+            }
         __syncthreads();
         const size_t cbase = g_colp(I, slab, band);
         for (int c = threadIdx.x; c < S; c += blockDim.x) {
-            I.cs0_part[cbase + c] = sum_f64_strided(s_col + c, P, S);
+            if constexpr (F32) {
+                const float2* sc = reinterpret_cast<const float2*>(s_col) + c;
+                DF a{0.f, 0.f};
+                for (int q = 0; q < P; ++q) a = df_add(a, df_ld(sc[(size_t)q * S]));
+                I.cs0_part[cbase + c] = df_val(a);
+            } else {
+                I.cs0_part[cbase + c] = sum_f64_strided(s_col + c, P, S);
+            }
             I.cs_part[cbase + c] = 0.0;
             I.cs32[cbase + c] = 0.f;
         }
         // y0 <- y-bar: A^T y0 pieces of this tile's rows (and, for band 0, columns)
         const size_t o = 2 * g_row(I, slab);
+        const double ih = 1.0 / I.h;                         // a power of two: exact
         auto set_anchor = [&](int idx) {
             const double a0 = I.ab0[o + idx] + (F32 ? df_val(df_ld(I.dab2[o + idx])) : I.dab64[o + idx]);
             I.ab0[o + idx] = a0;
             if (I.ab0_32) {
-                const double hi = rint(a0 / I.h) * I.h;          // on the grid 2^-E
+                const double hi = rint(a0 * ih) * I.h;           // on the grid 2^-E
                 I.ab0_32[o + idx] = make_float2((float)hi, (float)(a0 - hi));
             }
         };
         for (int rr = threadIdx.x; rr < r1 - r0; rr += blockDim.x) {
-            I.rs0[g_row(I, slab) + r0 + rr] = sum_f64_strided(s_row + rr * NC, NC, 1);
+            if constexpr (F32) {
+                const float2* sr = reinterpret_cast<const float2*>(s_row) + (size_t)rr * NC;
+                DF a{0.f, 0.f};
+                for (int q = 0; q < NC; ++q) a = df_add(a, df_ld(sr[q]));
+                I.rs0[g_row(I, slab) + r0 + rr] = df_val(a);
+            } else {
+                I.rs0[g_row(I, slab) + r0 + rr] = sum_f64_strided(s_row + rr * NC, NC, 1);
+            }
             if (!F32) I.rs[g_row(I, slab) + r0 + rr] = 0.0;      // FP32: k_anchor resets rs2
             set_anchor(r0 + rr);
         }
@@ -1572,7 +1668,7 @@ __device__ __forceinline__ void restart_tile(const HotInst& I, int slab, int ban
 }
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(kThreads) k_restart(const WorkDev* __restrict__ W) {
+__global__ void __launch_bounds__(kThreads, 3) k_restart(const WorkDev* __restrict__ W) {
     __shared__ double s_row[MODE == 1 ? kRowSmemBytes / 8 * 2 : 1];
     __shared__ double s_col[MODE == 1 ? kThreads * 4 : 1];
     __shared__ double s_red[2 * 32];
@@ -1670,16 +1766,21 @@ __global__ void __launch_bounds__(kThreads) k_init(HotInst I, double sigma0) {
         for (int rr = threadIdx.x; rr < r1 - r0; rr += blockDim.x)
             I.rs0[g_row(I, slab) + r0 + rr] = sum_f64_strided(s_row + rr * NC, NC, 1);
         if constexpr (std::is_same<T, float>::value) {
-            double cu[1] = {df_val(cuf)};
-            block_sum<1>(cu, s_red);
-            if (threadIdx.x == 0) I.cu_part[g_tile(I, slab, band)] = cu[0];
+            DF cu[1] = {cuf};
+            block_sum_df<1>(cu, reinterpret_cast<float2*>(s_red));
+            if (threadIdx.x == 0) reinterpret_cast<float2*>(I.cu_part)[g_tile(I, slab, band)] = df_st(cu[0]);
         }
         __syncthreads();
     }
 }
 
 // --------------------------------------------------------------- k_kkt1 --
-// Partial sums of ||A x-bar - b||^2 from the x-bar slab sums.
+// Partial sums of ||A x-bar - b||^2 from the x-bar slab sums.  F32 (FP32 bulk
+// mode): the partials are double-float pairs, like every per-block partial of
+// that mode (tile KKT sums, <c, u>, <b, y>, the restart norms): GB300 runs FP64
+// at a small fraction of the FP32 rate, and FP64 block reductions dominated
+// these small kernels.  FP64 mode keeps FP64 throughout.
+template <bool F32>
 __global__ void __launch_bounds__(kThreads) k_kkt1(const WorkDev* __restrict__ W) {
     __shared__ double s_red[32];
     __shared__ int s_t[3];
@@ -1701,9 +1802,8 @@ __global__ void __launch_bounds__(kThreads) k_kkt1(const WorkDev* __restrict__ W
         const int m = I.m, n = I.n;
         const int MN = m * n;
         const int q = s_t[1] * kThreads + threadIdx.x;
-        double v[1] = {0.0};
+        double res = 0.0;
         if (q < 3 * MN - 1) {
-            double res;
             if (q < MN) {                                  // conservation rows (k, j)
                 const int j = q / m, k = q % m;
                 res = I.xrs[(size_t)j * m + k] - I.xrs[(size_t)MN + (size_t)k * n + j];
@@ -1718,16 +1818,41 @@ __global__ void __launch_bounds__(kThreads) k_kkt1(const WorkDev* __restrict__ W
                 kap += sum_bands(I.xcs_part + g_colp(I, n + k, 0) + l, (size_t)n, I.nb2);
                 res = kap - I.mu2[(size_t)k * n + l];
             }
-            v[0] = res * res;
         }
-        block_sum<1>(v, s_red);
-        if (threadIdx.x == 0) I.k1_part[s_t[1]] = v[0];
+        if constexpr (F32) {
+            const DF r = df_from(res);
+            DF v[1] = {df_mul(r, r)};
+            block_sum_df<1>(v, reinterpret_cast<float2*>(s_red));
+            if (threadIdx.x == 0) reinterpret_cast<float2*>(I.k1_part)[s_t[1]] = df_st(v[0]);
+        } else {
+            double v[1] = {res * res};
+            block_sum<1>(v, s_red);
+            if (threadIdx.x == 0) I.k1_part[s_t[1]] = v[0];
+        }
         __syncthreads();
     }
 }
 
+// Sum of count pairs p[0], p[stride], ... of this thread's share (q = threadIdx.x,
+// q + blockDim.x, ...), the loads issued four at a time.
+__device__ __forceinline__ DF sum_pairs(const float2* __restrict__ p, int count, int stride) {
+    DF acc{0.f, 0.f};
+    for (int q0 = threadIdx.x; q0 < count; q0 += 4 * blockDim.x) {
+        float2 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int q = q0 + u * blockDim.x;
+            v[u] = q < count ? p[(size_t)q * stride] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc = df_add(acc, df_ld(v[u]));
+    }
+    return acc;
+}
+
 // --------------------------------------------------------------- k_check --
 // Stopping rule eq. (kkt_res) and the restart rule, one CTA per instance.
+template <bool F32>
 __global__ void __launch_bounds__(kThreads) k_check(const WorkDev* __restrict__ W, int K, double a1, double a2,
                                                     double a3) {
     __shared__ double s_red[8 * 32];
@@ -1738,19 +1863,48 @@ __global__ void __launch_bounds__(kThreads) k_check(const WorkDev* __restrict__ 
         if (C->status != ST_RUNNING) continue;   // block-uniform
         const int ntile = g_ntiles(I), nslab = g_nslab(I);
         double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        for (int q = threadIdx.x; q < ntile; q += blockDim.x) {
-            for (int e = 0; e < kNK; ++e) v[e] += I.tile_kkt[(size_t)q * kNK + e];
-            if (!I.fp64) v[7] += I.cu_part[q];
+        if constexpr (F32) {
+            // pairs: the check sweep's per-tile sums, <c, u> per tile, the
+            // ||A x - b||^2 chunks and k_alpha32's <b, y> and <c, A^T(y-bar - y0)>
+            // per chunk
+            // (every load of a round is issued before the adds: the sums cost
+            // a few round trips, not one per array)
+            const float2* tk = reinterpret_cast<const float2*>(I.tile_kkt);
+            const float2* cu = reinterpret_cast<const float2*>(I.cu_part);
+            DF w[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) w[e] = DF{0.f, 0.f};
+            for (int q0 = threadIdx.x; q0 < ntile; q0 += 4 * blockDim.x) {
+                float2 t[4][kNK + 1];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int q = q0 + u * blockDim.x;
+#pragma unroll
+                    for (int e = 0; e < kNK; ++e) t[u][e] = q < ntile ? tk[(size_t)q * kNK + e] : make_float2(0.f, 0.f);
+                    t[u][kNK] = q < ntile ? cu[q] : make_float2(0.f, 0.f);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+#pragma unroll
+                    for (int e = 0; e < kNK; ++e) w[e] = df_add(w[e], df_ld(t[u][e]));
+                    w[7] = df_add(w[7], df_ld(t[u][kNK]));
+                }
+            }
+            w[5] = sum_pairs(reinterpret_cast<const float2*>(I.k1_part), I.n_k1, 1);
+            w[6] = sum_pairs(reinterpret_cast<const float2*>(I.dobj_part), I.n_achunk, 1);
+            const DF cD = sum_pairs(reinterpret_cast<const float2*>(I.cD_part), I.n_achunk, 1);
+            w[4] = df_add(w[4], df_mul(cD, df_from(C->sigma)));
+            block_sum_df<8>(w, reinterpret_cast<float2*>(s_red));
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] = df_val(w[e]);
+        } else {
+            for (int q = threadIdx.x; q < ntile; q += blockDim.x)
+                for (int e = 0; e < kNK; ++e) v[e] += I.tile_kkt[(size_t)q * kNK + e];
+            for (int q = threadIdx.x; q < I.n_k1; q += blockDim.x) v[5] += I.k1_part[q];
+            // partial sums of <b, y>: one per slab
+            for (int q = threadIdx.x; q < nslab; q += blockDim.x) v[6] += I.dobj_part[q];
+            block_sum<8>(v, s_red);
         }
-        for (int q = threadIdx.x; q < I.n_k1; q += blockDim.x) v[5] += I.k1_part[q];
-        // partial sums of <b, y> (and FP32 mode: <c, A^T(y-bar - y0)>): one per
-        // slab in FP64 mode, one per k_alpha32 chunk in FP32 mode
-        const int npart = I.fp64 ? nslab : I.n_achunk;
-        for (int q = threadIdx.x; q < npart; q += blockDim.x) {
-            v[6] += I.dobj_part[q];
-            if (!I.fp64) v[4] += C->sigma * I.cD_part[q];
-        }
-        block_sum<8>(v, s_red);
         if (threadIdx.x == 0) {
             // FP32 mode: <c, x-bar> = <c, u> + <c, d> + sigma <c, A^T(y-bar - y0)>
             // from exact per-tile and per-slab parts (the per-element x-bar is
@@ -1806,6 +1960,7 @@ __global__ void __launch_bounds__(kThreads) k_check(const WorkDev* __restrict__ 
 }
 
 // Sigma update at a restart: sigma <- sqrt(sigma ||x-bar - x_r|| / ||z-bar - z_r||) on the grid 2^(j/16).
+template <bool F32>
 __global__ void __launch_bounds__(kThreads) k_restart_sigma(const WorkDev* __restrict__ W) {
     __shared__ double s_red[2 * 32];
     const int ninst = W->ninst;
@@ -1815,11 +1970,19 @@ __global__ void __launch_bounds__(kThreads) k_restart_sigma(const WorkDev* __res
         if (C->status != ST_RUNNING || !C->restart_pending) continue;
         const int ntile = g_ntiles(I);
         double v[2] = {0.0, 0.0};
-        for (int q = threadIdx.x; q < ntile; q += blockDim.x) {
-            v[0] += I.rst_part[(size_t)q * 2];
-            v[1] += I.rst_part[(size_t)q * 2 + 1];
+        if constexpr (F32) {
+            const float2* rp = reinterpret_cast<const float2*>(I.rst_part);
+            DF w[2] = {sum_pairs(rp, ntile, 2), sum_pairs(rp + 1, ntile, 2)};
+            block_sum_df<2>(w, reinterpret_cast<float2*>(s_red));
+            v[0] = df_val(w[0]);
+            v[1] = df_val(w[1]);
+        } else {
+            for (int q = threadIdx.x; q < ntile; q += blockDim.x) {
+                v[0] += I.rst_part[(size_t)q * 2];
+                v[1] += I.rst_part[(size_t)q * 2 + 1];
+            }
+            block_sum<2>(v, s_red);
         }
-        block_sum<2>(v, s_red);
         if (threadIdx.x == 0) {
             const double dx = sqrt(v[0]), dz = sqrt(v[1]);
             const double old = C->sigma;
@@ -1878,7 +2041,7 @@ LaunchDims make_launch_dims(int device, int fp64) {
         d.grid_alpha = occ_grid(k_alpha32<true>, sms, 0, 2);
         d.grid_vec = occ_grid(k_vec32, sms, 0, 4);
     }
-    d.grid_k1 = sms * 2;
+    d.grid_k1 = occ_grid(k_kkt1<true>, sms, 0, 6);
     d.grid_inst = sms * 2;
     return d;
 }
@@ -1930,7 +2093,7 @@ void launch_solve_kernels(const WorkDev* w, const LaunchDims& ld, int fp64, int 
         launch(ld, k_marg, ld.grid_inst, 7 * kMaxS * 8, st, w);
         launch(ld, check ? k_alpha<true> : k_alpha<false>, ld.grid_slab, 0, st, w);
     } else {
-        launch(ld, k_vec32, ld.grid_vec, 0, st, w);
+        launch(ld, k_vec32, ld.grid_vec, 0, st, w, j);
         launch(ld, check ? k_alpha32<true> : k_alpha32<false>, ld.grid_alpha, 0, st, w, j);
     }
 }
@@ -1946,17 +2109,19 @@ void launch_sweep(const WorkDev* w, const LaunchDims& ld, int fp64, int j, bool 
 
 void launch_block_end(const WorkDev* w, const LaunchDims& ld, int fp64, int K, double a1, double a2, double a3,
                       cudaStream_t st) {
-    launch(ld, k_kkt1, ld.grid_k1, 0, st, w);
-    launch(ld, k_check, ld.grid_inst, 0, st, w, K, a1, a2, a3);
     if (fp64) {
+        launch(ld, k_kkt1<false>, ld.grid_k1, 0, st, w);
+        launch(ld, k_check<false>, ld.grid_inst, 0, st, w, K, a1, a2, a3);
         launch(ld, k_restart<double, 0>, ld.grid_rst, 0, st, w);
-        launch(ld, k_restart_sigma, ld.grid_inst, 0, st, w);
+        launch(ld, k_restart_sigma<false>, ld.grid_inst, 0, st, w);
         launch(ld, k_restart<double, 1>, ld.grid_rst, 0, st, w);
         launch(ld, k_anchor, ld.grid_slab, 0, st, w);
         launch(ld, k_restart<double, 2>, ld.grid_rst, 0, st, w);
     } else {
+        launch(ld, k_kkt1<true>, ld.grid_k1, 0, st, w);
+        launch(ld, k_check<true>, ld.grid_inst, 0, st, w, K, a1, a2, a3);
         launch(ld, k_restart<float, 0>, ld.grid_rst, 0, st, w);
-        launch(ld, k_restart_sigma, ld.grid_inst, 0, st, w);
+        launch(ld, k_restart_sigma<true>, ld.grid_inst, 0, st, w);
         launch(ld, k_restart<float, 1>, ld.grid_rst, 0, st, w);
         launch(ld, k_anchor, ld.grid_slab, 0, st, w);
         launch(ld, k_restart<float, 2>, ld.grid_rst, 0, st, w);
