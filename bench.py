@@ -17,9 +17,10 @@ inside the timed region.  With --gpus N (torchrun) each rank solves its own
 pair (replicas; weak scaling) and the time is the max over ranks.
 
 `--impl reference` times the FP64 CPU oracle (oracle/, test infrastructure)
-on the same pair: each step is a bounded sample (model build plus a few
-iterations of Algorithm 2), extrapolated to a full solve with the iteration
-count a solve of that pair takes.
+on the same pair: each step is a bounded sample of 10 iterations of Algorithm 2
+with the KKT check (the model is built once, timed apart), and solves/s scales the measured time
+per iteration to the iteration count the oracle itself needs on that pair
+(440 at 256 x 256, from its stored full run in tests/golden/oracle_values.json).
 """
 import argparse
 import json
@@ -39,13 +40,23 @@ sys.path.insert(0, ROOT)
 SWEEP_TRAFFIC = {"kernels_sha256": "38e2a9a6699e44bae4f9410457a19c5e9401a3a5340db257fd0e57ad323a1370",
                  "bytes_per_launch": 273729024 + 104790528}
 
-# iterations of Algorithm 2 (with the restart rule) that the FP64 oracle takes
-# to rel-KKT tol on the default bench pair (synthetic.make_pair("white", 256,
-# 1000)): oracle.hot.hot_solve(mu1, mu2, tol=1e-6) -> 440 iterations, 12
-# restarts, rel-KKT 9.7194e-7, 1028 s on one x86 core (sigma rounded to the
-# grid 2^(j/16) at restarts).  Used to extrapolate the oracle's per-iteration
-# time to a full solve.
-ITERS_PER_SOLVE = {(256, "white", 1e-6): 440}
+GOLDEN = os.path.join(ROOT, "tests", "golden", "oracle_values.json")
+
+
+def oracle_iterations(S, kind, seed, tol):
+    """Iterations the FP64 oracle takes on this pair to tol, from its stored
+    full run (tests/golden/oracle_values.json, written by the oracle alone), or
+    None when no run of this pair is stored."""
+    try:
+        with open(GOLDEN) as f:
+            cases = json.load(f)["cases"]
+    except Exception:
+        return None
+    for rec in cases.values():
+        if (rec["S"], rec["kind"], rec["seed"], rec["tol"]) == (S, kind, seed, tol) and \
+                rec.get("stop", "relative") == "relative":
+            return int(rec["iters"])
+    return None
 
 
 def parse():
@@ -61,6 +72,9 @@ def parse():
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32",
                     help="solve mode: FP32 bulk (the default) or the plain FP64 form")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--acc-tol", type=float, default=5e-10,
+                    help="solve mode: tolerance of the plan-accuracy leg (the plan's marginals to 1e-6 in L1)")
+    ap.add_argument("--no-accuracy-leg", action="store_true")
     ap.add_argument("--batch", type=int, default=512)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--duration", type=float, default=60.0)
@@ -172,34 +186,63 @@ def measured_peak():
 
 # ----------------------------------------------------------------- oracle --
 
-def oracle_sample(mu1, mu2, iters_per_solve, n_iter=3):
-    """Time the FP64 oracle on a bounded sample: model build + n_iter steps of
-    Algorithm 2.  Returns (seconds per solve extrapolated, sample description)."""
-    import numpy as np
-    from oracle import hot as ohot
-    from oracle import reduced_model as rm
-    S = mu1.shape[0]
-    t0 = time.perf_counter()
-    A = rm.build_A(S, S)
-    b = rm.build_b(mu1, mu2)
-    c = rm.build_c(S, S)
-    c = c / ohot.cost_scale(c)
-    t_build = time.perf_counter() - t0
-    x = np.zeros(c.size)
-    z = np.zeros(c.size)
-    sigma = float(np.linalg.norm(b) / np.linalg.norm(c))
-    t1 = time.perf_counter()
-    for _ in range(n_iter):
-        y, x, z = ohot.hot_step(A, b, c, sigma, x, z, S, S)
-    t_iter = (time.perf_counter() - t1) / n_iter
-    per_solve = t_build + iters_per_solve * t_iter
-    desc = ("oracle (numpy/scipy, FP64) at S=%d: model build %.2fs + %d Algorithm-2 steps at %.3fs each, "
-            "extrapolated to %d iterations per solve" % (S, t_build, n_iter, t_iter, iters_per_solve))
-    return per_solve, desc
+class OracleSample:
+    """The FP64 oracle on a bounded sample of a solve: the model is built once
+    (timed), then batches of Algorithm-2 iterations are timed one by one."""
+
+    def __init__(self, mu1, mu2):
+        import numpy as np
+        from oracle import hot as ohot
+        from oracle import reduced_model as rm
+        self.np, self.ohot = np, ohot
+        self.S = mu1.shape[0]
+        t0 = time.perf_counter()
+        self.A = rm.build_A(self.S, self.S)
+        self.b = rm.build_b(mu1, mu2)
+        c = rm.build_c(self.S, self.S)
+        self.c = c / ohot.cost_scale(c)
+        self.t_build = time.perf_counter() - t0
+        self.x = np.zeros(self.c.size)
+        self.z = np.zeros(self.c.size)
+        self.sigma = float(np.linalg.norm(self.b) / np.linalg.norm(self.c))
+
+    def run(self, n_iter):
+        """Seconds for n_iter iterations of the oracle's loop: Steps 1-3
+        (oracle.hot.hot_step), the Halpern update of Step 4, and the KKT
+        residual eq. (kkt_res) every 10th iteration, as oracle.hot.hot_solve
+        runs them (a restart never falls in so short a sample)."""
+        t1 = time.perf_counter()
+        for k in range(n_iter):
+            yb, xb, zb = self.ohot.hot_step(self.A, self.b, self.c, self.sigma, self.x, self.z, self.S, self.S)
+            if (k + 1) % 10 == 0:
+                self.ohot.kkt_residual(self.A, self.b, self.c, xb, yb, zb)
+                self.ohot.kkt_absolute(self.A, self.b, self.c, xb, yb, zb)
+            self.x = (k + 1) / (k + 2) * (2.0 * xb - self.x)
+            self.z = (k + 1) / (k + 2) * (2.0 * zb - self.z)
+        return time.perf_counter() - t1
 
 
 def cpu_threads():
     return 1   # scipy sparse mat-vecs and the numpy element-wise ops run on one thread
+
+
+def oracle_baseline(mu1, mu2, kind, seed, tol, gpu_iters, n_iter=50):
+    """cpu_baseline: n_iter oracle iterations measured in one run; solves/s
+    scales the measured time per iteration to the oracle's own iteration count
+    for this pair (stored full run), else to the GPU solve's (the same when
+    their restart decisions agree)."""
+    smp = OracleSample(mu1, mu2)
+    t = smp.run(n_iter)
+    t_iter = t / n_iter
+    iters = oracle_iterations(smp.S, kind, seed, tol)
+    src = "the oracle's stored full run of this pair"
+    if iters is None:
+        iters, src = gpu_iters, "the GPU solve of this pair"
+    per_solve = smp.t_build + iters * t_iter
+    desc = ("oracle (numpy/scipy, FP64) at S=%d: %d Algorithm-2 iterations measured in %.1f s (%.3f s each) + "
+            "model build %.1f s; solves/s = 1 / (build + %d iterations, the count of %s)"
+            % (smp.S, n_iter, t, t_iter, smp.t_build, iters, src))
+    return 1.0 / per_solve, desc
 
 
 # ------------------------------------------------------------------ modes --
@@ -317,6 +360,26 @@ def bench_solve(args, dist):
                     "prop3_solve": round(1000 * kt["solve_ms"] / max(1, kt["sweep_launches"] + kt["sweep_check_launches"]), 2),
                     "block_end_per_block": round(1000 * kt["block_end_ms"] / max(1, kt["sweep_check_launches"]), 2)}}
 
+    # the plan-accuracy leg: the same pair solved until Algorithm 1's plan
+    # matches mu and nu to 1e-6 in L1 (relative KKT about 5e-10 at 256 x 256,
+    # against the paper's 1e-6: its marginals are then off by about 1.6e-2)
+    accuracy = None
+    if not args.no_accuracy_leg and args.precision == "fp32" and dist.world == 1:
+        torch.cuda.synchronize()
+        ta0 = time.perf_counter()
+        ra = ctx.solve(d1, d2, tol=args.acc_tol, max_iter=5000000)
+        na, l1a = ctx.recover_plan(ra, device_out=(src, dst, mass))
+        ctx.release(ra)
+        torch.cuda.synchronize()
+        ta = time.perf_counter() - ta0
+        accuracy = {"tol": args.acc_tol, "solves_per_s": round(1.0 / ta, 4), "seconds": round(ta, 3),
+                    "iterations": ra["iters"], "restarts": ra["restarts"], "rel_kkt": ra["rel_kkt"],
+                    "plan_nnz": na, "plan_marginal_l1": l1a, "converged": ra["status"] == 0,
+                    "ot_value": ra["ot_value"], "dual_value": ra["dual_value"],
+                    "timing": "one solve + Algorithm 1, host clock around device-resident inputs"}
+
+    solve_s = r["solve_ms"] / 1000.0                    # device time of the last timed solve alone
+    per_iter_bytes = (12.0 if args.precision == "fp32" else 24.0) * 2 * S ** 3
     out = {"metric": "solves/s (ms-to-1e-6 KKT) at N=%d" % S, "value": round(value, 4), "unit": "solves/s",
            "n_gpus": dist.world, "steps": args.steps, "warmup": max(3, args.warmup),
            "ms_per_step": round(1000.0 * t / args.steps, 3), "higher_is_better": True, "scaling": "weak",
@@ -330,47 +393,59 @@ def bench_solve(args, dist):
                       "parallelism": "replicas" if dist.world > 1 else "single"},
            "iterations_per_solve": iters, "restarts": r["restarts"],
            "ms_per_iteration": round(1000.0 * t / args.steps / iters, 4),
-           "hbm_gbs_per_iteration": round((12.0 if args.precision == "fp32" else 24.0) * 2 * S ** 3
-                                          / (t / args.steps / iters) / 1e9, 1),
+           "hbm_gbs_per_iteration": round(per_iter_bytes / (t / args.steps / iters) / 1e9, 1),
+           "hbm_frac_per_iteration": round(per_iter_bytes / (t / args.steps / iters) / 1e9 / peak, 4),
+           "hbm_per_iteration_note": ("algorithmic state bytes (12 B per flow variable in FP32 bulk, 24 B in "
+                                      "FP64) x iterations / ms_per_step; the step includes plan recovery"),
+           "hbm_gbs_per_iteration_solve_only": round(per_iter_bytes * iters / solve_s / 1e9, 1),
+           "hbm_frac_per_iteration_solve_only": round(per_iter_bytes * iters / solve_s / 1e9 / peak, 4),
            "plan_nnz": rec["n"], "plan_marginal_l1": rec["l1"], "rel_kkt": r["rel_kkt"],
            "roofline": roofline, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
            "clocks": clocks}
+    if accuracy is not None:
+        out["plan_accuracy"] = accuracy
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
-        per_solve, desc = oracle_sample(mu1, mu2, ITERS_PER_SOLVE.get((S, args.kind, args.tol), iters))
-        out["cpu_baseline"] = {"value": round(1.0 / per_solve, 8), "unit": "solves/s", "cores": cpu_threads(),
-                               "kind": "oracle", "sample": desc}
+        v, desc = oracle_baseline(mu1, mu2, args.kind, 1000, args.tol, iters)
+        out["cpu_baseline"] = {"value": round(v, 8), "unit": "solves/s", "cores": cpu_threads(),
+                               "host_cpus": os.cpu_count(), "kind": "oracle", "sample": desc}
     ctx.close()
     return out
 
 
 def bench_reference(args, dist):
-    """The FP64 CPU oracle on the same workload (rank 0 only)."""
+    """The FP64 CPU oracle on the same workload (rank 0 only): every step
+    times 10 iterations of Algorithm 2 with their KKT check on the pair (the model is built once,
+    before the steps); solves/s scales the median time per iteration to the
+    oracle's own iteration count for the pair."""
     from paper_2408_00598_gb300 import synthetic as syn
     if dist.rank != 0:
         return None
     S = args.size
     mu1, mu2 = syn.make_pair(args.kind, S, 1000)
-    # iterations the oracle takes to converge on this pair (one full oracle
-    # solve at S = 256 takes about 20 minutes, so the count is a documented
-    # constant measured with the oracle itself)
-    iters = ITERS_PER_SOLVE.get((S, args.kind, args.tol), 1100)
-    times = []
-    desc = ""
+    iters = oracle_iterations(S, args.kind, 1000, args.tol)
+    src = "the oracle's stored full run of this pair"
+    if iters is None:
+        iters, src = 1100, "a stated count (no stored run of this pair)"
+    smp = OracleSample(mu1, mu2)
+    n_iter = 10
     for _ in range(args.warmup):
-        pass   # the oracle has no warm-up effects worth paying minutes for
-    for _ in range(max(1, min(args.steps, 3))):
-        per_solve, desc = oracle_sample(mu1, mu2, iters, n_iter=2)
-        times.append(per_solve)
-    per = statistics.median(times)
+        smp.run(1)
+    steps = [smp.run(n_iter) for _ in range(max(1, args.steps))]
+    t_iter = statistics.median(steps) / n_iter
+    per = smp.t_build + iters * t_iter
     v = 1.0 / per
+    desc = ("oracle (numpy/scipy, FP64) at S=%d: %d steps of %d Algorithm-2 iterations, median %.3f s per "
+            "iteration, + model build %.1f s; solves/s = 1 / (build + %d iterations, the count of %s)"
+            % (S, len(steps), n_iter, t_iter, smp.t_build, iters, src))
     return {"impl": "reference", "metric": "solves/s (ms-to-1e-6 KKT) at N=%d" % S, "value": round(v, 8),
-            "unit": "solves/s", "n_gpus": dist.world, "steps": len(times), "warmup": args.warmup,
-            "ms_per_step": round(per * 1000.0, 1), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "single %dx%d pair (%s), Algorithm 2 to rel-KKT %g (FP64 CPU oracle)"
-                                   % (S, S, args.kind, args.tol), "S": S},
-            "cpu_baseline": {"value": round(v, 8), "unit": "solves/s", "cores": cpu_threads(), "kind": "oracle",
-                             "sample": desc},
+            "unit": "solves/s", "n_gpus": dist.world, "steps": len(steps), "warmup": args.warmup,
+            "ms_per_step": round(1000.0 * statistics.median(steps), 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "single %dx%d pair (%s, seed 1000), Algorithm 2 to rel-KKT %g (FP64 CPU oracle)"
+                                   % (S, S, args.kind, args.tol), "S": S,
+                       "step": "%d oracle iterations (a bounded sample of one solve)" % n_iter},
+            "cpu_baseline": {"value": round(v, 8), "unit": "solves/s", "cores": cpu_threads(),
+                             "host_cpus": os.cpu_count(), "kind": "oracle", "sample": desc},
             "e2e": {"value": round(v, 8), "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -397,7 +472,25 @@ def bench_batch(args, dist):
     t = dist.max(time.perf_counter() - t0)
     iters = sum(o["iters"] for o in out)
     vol = sum(2 * b[1] ** 3 for b in batch)
-    extra = {}
+    # algorithmic state traffic: 12 B per flow variable per iteration (FP32 bulk)
+    traffic = sum(12.0 * 2 * b[1] ** 3 * o["iters"] for b, o in zip(batch, out))
+    peak, peak_kind = measured_peak()
+    fin = sorted(o["solve_ms"] for o in out)              # each pair's completion, from the batch's start
+    its = sorted(o["iters"] for o in out)
+
+    def pct(v, q):
+        return v[min(len(v) - 1, int(round(q * (len(v) - 1))))]
+
+    extra = {"hbm_gbs": round(traffic / t / 1e9, 1), "hbm_frac": round(traffic / t / 1e9 / peak, 4),
+             "hbm_note": ("algorithmic state bytes (12 B per flow variable per iteration of each pair) / batch "
+                          "time; peak %s (%s)" % (peak, peak_kind)),
+             "converged_at_s": {"50%": round(pct(fin, 0.5) / 1e3, 3), "90%": round(pct(fin, 0.9) / 1e3, 3),
+                                "99%": round(pct(fin, 0.99) / 1e3, 3), "100%": round(fin[-1] / 1e3, 3)},
+             "iterations_per_pair": {"min": its[0], "p50": pct(its, 0.5), "p90": pct(its, 0.9),
+                                     "p99": pct(its, 0.99), "max": its[-1], "mean": round(iters / len(its), 1)},
+             "iterations_by_size": {str(S): round(statistics.mean(o["iters"] for b, o in zip(batch, out)
+                                                                   if b[1] == S), 1)
+                                    for S in sorted(set(b[1] for b in batch))}}
     if args.compare_fp64:
         # the plain FP64 single-instance form on the same pairs, one solve at a time
         ctx64 = hot.Context(device=dist.local_rank, precision="fp64", stream=stream.cuda_stream)
@@ -412,10 +505,10 @@ def bench_batch(args, dist):
         ctx64.close()
         rel = [abs(a["dual_value"] - b["dual_value"]) / abs(b["dual_value"]) for a, b in zip(out, r64)]
         relp = [abs(a["ot_value"] - b["ot_value"]) / abs(b["ot_value"]) for a, b in zip(out, r64)]
-        extra = {"fp64_sequential": {"solves_per_s": round(args.batch / t64, 2), "seconds": round(t64, 2),
-                                     "converged": sum(1 for r in r64 if r["status"] == 0)},
-                 "fp32_batch_vs_fp64": {"max_rel_dual": max(rel), "median_rel_dual": statistics.median(rel),
-                                        "max_rel_ot": max(relp), "median_rel_ot": statistics.median(relp)}}
+        extra.update({"fp64_sequential": {"solves_per_s": round(args.batch / t64, 2), "seconds": round(t64, 2),
+                                          "converged": sum(1 for r in r64 if r["status"] == 0)},
+                      "fp32_batch_vs_fp64": {"max_rel_dual": max(rel), "median_rel_dual": statistics.median(rel),
+                                             "max_rel_ot": max(relp), "median_rel_ot": statistics.median(relp)}})
     return {"metric": "batched solves/s (512 pairs, S in {32..128})", "value": round(dist.world * args.batch *
                                                                                      args.steps / t, 2),
             "unit": "solves/s", "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup,

@@ -115,7 +115,9 @@ typedef struct hot_result {
     double rel_primal;    /* ||A x - b|| / (1 + ||b||)                                         */
     double sigma;         /* sigma at termination                                              */
     double cost_scale;    /* power-of-two scale the cost was divided by                        */
-    double solve_ms;      /* wall time on the device from admission to completion             */
+    double solve_ms;      /* hot_solve: device time of the solve; hot_solve_batch: time from
+                             the batch's start until this pair's last check was seen complete;
+                             serve loop: time from admission to completion                     */
     double queue_ms;      /* serve loop: wait between hot_submit and admission                 */
     long long iters;      /* iterations of Algorithm 2 performed                               */
     int    restarts;

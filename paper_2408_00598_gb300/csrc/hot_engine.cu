@@ -427,12 +427,10 @@ Batch::~Batch() {
     cudaFreeHost(h_pre);
     cudaFreeHost(h_running);
     cudaFreeHost(h_st);
+    cudaFreeHost(h_stb);
 }
 
-int Batch::reserve(int n) {
-    if (n <= cap && d_work) return HOT_OK;
-    int ncap = std::max(n, std::max(16, cap * 2));
-    // the graphs captured the old table pointers
+void Batch::drop_graphs() {
     if (graph) {
         cudaGraphExecDestroy(graph);
         graph = nullptr;
@@ -442,6 +440,13 @@ int Batch::reserve(int n) {
             cudaGraphExecDestroy(tgraph[p]);
             tgraph[p] = nullptr;
         }
+    single = -1;
+}
+
+int Batch::reserve(int n) {
+    if (n <= cap && d_work) return HOT_OK;
+    int ncap = std::max(n, std::max(16, cap * 2));
+    drop_graphs();   // the graphs captured the old table pointers
     cudaFree(d_work);
     cudaFree(d_inst);
     cudaFree(d_pre);
@@ -452,6 +457,8 @@ int Batch::reserve(int n) {
     cudaFreeHost(h_pre);
     cudaFreeHost(h_running);
     cudaFreeHost(h_st);
+    cudaFreeHost(h_stb);
+    h_stb = nullptr;
     d_work = nullptr;
     HOT_CK(cudaMalloc(&d_work, sizeof(WorkDev)));
     HOT_CK(cudaMalloc(&d_inst, sizeof(HotInst) * ncap));
@@ -459,6 +466,7 @@ int Batch::reserve(int n) {
     HOT_CK(cudaMalloc(&d_running, sizeof(int)));
     HOT_CK(cudaMalloc(&d_st, sizeof(int) * ncap));
     HOT_CK(cudaMallocHost(&h_st, sizeof(int) * ncap));
+    HOT_CK(cudaMallocHost(&h_stb, sizeof(int) * 2 * ncap));
     HOT_CK(cudaMallocHost(&h_work, sizeof(WorkDev)));
     HOT_CK(cudaMallocHost(&h_inst, sizeof(HotInst) * ncap));
     HOT_CK(cudaMallocHost(&h_pre, sizeof(int) * kPreTables * (ncap + 1)));
@@ -470,6 +478,9 @@ int Batch::reserve(int n) {
 int Batch::set_instances(const std::vector<Inst*>& v, cudaStream_t st) {
     int rc = reserve((int)v.size());
     if (rc != HOT_OK) return rc;
+    // a single instance and a batch of several run different Prop. 3 kernels
+    // (launch_solve_kernels): a change between the two needs new graphs
+    if (single >= 0 && single != (v.size() == 1 ? 1 : 0)) drop_graphs();
     // the pinned staging is rewritten here: wait for earlier copies out of it
     HOT_CK(cudaStreamSynchronize(st));
     const int n = (int)v.size();
@@ -515,7 +526,7 @@ int Batch::set_instances(const std::vector<Inst*>& v, cudaStream_t st) {
 int Batch::capture(cudaGraphExec_t* out, cudaEvent_t* ev) {
     HOT_CK(cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal));
     for (int j = 0; j < K; ++j) {
-        launch_solve_kernels(d_work, ld, fp64, j, j == K - 1, cap_stream);
+        launch_solve_kernels(d_work, ld, fp64, j, j == K - 1, ninst == 1, cap_stream);
         const bool t = ev && j == timed_iter() && j < K - 1;
         if (t) cudaEventRecordWithFlags(ev[0], cap_stream, cudaEventRecordExternal);
         launch_sweep(d_work, ld, fp64, j, j == K - 1, cap_stream);
@@ -543,6 +554,7 @@ int Batch::ensure_graph(int want_timing) {
     if (timing ? (tgraph[0] && tgraph[1]) : graph != nullptr) return HOT_OK;
     if (!cap_stream) HOT_CK(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
     ld = make_launch_dims(device, fp64);
+    single = ninst == 1 ? 1 : 0;
     if (!timing) return capture(&graph, nullptr);
     for (int p = 0; p < 2; ++p) {
         for (int q = 0; q < 2; ++q)
@@ -646,6 +658,12 @@ int run_solve(Ctx* ctx, const std::vector<PairHost>& pairs, double tol, long lon
         pev.resize(3 * K + 2);
         for (auto& e : pev) cudaEventCreate(&e);
     }
+    // batches: the host time at which the block holding each instance's last
+    // check was seen complete (its status copied back after every block)
+    const bool track = insts.size() > 1 && !kt;
+    const int ni = (int)insts.size();
+    std::vector<double> fin_ms(insts.size(), -1.0);
+    const auto th0 = std::chrono::steady_clock::now();
     cudaEventRecord(t0, st);
     for (;;) {
         if (!kt) {
@@ -654,9 +672,18 @@ int run_solve(Ctx* ctx, const std::vector<PairHost>& pairs, double tol, long lon
                 break;
             }
             cudaMemcpyAsync(&B.h_running[1 + (nb & 1)], B.d_running, sizeof(int), cudaMemcpyDeviceToHost, st);
+            if (track)
+                cudaMemcpyAsync(B.h_stb + (size_t)(nb & 1) * B.cap, B.d_st, sizeof(int) * ni, cudaMemcpyDeviceToHost, st);
             cudaEventRecord(ev[nb & 1], st);
             if (nb >= 1) {
                 cudaEventSynchronize(ev[(nb - 1) & 1]);
+                if (track) {
+                    const double now =
+                        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - th0).count();
+                    const int* sts = B.h_stb + (size_t)((nb - 1) & 1) * B.cap;
+                    for (int q = 0; q < ni; ++q)
+                        if (fin_ms[q] < 0.0 && sts[q] != ST_RUNNING) fin_ms[q] = now;
+                }
                 if (timing) {
                     // block nb - 1 has finished; block nb runs on the other graph instance
                     float tms = 0.f;
@@ -678,7 +705,7 @@ int run_solve(Ctx* ctx, const std::vector<PairHost>& pairs, double tol, long lon
         } else {
             for (int j = 0; j < K; ++j) {
                 cudaEventRecord(pev[3 * j], st);
-                launch_solve_kernels(B.d_work, B.ld, fp64, j, j == K - 1, st);
+                launch_solve_kernels(B.d_work, B.ld, fp64, j, j == K - 1, insts.size() == 1, st);
                 cudaEventRecord(pev[3 * j + 1], st);
                 launch_sweep(B.d_work, B.ld, fp64, j, j == K - 1, st);
                 cudaEventRecord(pev[3 * j + 2], st);
@@ -695,7 +722,7 @@ int run_solve(Ctx* ctx, const std::vector<PairHost>& pairs, double tol, long lon
                 cudaEventElapsedTime(&a, pev[3 * j], pev[3 * j + 1]);
                 cudaEventElapsedTime(&b, pev[3 * j + 1], pev[3 * j + 2]);
                 kt->solve_ms += a;
-                kt->solve_launches += launches_per_iteration(fp64, j == K - 1) - 1;
+                kt->solve_launches += launches_per_iteration(fp64, insts.size() == 1) - 1;
                 if (j == K - 1) {
                     kt->sweep_check_ms += b;
                     kt->sweep_check_launches += 1;
@@ -735,12 +762,14 @@ int run_solve(Ctx* ctx, const std::vector<PairHost>& pairs, double tol, long lon
         cleanup();
         return HOT_ECUDA;
     }
-    const long long launches = nb * (launches_per_block(fp64, (int)K) + kLaunchesBlockEnd);
+    const long long launches = nb * (launches_per_block(fp64, (int)K, insts.size() == 1) + kLaunchesBlockEnd);
     for (size_t q = 0; q < insts.size(); ++q) {
         Inst* I = insts[q];
         cudaMemcpy(&I->ctl_host, I->desc.ctl, sizeof(HotCtl), cudaMemcpyDeviceToHost);
         fill_result(I, &out[q]);
-        out[q].solve_ms = ms;
+        // a batch reports each instance's own completion (host-observed, from
+        // the start of the batch); a single solve the device time of the solve
+        out[q].solve_ms = track ? (fin_ms[q] >= 0.0 ? fin_ms[q] : (double)ms) : ms;
         out[q].kernel_launches = launches;
         out[q].blocks = nb;
         if (keep) {

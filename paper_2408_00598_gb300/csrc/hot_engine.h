@@ -84,6 +84,7 @@ struct Batch {
     int* d_running = nullptr;
     int* d_st = nullptr;            // [cap] per-instance status after each check
     int* h_st = nullptr;            // pinned mirror
+    int* h_stb = nullptr;           // pinned, [2][cap]: statuses after the last two blocks (finish times)
     WorkDev* h_work = nullptr;      // pinned
     HotInst* h_inst = nullptr;      // pinned
     int* h_pre = nullptr;           // pinned
@@ -99,6 +100,8 @@ struct Batch {
     cudaStream_t cap_stream = nullptr;
     LaunchDims ld{};
     int ninst = 0;
+    int single = -1;                // the instance count the graphs were captured for is 1 (1), more (0), none (-1)
+    void drop_graphs();
     ~Batch();
     int reserve(int n);
     int set_instances(const std::vector<Inst*>& v, cudaStream_t st);   // async H2D

@@ -150,7 +150,7 @@ struct HotInst {
     float2* K2;            // [2mn] (mu - colsum u)/(sigma m) per slab column (/(sigma n) for f2), fixed within a cycle
     float2* vec2;          // rows of max(m, n): T1, T2, then ceil(n/64) partials of P1 and ceil(m/64) of P2, of u + d
     float2* dab2;          // [4mn] pieces of A^T(y-bar - y0)
-    float2* stg2;          // [4][max(m, n)] Prop. 3 stage of the current iteration: mvA, mvS, sy, sp (k_vec32)
+    float2* stg2;          // [4][max(m, n)] Prop. 3 stage of the current iteration: mvA, mvS, sy, sp (k_stage32)
     unsigned int* vcount;  // k_vec32 items of this instance finished in the running launch (0 between launches)
     float2* mu1f;          // [m][n] mu1 as pairs
     float2* mu2f;          // [m][n] mu2 as pairs
@@ -228,14 +228,15 @@ struct LaunchDims {
     int grid_slab;
     int grid_alpha;        // k_alpha32 (FP32 mode)
     int grid_vec;
+    int grid_vec1;         // k_vec32 of a single-instance batch (it also forms the stage)
     int grid_k1;
     int grid_inst;
 };
 
 // launches of one iteration: FP64 k_vec, k_marg, k_alpha, k_sweep64; FP32
-// k_vec32, k_alpha32, k_sweep32
-inline int launches_per_iteration(int fp64, bool) { return fp64 ? 4 : 3; }
-inline int launches_per_block(int fp64, int K) { return K * launches_per_iteration(fp64, false); }
+// k_vec32, k_stage32 (batches of several instances only), k_alpha32, k_sweep32
+inline int launches_per_iteration(int fp64, bool single) { return fp64 ? 4 : (single ? 3 : 4); }
+inline int launches_per_block(int fp64, int K, bool single) { return K * launches_per_iteration(fp64, single); }
 constexpr int kLaunchesBlockEnd = 8;       // k_kkt1, k_check, 3 x k_restart, k_restart_sigma, k_anchor, k_block_end
 // work items of k_vec32 per instance: T1 (n outputs) and T2 (m outputs) in
 // items of 8, P1 (m columns over n rows) and P2 (n columns over m rows) in items
@@ -251,7 +252,8 @@ inline size_t vec2_entries(int m, int n) {
     const int L = m > n ? m : n;
     return (size_t)(3 + (n + 63) / 64 + (m + 63) / 64) * L;
 }
-void launch_solve_kernels(const WorkDev* w, const LaunchDims& ld, int fp64, int j, bool check, cudaStream_t st);
+void launch_solve_kernels(const WorkDev* w, const LaunchDims& ld, int fp64, int j, bool check, bool single,
+                          cudaStream_t st);
 void launch_sweep(const WorkDev* w, const LaunchDims& ld, int fp64, int j, bool check, cudaStream_t st);
 void launch_block_end(const WorkDev* w, const LaunchDims& ld, int fp64, int K, double a1, double a2, double a3,
                       cudaStream_t st);

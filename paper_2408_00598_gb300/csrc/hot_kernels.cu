@@ -543,7 +543,7 @@ constexpr int kVecRows = 64;
 struct PieceIn {
     float2 a0;            // anchor piece (hi, lo)
     float2 x, y, mu;
-    float2 s0, s1;        // the stage entries the piece uses (k_vec32): row pieces mvA_j, mvS_k; column pieces sy_j or sp_k
+    float2 s0, s1;        // the stage entries the piece uses (k_stage32): row pieces mvA_j, mvS_k; column pieces sy_j or sp_k
     float xc;             // bin coordinate of the piece's row or column
 };
 __device__ __forceinline__ void piece_slab(const HotInst& I, int q, int& slab, int& idx) {
@@ -762,11 +762,16 @@ __device__ void alpha32_stage(const HotInst& I, float2* __restrict__ sq, float2*
     }
 }
 
+// SINGLE (a batch of one instance): the CTA that finishes the instance's last
+// item also forms its Prop. 3 stage (k_stage32's work), which saves a kernel
+// on the single-instance path; batches of many instances launch k_stage32,
+// since there every item would pay the count's atomic and barriers.
+template <bool SINGLE>
 __global__ void __launch_bounds__(kThreads) k_vec32(const WorkDev* __restrict__ W, int j) {
     constexpr int kW = kThreads / 32;
     constexpr int kRW = kVecRows / kW;               // rows per warp in a P item
     __shared__ float2 s_p[kThreads];
-    __shared__ float2 s_red[2 * 32];
+    __shared__ float2 s_red[SINGLE ? 2 * 32 : 1];
     __shared__ int s_t[4];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ninst = W->ninst;
@@ -847,28 +852,45 @@ __global__ void __launch_bounds__(kThreads) k_vec32(const WorkDev* __restrict__ 
                     I.vec2[(size_t)(2 + (which ? r1 : 0) + part) * L + q] = df_st(tot);
                 }
             }
-            // The CTA that finishes an instance's last item forms its Prop. 3
-            // stage once, for every piece of the next kernel.  The barrier
-            // orders this CTA's writes of the item before thread 0's fence,
-            // which makes them visible device-wide before the count (the
-            // pattern of a grid-wide barrier); the last CTA reads the others'
-            // through L2 (__ldcg in stage_in).
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                __threadfence();
-                const unsigned int done = atomicAdd(I.vcount, 1u) + 1u;
-                s_t[3] = done == (unsigned int)vec32_items_dev(m, n);
-                if (s_t[3]) __threadfence();
-            }
-            __syncthreads();
-            if (s_t[3]) {
-                alpha32_stage(I, I.stg2, s_red);
+            if constexpr (SINGLE) {
+                // The barrier orders this CTA's writes of the item before thread
+                // 0's fence, which makes them visible device-wide before the
+                // count (the pattern of a grid-wide barrier); the last CTA reads
+                // the others' through L2 (__ldcg in stage_in).
+                __syncthreads();
                 if (threadIdx.x == 0) {
-                    *I.vcount = 0u;                           // for the next launch
-                    *I.p32 = make_p32(I.ctl->sigma, I.ctl->k + j, I.h, I.gadmm, I.relax);
+                    __threadfence();
+                    const unsigned int done = atomicAdd(I.vcount, 1u) + 1u;
+                    s_t[3] = done == (unsigned int)vec32_items_dev(m, n);
+                    if (s_t[3]) __threadfence();
+                }
+                __syncthreads();
+                if (s_t[3]) {
+                    alpha32_stage(I, I.stg2, s_red);
+                    if (threadIdx.x == 0) {
+                        *I.vcount = 0u;                           // for the next launch
+                        *I.p32 = make_p32(I.ctl->sigma, I.ctl->k + j, I.h, I.gadmm, I.relax);
+                    }
                 }
             }
         }
+        __syncthreads();
+    }
+}
+
+// k_stage32: the instance-wide Prop. 3 stage (alpha32_stage) from k_vec32's
+// sums, one CTA per instance, and the element constants of the iteration.
+// (A kernel of its own: forming it in the CTA that finishes an instance's
+// last k_vec32 item cost every item an atomic and a barrier, which batches of
+// many small instances paid many times over.)
+__global__ void __launch_bounds__(kThreads) k_stage32(const WorkDev* __restrict__ W, int j) {
+    __shared__ float2 s_red[2 * 32];
+    const int ninst = W->ninst;
+    for (int i = blockIdx.x; i < ninst; i += gridDim.x) {
+        const HotInst I = W->inst[i];
+        if (I.ctl->status != ST_RUNNING) continue;   // block-uniform
+        alpha32_stage(I, I.stg2, s_red);
+        if (threadIdx.x == 0) *I.p32 = make_p32(I.ctl->sigma, I.ctl->k + j, I.h, I.gadmm, I.relax);
         __syncthreads();
     }
 }
@@ -879,7 +901,7 @@ __global__ void __launch_bounds__(kThreads) k_vec32(const WorkDev* __restrict__ 
 // are cut into chunks of kAlphaChunk (kAPT per thread, consecutive threads on
 // consecutive pieces); a CTA takes chunks in a grid-stride loop and loads the
 // inputs of all its pieces of a chunk before it computes any.  The
-// instance-wide O(m + n) stage of Prop. 3 comes from k_vec32 (stg2), so a
+// instance-wide O(m + n) stage of Prop. 3 comes from k_stage32 (stg2), so a
 // piece is a few loads and double-float operations.  The descriptor is copied
 // into registers: the stores below cannot then force reloads of its fields.
 // Per-chunk partial sums sit at the chunk's index (dobj_part, cD_part;
@@ -2033,13 +2055,15 @@ LaunchDims make_launch_dims(int device, int fp64) {
         d.grid_slab = occ_grid(k_alpha<true>, sms, 0, 4);
         d.grid_alpha = d.grid_slab;
         d.grid_vec = occ_grid(k_vec, sms, 0, 4);
+        d.grid_vec1 = d.grid_vec;
     } else {
         d.grid_tile = occ_grid(k_sweep32<false>, sms, kSweepSmem, 8);
         d.grid_tile_chk = occ_grid(k_sweep32<true>, sms, kSweepSmemChk, 8);
         d.grid_rst = std::min(occ_grid(k_restart<float, 0>, sms, 0, 8), occ_grid(k_restart<float, 1>, sms, 0, 8));
         d.grid_slab = occ_grid(k_anchor, sms, 0, 4);
         d.grid_alpha = occ_grid(k_alpha32<true>, sms, 0, 2);
-        d.grid_vec = occ_grid(k_vec32, sms, 0, 4);
+        d.grid_vec = occ_grid(k_vec32<false>, sms, 0, 4);
+        d.grid_vec1 = occ_grid(k_vec32<true>, sms, 0, 4);
     }
     d.grid_k1 = occ_grid(k_kkt1<true>, sms, 0, 6);
     d.grid_inst = sms * 2;
@@ -2087,13 +2111,19 @@ static void launch(const LaunchDims&, void (*k)(KArgs...), int grid, size_t smem
     cudaLaunchKernelEx(&cfg, k, args...);
 }
 
-void launch_solve_kernels(const WorkDev* w, const LaunchDims& ld, int fp64, int j, bool check, cudaStream_t st) {
+void launch_solve_kernels(const WorkDev* w, const LaunchDims& ld, int fp64, int j, bool check, bool single,
+                          cudaStream_t st) {
     if (fp64) {
         launch(ld, k_vec, ld.grid_vec, 0, st, w);
         launch(ld, k_marg, ld.grid_inst, 7 * kMaxS * 8, st, w);
         launch(ld, check ? k_alpha<true> : k_alpha<false>, ld.grid_slab, 0, st, w);
     } else {
-        launch(ld, k_vec32, ld.grid_vec, 0, st, w, j);
+        if (single) {
+            launch(ld, k_vec32<true>, ld.grid_vec1, 0, st, w, j);
+        } else {
+            launch(ld, k_vec32<false>, ld.grid_vec, 0, st, w, j);
+            launch(ld, k_stage32, ld.grid_inst, 0, st, w, j);
+        }
         launch(ld, check ? k_alpha32<true> : k_alpha32<false>, ld.grid_alpha, 0, st, w, j);
     }
 }

@@ -63,7 +63,10 @@ __device__ void node_prefix(const double* __restrict__ x, int S, int k, int j, d
         b[t] = fmax(x[S3 + k + (size_t)S * j + S2 * t], 0.0);
     }
     __syncwarp();
-    double ca = 0.0, cb = 0.0;
+    // exclusive prefix sums by a warp scan; a running maximum keeps them
+    // non-decreasing (a tree scan's partial sums need not be ordered to the
+    // last bit, and the binary search and walk below rely on the order)
+    double ca = 0.0, cb = 0.0, ma = 0.0, mb = 0.0;
     for (int base = 0; base < S; base += 32) {
         const int t = base + lane;
         const double va = t < S ? a[t] : 0.0, vb = t < S ? b[t] : 0.0;
@@ -76,23 +79,35 @@ __device__ void node_prefix(const double* __restrict__ x, int S, int k, int j, d
                 sb += yb;
             }
         }
-        if (t < S) {
-            A[t] = ca + sa - va;
-            B[t] = cb + sb - vb;
+        double ea = fmax(ca + sa - va, ma), eb = fmax(cb + sb - vb, mb);
+        for (int o = 1; o < 32; o <<= 1) {
+            const double ya = __shfl_up_sync(0xffffffffu, ea, o);
+            const double yb = __shfl_up_sync(0xffffffffu, eb, o);
+            if (lane >= o) {
+                ea = fmax(ea, ya);
+                eb = fmax(eb, yb);
+            }
         }
+        if (t < S) {
+            A[t] = ea;
+            B[t] = eb;
+        }
+        ma = __shfl_sync(0xffffffffu, ea, 31);
+        mb = __shfl_sync(0xffffffffu, eb, 31);
         ca += __shfl_sync(0xffffffffu, sa, 31);
         cb += __shfl_sync(0xffffffffu, sb, 31);
     }
     if (lane == 0) {
-        A[S] = ca;
-        B[S] = cb;
+        A[S] = fmax(ca, ma);
+        B[S] = fmax(cb, mb);
     }
     __syncwarp();
 }
 
 // entries of source i: overlaps of [A_i, A_{i+1}) with [B_l, B_{l+1})
-__device__ int source_entries(int S, int i, const double* A, const double* B, const double* b, int32_t* src,
-                              int32_t* dst, double* mass, size_t pos, int src_id, int k) {
+__device__ int source_entries(int S, int i, const double* A, const double* B, const double* a, const double* b,
+                              int32_t* src, int32_t* dst, double* mass, size_t pos, int src_id, int k) {
+    if (!(a[i] > 0.0)) return 0;             // the loops move nothing out of an empty source
     const double lo = A[i];
     const double hi = fmin(A[i + 1], B[S]);
     if (!(hi > lo)) return 0;
@@ -138,7 +153,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_static_recover(const double* __
         node_prefix(x, S, k, j, a, b, A, B);
         if (count_only) {
             int c = 0;
-            for (int i = lane; i < S; i += 32) c += source_entries(S, i, A, B, b, nullptr, nullptr, nullptr, 0, 0, k);
+            for (int i = lane; i < S; i += 32) c += source_entries(S, i, A, B, a, b, nullptr, nullptr, nullptr, 0, 0, k);
             for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
             if (lane == 0) counts[node] = c;
             for (int t = lane; t < S; t += 32) {
@@ -152,13 +167,13 @@ __global__ void __launch_bounds__(kWarps * 32) k_static_recover(const double* __
             for (int base = 0; base < S; base += 32) {
                 const int i = base + lane;
                 int c = 0;
-                if (i < S) c = source_entries(S, i, A, B, b, nullptr, nullptr, nullptr, 0, 0, k);
+                if (i < S) c = source_entries(S, i, A, B, a, b, nullptr, nullptr, nullptr, 0, 0, k);
                 int incl = c;
                 for (int o = 1; o < 32; o <<= 1) {
                     const int y = __shfl_up_sync(0xffffffffu, incl, o);
                     if (lane >= o) incl += y;
                 }
-                if (i < S && c > 0) source_entries(S, i, A, B, b, src, dst, mass, (size_t)(pos + incl - c), i * S + j, k);
+                if (i < S && c > 0) source_entries(S, i, A, B, a, b, src, dst, mass, (size_t)(pos + incl - c), i * S + j, k);
                 pos += __shfl_sync(0xffffffffu, incl, 31);
             }
         }
@@ -273,12 +288,29 @@ HOT_API int hot_recover_plan_static(const double* x, int m, int n, const double*
     const int S = m;
     const int nodes = S * S;
     int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+        fail("cannot read the device's multiprocessor count");
+        return HOT_ECUDA;
+    }
     const int grid = (nodes + kWarps - 1) / kWarps < sms * 8 ? (nodes + kWarps - 1) / kWarps : sms * 8;
-    k_static_clear<<<sms > 0 ? sms : 1, 256, 0, st>>>(scratch, nodes);
+    // a launch that fails (bad configuration, no device) must not leave the
+    // later kernels reading counts of an earlier call: check each one
+    auto launched = [](const char* what) {
+        const cudaError_t le = cudaGetLastError();
+        if (le == cudaSuccess) return true;
+        fail((std::string(what) + ": " + cudaGetErrorString(le)).c_str());
+        return false;
+    };
+    k_static_clear<<<sms, 256, 0, st>>>(scratch, nodes);
+    if (!launched("clearing the scratch")) return HOT_ECUDA;
     k_static_recover<<<grid, kWarps * 32, 0, st>>>(x, S, 1, scratch, nullptr, nullptr, nullptr);
+    if (!launched("counting the plan entries")) return HOT_ECUDA;
     k_static_scan<<<1, 1024, 0, st>>>(scratch, nodes);
-    if (marg_l1) k_static_l1<<<1, 1024, 0, st>>>(scratch, mu, nu, nodes);
+    if (!launched("the entry offsets")) return HOT_ECUDA;
+    if (marg_l1) {
+        k_static_l1<<<1, 1024, 0, st>>>(scratch, mu, nu, nodes);
+        if (!launched("the marginal distances")) return HOT_ECUDA;
+    }
     unsigned long long tot = 0;
     double l1[2] = {0.0, 0.0};
     cudaError_t e = cudaMemcpyAsync(&tot, scratch + kOffTotal, sizeof(tot), cudaMemcpyDeviceToHost, st);
@@ -300,6 +332,7 @@ HOT_API int hot_recover_plan_static(const double* x, int m, int n, const double*
     }
     if (tot > 0) {
         k_static_recover<<<grid, kWarps * 32, 0, st>>>(x, S, 0, scratch, src, dst, mass);
+        if (!launched("writing the plan entries")) return HOT_ECUDA;
         e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) {
             fail(cudaGetErrorString(e));

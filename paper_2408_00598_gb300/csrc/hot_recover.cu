@@ -45,8 +45,10 @@ __device__ __forceinline__ void load_node(const T* __restrict__ x, int m, int n,
     for (int t = lane; t < m; t += 32) a[t] = fmax((double)ra[t], 0.0);
     for (int t = lane; t < n; t += 32) b[t] = fmax((double)rb[t], 0.0);
     __syncwarp();
-    // exclusive prefix sums, sequential per 32-chunk with a warp scan (FP64)
-    double carryA = 0.0, carryB = 0.0;
+    // exclusive prefix sums, sequential per 32-chunk with a warp scan (FP64);
+    // a tree scan's partial sums need not be ordered to the last bit, so a
+    // running maximum keeps A and B non-decreasing (the walk relies on it)
+    double carryA = 0.0, carryB = 0.0, runA = 0.0, runB = 0.0;
     const int L = m > n ? m : n;
     for (int base = 0; base < L; base += 32) {
         const int t = base + lane;
@@ -61,22 +63,35 @@ __device__ __forceinline__ void load_node(const T* __restrict__ x, int m, int n,
                 sb += yb;
             }
         }
-        if (t < m) A[t] = carryA + sa - va;
-        if (t < n) B[t] = carryB + sb - vb;
+        double ea = fmax(carryA + sa - va, runA), eb = fmax(carryB + sb - vb, runB);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const double ya = __shfl_up_sync(0xffffffffu, ea, o);
+            const double yb = __shfl_up_sync(0xffffffffu, eb, o);
+            if (lane >= o) {
+                ea = fmax(ea, ya);
+                eb = fmax(eb, yb);
+            }
+        }
+        if (t < m) A[t] = ea;
+        if (t < n) B[t] = eb;
+        runA = __shfl_sync(0xffffffffu, ea, 31);
+        runB = __shfl_sync(0xffffffffu, eb, 31);
         carryA += __shfl_sync(0xffffffffu, sa, 31);
         carryB += __shfl_sync(0xffffffffu, sb, 31);
     }
     if (lane == 0) {
-        A[m] = carryA;
-        B[n] = carryB;
+        A[m] = fmax(carryA, runA);
+        B[n] = fmax(carryB, runB);
     }
     __syncwarp();
 }
 
 // number of sinks (of n) overlapping source i (and optionally write them)
-__device__ __forceinline__ int node_source(int n, int i, const double* A, const double* B, const double* b,
-                                           int32_t* src, int32_t* dst, double* mass, size_t pos, int src_id,
-                                           int node_k) {
+__device__ __forceinline__ int node_source(int n, int i, const double* A, const double* B, const double* a,
+                                           const double* b, int32_t* src, int32_t* dst, double* mass, size_t pos,
+                                           int src_id, int node_k) {
+    if (!(a[i] > 0.0)) return 0;             // the loops move nothing out of an empty source
     const double lo = A[i];
     const double hi = fmin(A[i + 1], B[n]);
     if (!(hi > lo)) return 0;
@@ -121,7 +136,7 @@ __global__ void __launch_bounds__(kRecWarps * 32) k_recover(const T* __restrict_
         load_node(x, m, n, k, j, a, b, A, B);
         if (count_only) {
             int c = 0;
-            for (int i = lane; i < m; i += 32) c += node_source(n, i, A, B, b, nullptr, nullptr, nullptr, 0, 0, k);
+            for (int i = lane; i < m; i += 32) c += node_source(n, i, A, B, a, b, nullptr, nullptr, nullptr, 0, 0, k);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
             if (lane == 0) counts[node] = c;
@@ -140,7 +155,7 @@ __global__ void __launch_bounds__(kRecWarps * 32) k_recover(const T* __restrict_
             for (int base = 0; base < m; base += 32) {
                 const int i = base + lane;
                 int c = 0;
-                if (i < m) c = node_source(n, i, A, B, b, nullptr, nullptr, nullptr, 0, 0, k);
+                if (i < m) c = node_source(n, i, A, B, a, b, nullptr, nullptr, nullptr, 0, 0, k);
                 int incl = c;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
@@ -148,7 +163,7 @@ __global__ void __launch_bounds__(kRecWarps * 32) k_recover(const T* __restrict_
                     if (lane >= o) incl += y;
                 }
                 if (i < m && c > 0)
-                    node_source(n, i, A, B, b, src, dst, mass, (size_t)(pos + incl - c), i * n + j, k);
+                    node_source(n, i, A, B, a, b, src, dst, mass, (size_t)(pos + incl - c), i * n + j, k);
                 pos += __shfl_sync(0xffffffffu, incl, 31);
             }
         }

@@ -37,9 +37,9 @@ for kind in syn.KINDS:
     CASES.append(("c2_%s32" % kind, kind, 32, 3, 1e-6, 100000, False))
     CASES.append(("s16_%s" % kind, kind, 16, 4, 1e-6, 100000, True))
 # 256 x 256 white-noise pair of the throughput benchmark (seed 1000), at the
-# paper's stopping rule and at 1e-8 (where the plan's marginals reach 1e-6)
+# paper's stopping rule (440 iterations; the 3.8e4 iterations to relative KKT
+# 1e-8 would take the oracle over a day)
 CASES.append(("c3_white256", "white", 256, 1000, 1e-6, 100000, False))
-CASES.append(("c3_white256_t8", "white", 256, 1000, 1e-8, 100000, False))
 # one 128 x 128 pair per class at the paper's stopping rule
 for kind in syn.KINDS:
     CASES.append(("c3_%s128" % kind, kind, 128, 5, 1e-6, 100000, False))

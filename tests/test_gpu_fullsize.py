@@ -93,9 +93,9 @@ def test_translation_512(ctx):
 
 # ------------------------------------------- the 256 x 256 benchmark pair --
 
-def test_benchmark_pair_plan_marginals_and_algorithm1_at_1e9(ctx):
+def test_benchmark_pair_plan_marginals_and_algorithm1(ctx):
     """The throughput benchmark's 256 x 256 white-noise pair (seed 1000) solved
-    to relative KKT 1e-9: the recovered plan's marginals agree with mu and nu
+    to relative KKT 5e-10: the recovered plan's marginals agree with mu and nu
     to 1e-6 in L1 (recomputed here on the host from the returned entries), and
     Algorithm 1 on the device gives, node by node, the entries of the oracle's
     literal loops (Alg. 1) run on the same clipped flows, for 64 sampled nodes
@@ -104,13 +104,13 @@ def test_benchmark_pair_plan_marginals_and_algorithm1_at_1e9(ctx):
     from oracle import reduced_model as rm
     S = 256
     mu1, mu2 = syn.make_pair("white", S, 1000)
-    # relative KKT 1e-8 leaves 3.6e-6 in L1 here: the 2-norm rule over the
-    # 3M - 1 rows of A x = b allows an L1 residual of about sqrt(3M) times it
-    r = ctx.solve(mu1, mu2, tol=1e-9, max_iter=300000)
+    # measured on this pair: relative KKT 1e-8 (37,800 iterations) leaves
+    # 3.6e-6 in L1, 1e-9 (57,070) 1.4e-6, 5e-10 (69,720) 3.3e-7
+    r = ctx.solve(mu1, mu2, tol=5e-10, max_iter=1000000)
     x = ctx.flows(r)
     src, dst, mass, l1 = ctx.recover_plan(r)
     ctx.release(r)
-    assert r["status"] == 0 and r["rel_kkt"] <= 1e-9
+    assert r["status"] == 0 and r["rel_kkt"] <= 5e-10
     m1 = np.bincount(src, weights=mass, minlength=S * S).reshape(S, S)
     m2 = np.bincount(dst, weights=mass, minlength=S * S).reshape(S, S)
     e1, e2 = np.abs(m1 - mu1).sum(), np.abs(m2 - mu2).sum()
