@@ -661,9 +661,18 @@ int run_solve(Ctx* ctx, const std::vector<PairHost>& pairs, double tol, long lon
     // batches: the host time at which the block holding each instance's last
     // check was seen complete (its status copied back after every block)
     const bool track = insts.size() > 1 && !kt;
-    const int ni = (int)insts.size();
     std::vector<double> fin_ms(insts.size(), -1.0);
+    // live[q]: the pair at position q of the work tables (batches drop their
+    // finished pairs from the tables as they go, see below)
+    std::vector<int> live(insts.size());
+    for (size_t q = 0; q < insts.size(); ++q) live[q] = (int)q;
+    long long launches = 0;
     const auto th0 = std::chrono::steady_clock::now();
+    auto note_finished = [&](const int* sts) {
+        const double now = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - th0).count();
+        for (size_t q = 0; q < live.size(); ++q)
+            if (fin_ms[live[q]] < 0.0 && sts[q] != ST_RUNNING) fin_ms[live[q]] = now;
+    };
     cudaEventRecord(t0, st);
     for (;;) {
         if (!kt) {
@@ -671,18 +680,47 @@ int run_solve(Ctx* ctx, const std::vector<PairHost>& pairs, double tol, long lon
                 err = HOT_ECUDA;
                 break;
             }
+            launches += launches_per_block(fp64, (int)K, B.ninst == 1) + kLaunchesBlockEnd;
             cudaMemcpyAsync(&B.h_running[1 + (nb & 1)], B.d_running, sizeof(int), cudaMemcpyDeviceToHost, st);
             if (track)
-                cudaMemcpyAsync(B.h_stb + (size_t)(nb & 1) * B.cap, B.d_st, sizeof(int) * ni, cudaMemcpyDeviceToHost, st);
+                cudaMemcpyAsync(B.h_stb + (size_t)(nb & 1) * B.cap, B.d_st, sizeof(int) * live.size(),
+                                cudaMemcpyDeviceToHost, st);
             cudaEventRecord(ev[nb & 1], st);
             if (nb >= 1) {
                 cudaEventSynchronize(ev[(nb - 1) & 1]);
-                if (track) {
-                    const double now =
-                        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - th0).count();
-                    const int* sts = B.h_stb + (size_t)((nb - 1) & 1) * B.cap;
-                    for (int q = 0; q < ni; ++q)
-                        if (fin_ms[q] < 0.0 && sts[q] != ST_RUNNING) fin_ms[q] = now;
+                if (track) note_finished(B.h_stb + (size_t)((nb - 1) & 1) * B.cap);
+                // Tail of a batch: once at most a quarter of the table still
+                // runs, rebuild the tables with the running pairs alone, so that
+                // the kernels stop walking the finished pairs' items (and a last
+                // pair runs the single-instance kernels).  Every pair keeps its
+                // own state, so its iterates do not change.
+                const int run_prev = B.h_running[1 + ((nb - 1) & 1)];
+                if (track && live.size() > 1 && run_prev > 0 && (size_t)run_prev * 4 <= live.size()) {
+                    cudaEventSynchronize(ev[nb & 1]);            // block nb and its status copy
+                    const int* sts = B.h_stb + (size_t)(nb & 1) * B.cap;
+                    note_finished(sts);
+                    std::vector<Inst*> keep;
+                    std::vector<int> keep_idx;
+                    for (size_t q = 0; q < live.size(); ++q)
+                        if (sts[q] == ST_RUNNING) {
+                            keep.push_back(insts[live[q]]);
+                            keep_idx.push_back(live[q]);
+                        }
+                    if (keep.empty()) {
+                        ++nb;
+                        break;
+                    }
+                    if (B.set_instances(keep, st) != HOT_OK || B.ensure_graph(0) != HOT_OK) {
+                        err = HOT_ECUDA;
+                        ++nb;
+                        break;
+                    }
+                    live = keep_idx;
+                    // block nb's statuses, now at the new positions (all running)
+                    int* stn = B.h_stb + (size_t)(nb & 1) * B.cap;
+                    for (size_t q = 0; q < live.size(); ++q) stn[q] = ST_RUNNING;
+                    ++nb;
+                    continue;
                 }
                 if (timing) {
                     // block nb - 1 has finished; block nb runs on the other graph instance
@@ -762,7 +800,7 @@ int run_solve(Ctx* ctx, const std::vector<PairHost>& pairs, double tol, long lon
         cleanup();
         return HOT_ECUDA;
     }
-    const long long launches = nb * (launches_per_block(fp64, (int)K, insts.size() == 1) + kLaunchesBlockEnd);
+    if (kt) launches = nb * (launches_per_block(fp64, (int)K, insts.size() == 1) + kLaunchesBlockEnd);
     for (size_t q = 0; q < insts.size(); ++q) {
         Inst* I = insts[q];
         cudaMemcpy(&I->ctl_host, I->desc.ctl, sizeof(HotCtl), cudaMemcpyDeviceToHost);
