@@ -251,7 +251,12 @@ HOT_API int hot_sweep_timing(hot_ctx *ctx, int enable, double *total_ms, long lo
  *   stream:  cudaStream_t to run on (NULL: the legacy default stream); the call
  *            returns after its work on that stream has finished.
  * Every call shares the one scratch array and overwrites it; calls whose work
- * overlaps on the GPU race and produce wrong results. */
+ * overlaps on the GPU race and produce wrong results.
+ * The prefix sums of Algorithm 1 are formed in FP64 from x.  For a solution of
+ * an FP64-mode context the result equals hot_recover_plan's; for an FP32-bulk
+ * solution (x its hot_get_flows export) hot_recover_plan works on the FP32
+ * flows with double-float prefix sums, so the two plans agree to the rounding
+ * of those sums (about 1e-12 of the total mass), not entry for entry. */
 HOT_API int hot_recover_plan_static(const double *x, int m, int n, const double *mu, const double *nu,
                             int32_t *src, int32_t *dst, double *mass, size_t cap, size_t *nnz,
                             double *marg_l1, void *stream);

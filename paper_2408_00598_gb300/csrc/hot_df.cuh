@@ -1,9 +1,11 @@
 // Double-float arithmetic for the CUDA kernels of the HOT library.
 //
 // An unevaluated pair (hi, lo) of FP32 values whose sum carries about twice
-// the FP32 precision (about 48 significant bits); each add is an exact
-// two-sum followed by renormalisation, products take the exact error of
-// hi * hi from an fma.  FP64 arithmetic runs at a small fraction of the FP32
+// the FP32 precision (about 48 significant bits): the double-length arithmetic
+// of Dekker (1971).  Each add is Knuth's exact two-sum (TAOCP vol. 2, 4.2.2)
+// followed by renormalisation (fast two-sum); a product takes the exact
+// rounding error of hi * hi from a fused multiply-add in place of Dekker's
+// splitting.  FP64 arithmetic runs at a small fraction of the FP32
 // rate on GB300, so sums and comparisons that must be accurate to FP64 level
 // use these pairs on the FP32 pipe.
 #pragma once

@@ -274,10 +274,12 @@ def _dense_plan(entries, S):
     return P
 
 
-def test_recovery_matches_oracle_algorithm1(ctx64):
-    """Algorithm 1 on the GPU vs the literal loops on the oracle's own x-bar."""
+@pytest.mark.parametrize("kind", ["white", "shapes"])
+def test_recovery_matches_oracle_algorithm1(ctx64, kind):
+    """Algorithm 1 on the GPU vs the literal loops on the oracle's own x-bar
+    (shapes: bins of zero mass, i.e. empty sources and sinks at many nodes)."""
     S = 16
-    mu1, mu2 = syn.make_pair("white", S, 1)
+    mu1, mu2 = syn.make_pair(kind, S, 1)
     ref = ohot.hot_solve(mu1, mu2, tol=1e-8)
     r = ctx64.solve(mu1, mu2, tol=1e-8)
     src, dst, mass, l1 = ctx64.recover_plan(r)
