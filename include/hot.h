@@ -14,9 +14,9 @@
  * Conventions for every entry point:
  *   - histograms are row-major m x n arrays of double: mu[i*n + j] is the mass
  *     of bin (i, j) (row i, column j);
- *   - m and n are multiples of 4 in [8, 1024] (FP64 mode: [8, 512]); m may
- *     differ from n (the cost along each axis is that axis' own squared
- *     distance, Sec. II-A); other shapes return HOT_EINVAL;
+ *   - m and n are in [2, 1024] (FP64 mode: [2, 512]); m may differ from n
+ *     (the cost along each axis is that axis' own squared distance, Sec.
+ *     II-A); other shapes return HOT_EINVAL;
  *   - a histogram is valid when every entry is finite and >= 0 and its sum is
  *     1 within 1e-9; unequal masses are rejected, never renormalised;
  *   - pointers marked "host or device" are read according to `space`

@@ -82,9 +82,10 @@ void tune_pair(int S, PairHost& p) {
 
 std::vector<int> tile_candidates(int S, int fp64) {
     const int cap = fp64 ? 4096 : 16384;
+    const int Sp = (S + 3) & ~3;             // the row pitch of an S x S slab
     std::vector<int> out;
-    for (int tr = std::min(S, cap / S); tr >= 1 && out.size() < 4; tr /= 2) {
-        if ((long long)tr * S < 1024 && !out.empty()) break;
+    for (int tr = std::min(S, cap / Sp); tr >= 1 && out.size() < 4; tr /= 2) {
+        if ((long long)tr * Sp < 1024 && !out.empty()) break;
         if (fp64 && S >= 96 && tr > 32) continue;
         out.push_back(tr);
     }
@@ -109,7 +110,7 @@ void autotune_load(Ctx* ctx) {
 
 int autotune(Ctx* ctx, int S, int* tr_out, double* us_out) {
     const int fp64 = ctx->cfg.precision == HOT_FP64 ? 1 : 0;
-    if (S < 8 || S > kMaxS || (S & 3) || (fp64 && S > 512)) {
+    if (S < 2 || S > kMaxS || (fp64 && S > 512)) {
         set_error("autotune: unsupported grid side");
         return HOT_EINVAL;
     }

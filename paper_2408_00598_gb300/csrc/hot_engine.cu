@@ -22,11 +22,13 @@ const char* get_error() { return g_err.c_str(); }
 
 int tile_rows(int m, int n, int fp64, int grid) {
     // one TR for both halves: the row-partial buffer holds TR rows of the
-    // longer slab side L = max(m, n)
-    const int L = std::max(m, n);
+    // longer slab pitch Lp (the side L = max(m, n) rounded up to a multiple
+    // of 4); a tile has at most L rows
+    const int Ls = std::max(m, n);
+    const int L = (Ls + 3) & ~3;
     if (fp64) {
-        // row-partial buffer: TR * L <= 4096
-        int tr = std::min(L, 4096 / L);
+        // row-partial buffer: TR * Lp <= 4096
+        int tr = std::min(Ls, 4096 / L);
         if (L >= 96) tr = std::min(tr, 32);
         return std::max(tr, 1);
     }
@@ -36,7 +38,7 @@ int tile_rows(int m, int n, int fp64, int grid) {
     // of the grid's CTAs without a tile and a tile keeps at least 4 passes
     // (measured with the autotuner on GB300: TR = 64 at 64^2, 128^2 and 256^2,
     // 32 at 512^2)
-    int tr = std::min(std::min(L, 16384 / L), kMaxTR);
+    int tr = std::min(std::min(Ls, 16384 / L), kMaxTR);
     auto tiles = [&](int t) { return (long long)n * ((m + t - 1) / t) + (long long)m * ((n + t - 1) / t); };
     if (grid > 0)
         while (tiles(tr) < (long long)grid && (long long)(tr / 2) * L >= 4096) tr /= 2;
@@ -79,9 +81,9 @@ int validate_pair(const double* mu, const double* nu, int m, int n, int space, i
     }
     const int smax = fp64 ? 512 : kMaxS;
     for (int side : {m, n})
-        if (side < 8 || side > smax || (side % 4) != 0) {
-            set_error("grid sides must be multiples of 4 in [8, " + std::to_string(smax) + "], got " +
-                      std::to_string(m) + " x " + std::to_string(n));
+        if (side < 2 || side > smax) {
+            set_error("grid sides must be in [2, " + std::to_string(smax) + "], got " + std::to_string(m) + " x " +
+                      std::to_string(n));
             return HOT_EINVAL;
         }
     out.m = m;
@@ -132,13 +134,14 @@ int inst_create(const PairHost& p, int fp64, const hot_config& cfg, double tol, 
     *out = nullptr;
     std::unique_ptr<Inst> I(new Inst());
     const int m = p.m, n = p.n, L = std::max(m, n);
+    const int Lp = (L + 3) & ~3;              // longest row pitch
     I->m = m;
     I->n = n;
     I->fp64 = fp64;
     I->TR = tr_override > 0 ? tr_override : tile_rows(m, n, fp64, sweep_grid(fp64));
     const int NV = fp64 ? 2 : 4;
-    if (I->TR > (fp64 ? L : kMaxTR) || (size_t)I->TR * L > (size_t)(fp64 ? 4096 : 16384) ||
-        kThreads / (L / NV) < 1) {
+    if (I->TR > (fp64 ? L : kMaxTR) || (size_t)I->TR * Lp > (size_t)(fp64 ? 4096 : 16384) ||
+        kThreads / (Lp / NV) < 1) {
         set_error("invalid tile rows for this grid");
         return HOT_EINVAL;
     }
@@ -146,8 +149,10 @@ int inst_create(const PairHost& p, int fp64, const hot_config& cfg, double tol, 
     I->nb2 = (n + I->TR - 1) / I->TR;
     const size_t MN = (size_t)m * n;
     I->n_k1 = (int)((3 * MN - 1 + kThreads - 1) / kThreads);
-    // flow variables: n f1 slabs of m x m, m f2 slabs of n x n
-    const size_t V = MN * (size_t)(m + n);
+    // flow variables: n f1 slabs of m x m, m f2 slabs of n x n, rows stored
+    // at a pitch of the side rounded up to a multiple of 4
+    const int mp = (m + 3) & ~3, np = (n + 3) & ~3;
+    const size_t V = MN * (size_t)(mp + np);
     const size_t es = fp64 ? 8 : 4;
     I->big_bytes = 5 * align256(V * es);
 
@@ -225,6 +230,8 @@ int inst_create(const PairHost& p, int fp64, const hot_config& cfg, double tol, 
     HotInst& d = I->desc;
     d.m = m;
     d.n = n;
+    d.mp = mp;
+    d.np = np;
     d.TR = I->TR;
     d.nb1 = I->nb1;
     d.nb2 = I->nb2;
@@ -441,6 +448,7 @@ void Batch::drop_graphs() {
             tgraph[p] = nullptr;
         }
     single = -1;
+    pad_captured = -1;
 }
 
 int Batch::reserve(int n) {
@@ -479,8 +487,12 @@ int Batch::set_instances(const std::vector<Inst*>& v, cudaStream_t st) {
     int rc = reserve((int)v.size());
     if (rc != HOT_OK) return rc;
     // a single instance and a batch of several run different Prop. 3 kernels
-    // (launch_solve_kernels): a change between the two needs new graphs
-    if (single >= 0 && single != (v.size() == 1 ? 1 : 0)) drop_graphs();
+    // (launch_solve_kernels), and padded slab rows a sweep variant of their
+    // own: a change of either needs new graphs
+    pad = 0;
+    for (const Inst* I : v) pad |= (I->m % 4 != 0) || (I->n % 4 != 0);
+    if ((single >= 0 && single != (v.size() == 1 ? 1 : 0)) || (pad_captured >= 0 && pad_captured != pad))
+        drop_graphs();
     // the pinned staging is rewritten here: wait for earlier copies out of it
     HOT_CK(cudaStreamSynchronize(st));
     const int n = (int)v.size();
@@ -529,7 +541,7 @@ int Batch::capture(cudaGraphExec_t* out, cudaEvent_t* ev) {
         launch_solve_kernels(d_work, ld, fp64, j, j == K - 1, ninst == 1, cap_stream);
         const bool t = ev && j == timed_iter() && j < K - 1;
         if (t) cudaEventRecordWithFlags(ev[0], cap_stream, cudaEventRecordExternal);
-        launch_sweep(d_work, ld, fp64, j, j == K - 1, cap_stream);
+        launch_sweep(d_work, ld, fp64, j, j == K - 1, pad != 0, cap_stream);
         if (t) cudaEventRecordWithFlags(ev[1], cap_stream, cudaEventRecordExternal);
     }
     launch_block_end(d_work, ld, fp64, K, a1, a2, a3, cap_stream);
@@ -555,6 +567,7 @@ int Batch::ensure_graph(int want_timing) {
     if (!cap_stream) HOT_CK(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
     ld = make_launch_dims(device, fp64);
     single = ninst == 1 ? 1 : 0;
+    pad_captured = pad;
     if (!timing) return capture(&graph, nullptr);
     for (int p = 0; p < 2; ++p) {
         for (int q = 0; q < 2; ++q)
@@ -745,7 +758,7 @@ int run_solve(Ctx* ctx, const std::vector<PairHost>& pairs, double tol, long lon
                 cudaEventRecord(pev[3 * j], st);
                 launch_solve_kernels(B.d_work, B.ld, fp64, j, j == K - 1, insts.size() == 1, st);
                 cudaEventRecord(pev[3 * j + 1], st);
-                launch_sweep(B.d_work, B.ld, fp64, j, j == K - 1, st);
+                launch_sweep(B.d_work, B.ld, fp64, j, j == K - 1, B.pad != 0, st);
                 cudaEventRecord(pev[3 * j + 2], st);
             }
             launch_block_end(B.d_work, B.ld, fp64, (int)K, B.a1, B.a2, B.a3, st);

@@ -94,6 +94,7 @@ struct CycleK {
 // Per-instance descriptor (read-only while a block runs).
 struct HotInst {
     int m, n;              // grid: mu is m x n (rows i/k, columns j/l)
+    int mp, np;            // row pitches of the f1 (side m) and f2 (side n) slabs: the side rounded up to a multiple of 4
     int E;                 // cost scale 2^E >= max c; scaled cost = c * 2^-E
     int TR;                // rows per sweep tile
     int nb1, nb2;          // bands (tiles) per f1 slab = ceil(m / TR), per f2 slab = ceil(n / TR)
@@ -171,10 +172,16 @@ struct HotInst {
 __host__ __device__ inline int g_nslab(const HotInst& I) { return I.n + I.m; }
 __host__ __device__ inline int g_side(const HotInst& I, int s) { return s < I.n ? I.m : I.n; }
 __host__ __device__ inline int g_nb(const HotInst& I, int s) { return s < I.n ? I.nb1 : I.nb2; }
-// first flow variable of slab s
+// A slab's rows are stored at a pitch of its side rounded up to a multiple of
+// 4 (16 bytes in FP32), so that every row starts aligned for the vector loads
+// of the sweeps; the pad columns hold zeros and take part in no sum.
+__host__ __device__ inline int g_pitch(const HotInst& I, int s) { return s < I.n ? I.mp : I.np; }
+// first flow variable of slab s (row r, column c at g_elem + r * g_pitch + c)
 __host__ __device__ inline size_t g_elem(const HotInst& I, int s) {
-    return s < I.n ? (size_t)s * I.m * I.m : (size_t)I.n * I.m * I.m + (size_t)(s - I.n) * I.n * I.n;
+    return s < I.n ? (size_t)s * I.m * I.mp : (size_t)I.n * I.m * I.mp + (size_t)(s - I.n) * I.n * I.np;
 }
+// entries of one state array: the slabs with their pad columns
+__host__ __device__ inline size_t g_state_len(const HotInst& I) { return (size_t)I.m * I.n * ((size_t)I.mp + I.np); }
 // first entry of slab s in arrays with one entry per slab row (or column)
 __host__ __device__ inline size_t g_row(const HotInst& I, int s) {
     return s < I.n ? (size_t)s * I.m : (size_t)I.n * I.m + (size_t)(s - I.n) * I.n;
@@ -254,7 +261,8 @@ inline size_t vec2_entries(int m, int n) {
 }
 void launch_solve_kernels(const WorkDev* w, const LaunchDims& ld, int fp64, int j, bool check, bool single,
                           cudaStream_t st);
-void launch_sweep(const WorkDev* w, const LaunchDims& ld, int fp64, int j, bool check, cudaStream_t st);
+// pad: some instance of the batch has a side that is not a multiple of 4
+void launch_sweep(const WorkDev* w, const LaunchDims& ld, int fp64, int j, bool check, bool pad, cudaStream_t st);
 void launch_block_end(const WorkDev* w, const LaunchDims& ld, int fp64, int K, double a1, double a2, double a3,
                       cudaStream_t st);
 LaunchDims make_launch_dims(int device, int fp64);

@@ -1075,8 +1075,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep64(const WorkDev* __restri
         }
         const HotInst& I = W->inst[tc.inst];
         const int slab = tc.slab, band = tc.band;
-        const int S = g_side(I, slab), TR = I.TR;        // this slab's side
-        const int NC = S / NV;
+        const int S = g_side(I, slab), Sp = g_pitch(I, slab), TR = I.TR;   // this slab's side and row pitch
+        const int NC = Sp / NV;
         const int P = kThreads / NC;
         const int cg = threadIdx.x % NC, ro = threadIdx.x / NC;
         const bool active = ro < P;
@@ -1097,25 +1097,31 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep64(const WorkDev* __restri
         const double* dab = I.dab64 + 2 * g_row(I, slab);
         const double* X = I.X64 + g_xbase(I, slab);            // bin coordinates of this half
         double bb[NV], db[NV], cf[NV];
+        const int nval = S - c0;                                // columns inside the slab (pad after)
 #pragma unroll
         for (int e = 0; e < NV; ++e) {
-            bb[e] = active ? ab[S + c0 + e] : 0.0;
-            db[e] = active ? dab[S + c0 + e] : 0.0;
-            cf[e] = active ? X[c0 + e] : 0.0;
+            bb[e] = active && e < nval ? ab[S + c0 + e] : 0.0;
+            db[e] = active && e < nval ? dab[S + c0 + e] : 0.0;
+            cf[e] = active && e < nval ? X[c0 + e] : 0.0;
         }
         if (active) {
             for (int r = r0 + ro; r < r1; r += P) {
                 const double a = ab[r], da = dab[r];
                 const double rf = X[r];
                 double uu[NV], dd[NV], out[NV], xo[NV];
-                VecT<double>::ld(u + (size_t)r * S + c0, uu);
-                VecT<double>::ld(din + (size_t)r * S + c0, dd);
+                VecT<double>::ld(u + (size_t)r * Sp + c0, uu);
+                VecT<double>::ld(din + (size_t)r * Sp + c0, dd);
 #pragma unroll
                 for (int e = 0; e < NV; ++e) {
                     const double dc = rf - cf[e];
                     const double cq = dc * dc;
                     const E64 el = elem64(uu[e], dd[e], cq, a, bb[e], da, db[e], p);
                     out[e] = p.rho * dd[e] + p.trs * el.r;
+                    xo[e] = 0.0;
+                    if (e >= nval) {
+                        out[e] = 0.0;                               // pad columns stay 0
+                        continue;
+                    }
                     if (check) {
                         double xb, zb;
                         xz64(el, p, xb, zb);
@@ -1130,7 +1136,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep64(const WorkDev* __restri
                     }
                     cacc[e] += out[e];
                 }
-                VecT<double>::st(dout + (size_t)r * S + c0, out);
+                VecT<double>::st(dout + (size_t)r * Sp + c0, out);
                 s_row[(r - r0) * (NC + 1) + cg] = out[0] + out[1];
                 if (check) s_xrow[(r - r0) * (NC + 1) + cg] = xo[0] + xo[1];
             }
@@ -1139,15 +1145,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep64(const WorkDev* __restri
         if (active) {
 #pragma unroll
             for (int e = 0; e < NV; ++e) {
-                s_col[ro * S + c0 + e] = cacc[e];
-                if (check) s_xcol[ro * S + c0 + e] = xacc[e];
+                s_col[ro * Sp + c0 + e] = cacc[e];
+                if (check) s_xcol[ro * Sp + c0 + e] = xacc[e];
             }
         }
         __syncthreads();
         const size_t cbase = g_colp(I, slab, band);
         for (int c = threadIdx.x; c < S; c += blockDim.x) {
-            I.cs_part[cbase + c] = sum_f64_strided(s_col + c, P, S);
-            if (check) I.xcs_part[cbase + c] = sum_f64_strided(s_xcol + c, P, S);
+            I.cs_part[cbase + c] = sum_f64_strided(s_col + c, P, Sp);
+            if (check) I.xcs_part[cbase + c] = sum_f64_strided(s_xcol + c, P, Sp);
         }
         for (int rr = threadIdx.x; rr < r1 - r0; rr += blockDim.x) {
             I.rs[g_row(I, slab) + r0 + rr] = sum_f64_strided(s_row + rr * (NC + 1), NC, 1);
@@ -1184,7 +1190,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep64(const WorkDev* __restri
 // so the sweep reads no coordinate array.  A tile's offsets in the per-slab
 // arrays are resolved once, by the issue side, into its descriptor.
 struct TileD {
-    int inst, slab, band, S, NC, P, r0, r1, npass;
+    int inst, slab, band, S, NC, P, r0, r1, npass;   // NC: column groups of the row pitch (S rounded up to 4)
     int row;          // g_row: first row entry of the slab
     int tile;         // g_tile: index of the tile within its instance
     int colp;         // g_colp: first column-partial entry of (slab, band)
@@ -1192,7 +1198,9 @@ struct TileD {
 };
 
 // Resolve tile t; npass = 0 marks a tile of an instance that is not running,
-// or t past the end.
+// or t past the end.  PAD = false: every side of the batch is a multiple of 4,
+// so the pitch is the side.
+template <bool PAD>
 __device__ __forceinline__ TileD tile_desc(const WorkDev* __restrict__ W, int t, int ntiles) {
     TileD d{};
     if (t >= ntiles) return d;
@@ -1202,19 +1210,24 @@ __device__ __forceinline__ TileD tile_desc(const WorkDev* __restrict__ W, int t,
     d.inst = i;
     g_tile_slab(I, loc, d.slab, d.band);
     d.S = g_side(I, d.slab);
-    d.NC = d.S / 4;
+    d.NC = (PAD ? g_pitch(I, d.slab) : d.S) / 4;
     d.P = kThreads / d.NC;
     d.r0 = d.band * I.TR;
     d.r1 = min(d.S, d.r0 + I.TR);
     d.row = (int)g_row(I, d.slab);
     d.tile = g_tile(I, d.slab, d.band);
     d.colp = (int)g_colp(I, d.slab, d.band);
-    d.elem = (long long)g_elem(I, d.slab);
+    d.elem = PAD ? (long long)g_elem(I, d.slab)
+                 : (d.slab < I.n ? (long long)d.slab * I.m * I.m
+                                 : (long long)I.n * I.m * I.m + (long long)(d.slab - I.n) * I.n * I.n);
     if (I.ctl->status == ST_RUNNING) d.npass = (d.r1 - d.r0 + d.P - 1) / d.P;
     return d;
 }
 
-template <bool CHECK>
+// PAD: some slab side of the batch is not a multiple of 4, so a thread's
+// last column group may reach into the pad columns, which are masked (a
+// variant of its own: the masks cost the unpadded sweep registers).
+template <bool CHECK, bool PAD>
 __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkDev* __restrict__ W, int j) {
     constexpr int NV = 4;
     constexpr int kW = kThreads / 32;
@@ -1247,21 +1260,22 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkD
         bool acopy;                // the next pass is the tile's first and this thread copies an alpha piece
     } c;
     auto set_tile = [&](int t) {
-        TileD d = tile_desc(W, t, ntiles);
+        TileD d = tile_desc<PAD>(W, t, ntiles);
         while (t < ntiles && d.npass == 0) {
             t += G;
-            d = tile_desc(W, t, ntiles);
+            d = tile_desc<PAD>(W, t, ntiles);
         }
         c.it = t;
         if (t < ntiles) {
             const HotInst& I = W->inst[d.inst];
             const int ro = tid / d.NC, cg = tid - ro * d.NC;
-            const size_t base = (size_t)d.elem + ((size_t)d.r0 + ro) * d.S + (size_t)cg * NV;
+            const int sp = PAD ? (d.S + 3) & ~3 : d.S;   // row pitch (without padded slabs, the side)
+            const size_t base = (size_t)d.elem + ((size_t)d.r0 + ro) * sp + (size_t)cg * NV;
             c.u = (const float*)I.u + base;
             c.d = (const float*)((j & 1) ? I.d1 : I.d0) + base;
             const int nr = d.r1 - d.r0;
             c.a = I.ab32 + 2 * (size_t)d.row + d.r0 + tid;
-            c.step = d.P * d.S;
+            c.step = d.P * sp;
             // rows ro, ro + P, ... below nr (threads past P rows copy nothing)
             c.mine = ro < d.P && ro < nr ? (nr - ro + d.P - 1) / d.P : 0;
             c.left = d.npass;
@@ -1308,7 +1322,7 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkD
         const float4* ab = I.ab32 + 2 * (size_t)d.row + d.S;
 #pragma unroll
         for (int e = 0; e < NV; ++e)
-            bq[e] = ro < d.P ? ab[c0 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
+            bq[e] = ro < d.P && (!PAD || c0 + e < d.S) ? ab[c0 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
     };
     bool have = false;                           // bq, p hold the current tile's values
     int n = 0;                                   // global index of the next pass to compute
@@ -1322,11 +1336,12 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkD
         const TileD dc = s_td[ck % kStages];
         if (!have) load_cols(dc);
         const HotInst& I = W->inst[dc.inst];
-        const int S = dc.S, NC = dc.NC, P = dc.P;
+        const int S = dc.S, Sp = PAD ? (dc.S + 3) & ~3 : dc.S, NC = dc.NC, P = dc.P;
         const int r0 = dc.r0, nr = dc.r1 - dc.r0;
         const int ro = tid / NC, cg = tid - ro * NC;
         const bool active = ro < P;
         const int c0 = cg * NV;
+        const int nval = PAD ? S - c0 : NV;       // columns of this thread's group inside the slab (pad after)
         const float h = p.h;
 #pragma unroll
         for (int e = 0; e < NV; ++e) {
@@ -1334,8 +1349,8 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkD
             bq[e] = make_float4(fmaf(cf * cf, h, -bq[e].x), bq[e].y, bq[e].z, cf);
         }
         const float4* sa = s_alpha[ck % kStages];
-        float* __restrict__ dout = (float*)((j & 1) ? I.d0 : I.d1) + dc.elem + ((size_t)r0 + ro) * S + c0;
-        const int ostep = P * S;
+        float* __restrict__ dout = (float*)((j & 1) ? I.d0 : I.d1) + dc.elem + ((size_t)r0 + ro) * Sp + c0;
+        const int ostep = P * Sp;
         float* srow = s_row + ro * (NC + 1) + cg;
         float* sxrow = s_xrow + (CHECK ? ro * (NC + 1) + cg : 0);
         const int rstep = P * (NC + 1);
@@ -1372,20 +1387,23 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkD
                     const float w = fmaf(-s, p.sih, -Dv);        // g - v/sigma
                     const float mg = -(Gh + Gl);                 // -g
                     const float r = fmaxf(w, mg);                // z-bar - g
-                    out[e] = fmaf(p.trs, r, p.rho * dd[e]);
+                    out[e] = !PAD || e < nval ? fmaf(p.trs, r, p.rho * dd[e]) : 0.f;   // pad columns stay 0
                     if constexpr (CHECK) {
-                        const float zb = (w > mg) ? ((Gh + Gl) + w) : 0.f;
-                        const float xb = fmaf(p.sf, Dv, s);
-                        const float dcol = rf - b.w;
-                        xo[e] = xb;
-                        const float mn = fminf(xb, zb);
-                        k32[0] = fmaf(r, r, k32[0]);
-                        k32[1] = fmaf(mn, mn, k32[1]);
-                        k32[2] = fmaf(xb, xb, k32[2]);
-                        k32[3] = fmaf(zb, zb, k32[3]);
-                        const float cq = dcol * dcol, pd = cq * dd[e];
-                        cd = df_add(cd, DF{pd, fmaf(cq, dd[e], -pd)});
-                        xacc[e] += xb;
+                        xo[e] = 0.f;
+                        if (!PAD || e < nval) {
+                            const float zb = (w > mg) ? ((Gh + Gl) + w) : 0.f;
+                            const float xb = fmaf(p.sf, Dv, s);
+                            const float dcol = rf - b.w;
+                            xo[e] = xb;
+                            const float mn = fminf(xb, zb);
+                            k32[0] = fmaf(r, r, k32[0]);
+                            k32[1] = fmaf(mn, mn, k32[1]);
+                            k32[2] = fmaf(xb, xb, k32[2]);
+                            k32[3] = fmaf(zb, zb, k32[3]);
+                            const float cq = dcol * dcol, pd = cq * dd[e];
+                            cd = df_add(cd, DF{pd, fmaf(cq, dd[e], -pd)});
+                            xacc[e] += xb;
+                        }
                     }
                     cacc[e] += out[e];
                 }
@@ -1400,9 +1418,9 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkD
         }
         // ---- tile epilogue: column and row sums as double-float pairs
         if (active) {
-            *reinterpret_cast<float4*>(&s_col[ro * S + c0]) = make_float4(cacc[0], cacc[1], cacc[2], cacc[3]);
+            *reinterpret_cast<float4*>(&s_col[ro * Sp + c0]) = make_float4(cacc[0], cacc[1], cacc[2], cacc[3]);
             if constexpr (CHECK)
-                *reinterpret_cast<float4*>(&s_xcol[ro * S + c0]) = make_float4(xacc[0], xacc[1], xacc[2], xacc[3]);
+                *reinterpret_cast<float4*>(&s_xcol[ro * Sp + c0]) = make_float4(xacc[0], xacc[1], xacc[2], xacc[3]);
         }
         __syncthreads();
         // the next tile's column values (thread 0 stored its descriptor while
@@ -1414,8 +1432,8 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkD
         for (int cc = tid; cc < S; cc += kThreads) {
             DF a{0.f, 0.f}, x{0.f, 0.f};
             for (int qq = 0; qq < P; ++qq) {
-                a = df_add(a, s_col[qq * S + cc]);
-                if constexpr (CHECK) x = df_add(x, s_xcol[qq * S + cc]);
+                a = df_add(a, s_col[qq * Sp + cc]);
+                if constexpr (CHECK) x = df_add(x, s_xcol[qq * Sp + cc]);
             }
             I.cs32[cbase + cc] = df_f(a);
             if constexpr (CHECK) I.xcs_part[cbase + cc] = df_val(x);
@@ -1480,8 +1498,8 @@ __device__ __forceinline__ void restart_tile(const HotInst& I, int slab, int ban
     using V = VecT<T>;
     constexpr int NV = V::N;
     constexpr bool F32 = std::is_same<T, float>::value;
-    const int S = g_side(I, slab), TR = I.TR;        // this slab's side
-    const int NC = S / NV;
+    const int S = g_side(I, slab), Sp = g_pitch(I, slab), TR = I.TR;   // this slab's side and row pitch
+    const int NC = Sp / NV;
     const int P = kThreads / NC;
     const int cg = threadIdx.x % NC, ro = threadIdx.x / NC;
     const bool active = ro < P;
@@ -1497,6 +1515,7 @@ __device__ __forceinline__ void restart_tile(const HotInst& I, int slab, int ban
     const double sig_old = (MODE == 1) ? I.ctl->sigma_old : I.ctl->sigma;
     const double sig_new = I.ctl->sigma;
     const int c0 = cg * NV;
+    const int nval = S - c0;                         // columns inside the slab (pad columns after)
     const int xb0 = g_xbase(I, slab);                // bin coordinates of this slab's half
     // sums that feed later iterations: FP64 (FP64 mode) or double-float (FP32 mode)
     double racc[2] = {0.0, 0.0};
@@ -1524,13 +1543,14 @@ __device__ __forceinline__ void restart_tile(const HotInst& I, int slab, int ban
         T xc[NV], bb[NV], db[NV];
 #pragma unroll
         for (int e = 0; e < NV; ++e) {
+            const bool v = e < nval;
             if constexpr (F32) {
-                bq[e] = ab32[S + c0 + e];
-                xc[e] = X32[c0 + e];
+                bq[e] = v ? ab32[S + c0 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
+                xc[e] = v ? X32[c0 + e] : 0.f;
             } else {
-                bb[e] = ab64[S + c0 + e];
-                db[e] = dab64[S + c0 + e];
-                xc[e] = X64[c0 + e];
+                bb[e] = v ? ab64[S + c0 + e] : 0.0;
+                db[e] = v ? dab64[S + c0 + e] : 0.0;
+                xc[e] = v ? X64[c0 + e] : 0.0;
             }
         }
         const float fsig = (float)sig_new;
@@ -1539,8 +1559,8 @@ __device__ __forceinline__ void restart_tile(const HotInst& I, int slab, int ban
 #pragma unroll 2
         for (int r = r0 + ro; r < r1; r += P) {
             T uu[NV], dd[NV], xbv[NV], zbv[NV], rv[NV];
-            V::ld(u + (size_t)r * S + c0, uu);
-            V::ld(d1 + (size_t)r * S + c0, dd);
+            V::ld(u + (size_t)r * Sp + c0, uu);
+            V::ld(d1 + (size_t)r * Sp + c0, dd);
             if constexpr (F32) {
                 const float4 a = ab32[r];
                 const float xrow = X32[r];
@@ -1562,10 +1582,13 @@ __device__ __forceinline__ void restart_tile(const HotInst& I, int slab, int ban
                     rv[e] = el.r;
                 }
             }
+#pragma unroll
+            for (int e = 0; e < NV; ++e)
+                if (e >= nval) xbv[e] = zbv[e] = rv[e] = T(0);   // pad columns: zero in every array
             if constexpr (MODE == 0) {
                 T xo[NV], zo[NV];
-                V::ld(xr + (size_t)r * S + c0, xo);
-                V::ld(zr + (size_t)r * S + c0, zo);
+                V::ld(xr + (size_t)r * Sp + c0, xo);
+                V::ld(zr + (size_t)r * Sp + c0, zo);
 #pragma unroll
                 for (int e = 0; e < NV; ++e) {
                     if constexpr (F32) {
@@ -1605,14 +1628,14 @@ __device__ __forceinline__ void restart_tile(const HotInst& I, int slab, int ban
                         ccol[e] += nu_[e];
                     }
                 }
-                V::st(u + (size_t)r * S + c0, nu_);
-                V::st(xr + (size_t)r * S + c0, xbv);
-                V::st(zr + (size_t)r * S + c0, zbv);
-                V::st(d0 + (size_t)r * S + c0, zero);
+                V::st(u + (size_t)r * Sp + c0, nu_);
+                V::st(xr + (size_t)r * Sp + c0, xbv);
+                V::st(zr + (size_t)r * Sp + c0, zbv);
+                V::st(d0 + (size_t)r * Sp + c0, zero);
                 if constexpr (F32) reinterpret_cast<float2*>(s_row)[(r - r0) * NC + cg] = df_st(rsf);
                 else s_row[(r - r0) * NC + cg] = rsd;
             } else {
-                V::st(xr + (size_t)r * S + c0, xbv);
+                V::st(xr + (size_t)r * Sp + c0, xbv);
             }
         }
     }
@@ -1644,8 +1667,8 @@ __device__ __forceinline__ void restart_tile(const HotInst& I, int slab, int ban
         if (active)
 #pragma unroll
             for (int e = 0; e < NV; ++e) {
-                if constexpr (F32) reinterpret_cast<float2*>(s_col)[ro * S + c0 + e] = df_st(fcol[e]);
-                else s_col[ro * S + c0 + e] = ccol[e];
+                if constexpr (F32) reinterpret_cast<float2*>(s_col)[ro * Sp + c0 + e] = df_st(fcol[e]);
+                else s_col[ro * Sp + c0 + e] = ccol[e];
             }
         __syncthreads();
         const size_t cbase = g_colp(I, slab, band);
@@ -1653,10 +1676,10 @@ __device__ __forceinline__ void restart_tile(const HotInst& I, int slab, int ban
             if constexpr (F32) {
                 const float2* sc = reinterpret_cast<const float2*>(s_col) + c;
                 DF a{0.f, 0.f};
-                for (int q = 0; q < P; ++q) a = df_add(a, df_ld(sc[(size_t)q * S]));
+                for (int q = 0; q < P; ++q) a = df_add(a, df_ld(sc[(size_t)q * Sp]));
                 I.cs0_part[cbase + c] = df_val(a);
             } else {
-                I.cs0_part[cbase + c] = sum_f64_strided(s_col + c, P, S);
+                I.cs0_part[cbase + c] = sum_f64_strided(s_col + c, P, Sp);
             }
             I.cs_part[cbase + c] = 0.0;
             I.cs32[cbase + c] = 0.f;
@@ -1730,8 +1753,8 @@ __global__ void __launch_bounds__(kThreads) k_init(HotInst I, double sigma0) {
     for (int t = blockIdx.x; t < g_ntiles(I); t += gridDim.x) {
         int slab, band;
         g_tile_slab(I, t, slab, band);
-        const int S = g_side(I, slab);                 // this slab's side
-        const int NC = S / NV;
+        const int S = g_side(I, slab), Sp = g_pitch(I, slab);   // this slab's side and row pitch
+        const int NC = Sp / NV;
         const int P = kThreads / NC;
         const int cg = threadIdx.x % NC, ro = threadIdx.x / NC;
         const bool active = ro < P;
@@ -1754,8 +1777,9 @@ __global__ void __launch_bounds__(kThreads) k_init(HotInst I, double sigma0) {
 #pragma unroll
                 for (int e = 0; e < NV; ++e) {
                     const int xb0 = g_xbase(I, slab);
-                    const double dc = I.X64[xb0 + r] - I.X64[xb0 + c0 + e];
-                    uu[e] = (T)(-sigma0 * (dc * dc * I.h));
+                    const bool v = c0 + e < S;                 // pad columns: 0
+                    const double dc = v ? I.X64[xb0 + r] - I.X64[xb0 + c0 + e] : 0.0;
+                    uu[e] = v ? (T)(-sigma0 * (dc * dc * I.h)) : T(0);
                     zero[e] = T(0);
                     if constexpr (std::is_same<T, float>::value) {
                         rsf = df_add(rsf, (float)uu[e]);
@@ -1768,10 +1792,10 @@ __global__ void __launch_bounds__(kThreads) k_init(HotInst I, double sigma0) {
                     }
                 }
                 if constexpr (std::is_same<T, float>::value) rs = df_val(rsf);
-                V::st((T*)I.u + off + (size_t)r * S + c0, uu);
-                V::st((T*)I.d0 + off + (size_t)r * S + c0, zero);
-                V::st((T*)I.xr + off + (size_t)r * S + c0, zero);
-                V::st((T*)I.zr + off + (size_t)r * S + c0, zero);
+                V::st((T*)I.u + off + (size_t)r * Sp + c0, uu);
+                V::st((T*)I.d0 + off + (size_t)r * Sp + c0, zero);
+                V::st((T*)I.xr + off + (size_t)r * Sp + c0, zero);
+                V::st((T*)I.zr + off + (size_t)r * Sp + c0, zero);
                 s_row[(r - r0) * NC + cg] = rs;
             }
         }
@@ -1781,10 +1805,10 @@ __global__ void __launch_bounds__(kThreads) k_init(HotInst I, double sigma0) {
         __syncthreads();
         if (active)
 #pragma unroll
-            for (int e = 0; e < NV; ++e) s_col[ro * S + c0 + e] = ccol[e];
+            for (int e = 0; e < NV; ++e) s_col[ro * Sp + c0 + e] = ccol[e];
         __syncthreads();
         const size_t cbase = g_colp(I, slab, band);
-        for (int c = threadIdx.x; c < S; c += blockDim.x) I.cs0_part[cbase + c] = sum_f64_strided(s_col + c, P, S);
+        for (int c = threadIdx.x; c < S; c += blockDim.x) I.cs0_part[cbase + c] = sum_f64_strided(s_col + c, P, Sp);
         for (int rr = threadIdx.x; rr < r1 - r0; rr += blockDim.x)
             I.rs0[g_row(I, slab) + r0 + rr] = sum_f64_strided(s_row + rr * NC, NC, 1);
         if constexpr (std::is_same<T, float>::value) {
@@ -2057,8 +2081,8 @@ LaunchDims make_launch_dims(int device, int fp64) {
         d.grid_vec = occ_grid(k_vec, sms, 0, 4);
         d.grid_vec1 = d.grid_vec;
     } else {
-        d.grid_tile = occ_grid(k_sweep32<false>, sms, kSweepSmem, 8);
-        d.grid_tile_chk = occ_grid(k_sweep32<true>, sms, kSweepSmemChk, 8);
+        d.grid_tile = occ_grid(k_sweep32<false, false>, sms, kSweepSmem, 8);
+        d.grid_tile_chk = occ_grid(k_sweep32<true, false>, sms, kSweepSmemChk, 8);
         d.grid_rst = std::min(occ_grid(k_restart<float, 0>, sms, 0, 8), occ_grid(k_restart<float, 1>, sms, 0, 8));
         d.grid_slab = occ_grid(k_anchor, sms, 0, 4);
         d.grid_alpha = occ_grid(k_alpha32<true>, sms, 0, 2);
@@ -2093,9 +2117,13 @@ void launch_init(const HotInst& I, double sigma0, cudaStream_t st) {
 
 cudaError_t kernels_init(int device) {
     (void)device;
-    cudaError_t e = cudaFuncSetAttribute(k_sweep32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSweepSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_sweep32<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSweepSmem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_sweep32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSweepSmemChk);
+        e = cudaFuncSetAttribute(k_sweep32<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSweepSmemChk);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_sweep32<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSweepSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_sweep32<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSweepSmemChk);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_marg, cudaFuncAttributeMaxDynamicSharedMemorySize, 7 * kMaxS * 8);
     return e;
 }
@@ -2128,13 +2156,13 @@ void launch_solve_kernels(const WorkDev* w, const LaunchDims& ld, int fp64, int 
     }
 }
 
-void launch_sweep(const WorkDev* w, const LaunchDims& ld, int fp64, int j, bool check, cudaStream_t st) {
+void launch_sweep(const WorkDev* w, const LaunchDims& ld, int fp64, int j, bool check, bool pad, cudaStream_t st) {
     if (fp64)
         launch(ld, k_sweep64, check ? ld.grid_tile_chk : ld.grid_tile, 0, st, w, j, check ? 1 : 0);
     else if (check)
-        launch(ld, k_sweep32<true>, ld.grid_tile_chk, kSweepSmemChk, st, w, j);
+        launch(ld, pad ? k_sweep32<true, true> : k_sweep32<true, false>, ld.grid_tile_chk, kSweepSmemChk, st, w, j);
     else
-        launch(ld, k_sweep32<false>, ld.grid_tile, kSweepSmem, st, w, j);
+        launch(ld, pad ? k_sweep32<false, true> : k_sweep32<false, false>, ld.grid_tile, kSweepSmem, st, w, j);
 }
 
 void launch_block_end(const WorkDev* w, const LaunchDims& ld, int fp64, int K, double a1, double a2, double a3,

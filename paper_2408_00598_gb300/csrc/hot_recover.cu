@@ -30,10 +30,12 @@ __host__ __device__ constexpr size_t recover_df_words(int m, int n) {
 // the same for k_recover, in doubles
 __host__ __device__ constexpr size_t recover_words(int m, int n) { return 2 * ((size_t)m + n) + 2; }
 
-// first entries of f1 row k of slab j and of f2 row j of slab k
-__device__ __forceinline__ size_t node_row_a(int m, int k, int j) { return ((size_t)j * m + k) * m; }
+// first entries of f1 row k of slab j and of f2 row j of slab k; a slab's
+// rows are stored at a pitch of its side rounded up to a multiple of 4
+__host__ __device__ constexpr int row_pitch(int side) { return (side + 3) & ~3; }
+__device__ __forceinline__ size_t node_row_a(int m, int k, int j) { return ((size_t)j * m + k) * row_pitch(m); }
 __device__ __forceinline__ size_t node_row_b(int m, int n, int k, int j) {
-    return (size_t)n * m * m + ((size_t)k * n + j) * n;
+    return (size_t)n * m * row_pitch(m) + ((size_t)k * n + j) * row_pitch(n);
 }
 
 template <typename T>
@@ -375,18 +377,22 @@ __global__ void k_marg_l1(const double* __restrict__ marg, const double* __restr
 
 // x-bar from the slab layout into the paper's vec order (eq. 4-6):
 // f1_{i,k,j} at i + m k + m^2 j (same as slab j, row k, col i);
-// f2_{k,j,l} at n m^2 + k + m j + m n l (slab n + k, row j, col l).
+// f2_{k,j,l} at n m^2 + k + m j + m n l (slab n + k, row j, col l); the
+// slab rows sit at their padded pitch.
 template <typename T>
 __global__ void k_export(const T* __restrict__ x, int m, int n, double* __restrict__ out) {
-    const size_t half = (size_t)m * m * n, nn = (size_t)n * n;
-    const size_t V = half + (size_t)m * nn;
+    const size_t half = (size_t)m * m * n;
+    const size_t V = half + (size_t)m * n * n;
+    const size_t mp = row_pitch(m), np = row_pitch(n);
+    // one thread per entry of the paper's order (coalesced writes)
     for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < V; q += (size_t)gridDim.x * blockDim.x) {
-        if (q < half) {
-            out[q] = (double)x[q];
-        } else {
-            const size_t p = q - half;            // internal f2 index: k n^2 + j n + l
-            const size_t k = p / nn, j = (p / n) % n, l = p % n;
-            out[half + k + (size_t)m * j + (size_t)m * n * l] = (double)x[q];
+        if (q < half) {                           // f1_{i,k,j} at i + m k + m^2 j: slab j, row k, column i
+            const size_t i = q % m, k = (q / m) % m, j = q / ((size_t)m * m);
+            out[q] = (double)x[(j * m + k) * mp + i];
+        } else {                                  // f2_{k,j,l} at k + m j + m n l: slab n + k, row j, column l
+            const size_t p = q - half;
+            const size_t k = p % m, j = (p / m) % n, l = p / ((size_t)m * n);
+            out[q] = (double)x[(size_t)n * m * mp + (k * n + j) * np + l];
         }
     }
 }

@@ -39,5 +39,6 @@ def test_autotune_picks_records_and_reloads(tmp_path):
 def test_autotune_rejects_bad_sizes():
     from paper_2408_00598_gb300 import hot
     with hot.Context(precision="fp32") as c:
-        with pytest.raises(hot.HotError):
-            c.autotune(6)
+        for S in (1, 1025):
+            with pytest.raises(hot.HotError):
+                c.autotune(S)

@@ -221,10 +221,9 @@ def test_invalid_inputs_are_rejected(lib, ctx32):
     bad /= bad.sum()
     nan = good1.copy()
     nan[3, 3] = np.nan
+    one = np.ones((1, 16)) / 16.0
     cases = [(bad, good2), (good1 * 1.01, good2), (nan, good2), (good1, good2[:, :12] / good2[:, :12].sum()),
-             (good1[:, :10] / good1[:, :10].sum(), good2[:, :10] / good2[:, :10].sum()),
-             (syn.make_pair("white", 6, 1)[0], syn.make_pair("white", 6, 1)[1]),
-             (syn.make_pair("white", 10, 1)[0], syn.make_pair("white", 10, 1)[1])]
+             (one, one.copy()), (one.T.copy(), one.T.copy())]   # a side of 1: no grid
     for a, b in cases:
         with pytest.raises(lib.HotError) as e:
             ctx32.solve(a, b)
