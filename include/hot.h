@@ -163,10 +163,13 @@ HOT_API int hot_solve(hot_ctx *ctx, const double *mu, const double *nu, int m, i
  *   xs: host, m doubles (coordinates of the row index i, k)
  *   ys: host, n doubles (coordinates of the column index j, l)
  *   xs = ys = NULL: the unit grid 0..m-1, 0..n-1 (as hot_solve).
- * FP32 bulk mode keeps its exact reduced-cost arithmetic only for integer
- * coordinates: it takes integers in [-2048, 2048] and returns HOT_EINVAL for
- * others (use HOT_FP64).  The cost is scaled by the power of two
- * 2^ceil(log2 max c); results are unscaled as for hot_solve. */
+ * Coordinates must be finite.  FP32 bulk mode forms the reduced cost exactly
+ * on the cost grid for integer coordinates in [-2048, 2048]; it solves
+ * eq. (1) with every coordinate rounded to FP32 (exact for integers up to
+ * 2^24, the results are those of the rounded positions), and for
+ * non-integer or larger coordinates forms the reduced cost and the
+ * objective's parts in double-float pairs, in a slower sweep.  The cost is scaled by the power of two 2^ceil(log2 max c); results
+ * are unscaled as for hot_solve. */
 HOT_API int hot_solve_coords(hot_ctx *ctx, const double *mu, const double *nu, int m, int n, int space,
                              const double *xs, const double *ys, double tol, long long max_iter, hot_result *out);
 

@@ -62,14 +62,6 @@ int set_coordinates(const double* xs, const double* ys, int m, int n, int fp64, 
                 set_error("coordinates must be finite");
                 return HOT_EINVAL;
             }
-        if (!fp64)
-            for (double x : v)
-                // FP32 mode forms h (x_r - x_c)^2 from x_r^2, x_c^2 and x_r x_c, exact
-                // on the grid 2^-E only for integer coordinates of modest size
-                if (x != std::rint(x) || std::fabs(x) > 2048.0) {
-                    set_error("FP32 bulk mode takes integer coordinates in [-2048, 2048]; use HOT_FP64 for others");
-                    return HOT_EINVAL;
-                }
     }
     return HOT_OK;
 }
@@ -241,12 +233,25 @@ int inst_create(const PairHost& p, int fp64, const hot_config& cfg, double tol, 
     d.gadmm = cfg.method == HOT_METHOD_GADMM ? 1 : 0;
     d.stop_abs = cfg.stop_rule == HOT_STOP_ABSOLUTE ? 1 : 0;
     d.relax = cfg.relaxation;
+    // FP32 mode: integer coordinates of modest size keep the reduced cost
+    // exact on the grid 2^-E; others (and FP64 mode never needs it) take the
+    // pair arithmetic of the general sweep
+    d.coord_real = 0;
+    if (!fp64)
+        for (const std::vector<double>* v : {&p.xs, &p.ys})
+            for (double x : *v)
+                if (x != std::rint(x) || std::fabs(x) > 2048.0) d.coord_real = 1;
     // bin coordinates: X[0, m) are the row coordinates (i, k) that the f1
     // slabs' cost uses, X[m, m + n) the column coordinates (j, l) of the f2
     // slabs; default 0, 1, ...
     std::vector<double> X((size_t)NS);
     for (int r = 0; r < m; ++r) X[r] = p.xs.empty() ? (double)r : p.xs[r];
     for (int r = 0; r < n; ++r) X[m + r] = p.ys.empty() ? (double)r : p.ys[r];
+    // FP32 mode solves eq. (1) with the positions rounded to FP32 (exact for
+    // integers up to 2^24): the cost scale, ||c||, C(x) and every cost the
+    // kernels form all come from the same rounded positions
+    if (!fp64)
+        for (double& x : X) x = (double)(float)x;
     const int hb[3] = {0, m, m + n};
     // power-of-two cost scale: smallest 2^E >= max c (E = 0 for a zero cost)
     double cmax = 0.0;
@@ -361,8 +366,8 @@ int inst_create(const PairHost& p, int fp64, const hot_config& cfg, double tol, 
     if (ee == cudaSuccess) ee = cudaMemcpyAsync(d.rowmu2, rm.data(), m * 8, cudaMemcpyHostToDevice, st);
     if (ee == cudaSuccess) ee = cudaMemcpyAsync(d.ctl, &I->ctl_host, sizeof(HotCtl), cudaMemcpyHostToDevice, st);
     {
-        // coordinates (FP32 copies are exact: FP32 mode takes integer coordinates)
-        // and the row cost sums C(x) as double-float pairs
+        // coordinates (FP32 mode: already rounded, so the FP32 copies are
+        // exact) and the row cost sums C(x) as double-float pairs
         std::vector<float> x32(X.begin(), X.end());
         std::vector<float2> cs2(csum.size());
         for (size_t q = 0; q < csum.size(); ++q) {
@@ -490,7 +495,7 @@ int Batch::set_instances(const std::vector<Inst*>& v, cudaStream_t st) {
     // (launch_solve_kernels), and padded slab rows a sweep variant of their
     // own: a change of either needs new graphs
     pad = 0;
-    for (const Inst* I : v) pad |= (I->m % 4 != 0) || (I->n % 4 != 0);
+    for (const Inst* I : v) pad |= (I->m % 4 != 0) || (I->n % 4 != 0) || I->desc.coord_real;
     if ((single >= 0 && single != (v.size() == 1 ? 1 : 0)) || (pad_captured >= 0 && pad_captured != pad))
         drop_graphs();
     // the pinned staging is rewritten here: wait for earlier copies out of it

@@ -101,7 +101,8 @@ struct Batch {
     LaunchDims ld{};
     int ninst = 0;
     int single = -1;                // the instance count the graphs were captured for is 1 (1), more (0), none (-1)
-    int pad = 0;                    // some instance of the tables has a side that is not a multiple of 4
+    int pad = 0;                    // some instance needs the general sweep: a side that is not a
+                                    // multiple of 4, or (FP32) real-valued bin coordinates
     int pad_captured = -1;          // pad of the captured graphs
     void drop_graphs();
     ~Batch();

@@ -103,6 +103,8 @@ struct HotInst {
     int fp64;              // 1: FP64 state, 0: FP32 anchor + delta
     int gadmm;             // 1: Step 4 of the generalized ADMM instead of Halpern's
     int stop_abs;          // 1: stop on the absolute KKT residual
+    int coord_real;        // FP32 mode: some bin coordinate is not an integer in [-2048, 2048], so the
+                           // pieces carry h x^2 - alpha as pairs and the sweep forms the cost term in pairs
     double relax;          // rho of the generalized ADMM
     double h;              // 2^-E
     double norm_b;         // ||b||

@@ -176,6 +176,46 @@ __device__ __forceinline__ P64 make_p64(double sigma, int k, double h, int gadmm
     return p;
 }
 
+// (x_r - x_c)^2 of two FP32 coordinates as a pair (the difference exact by a
+// two-sum, its square by fma), and a product with an FP32 value as a pair:
+// the objective's parts in FP32 mode with real-valued coordinates.
+__device__ __forceinline__ DF cost_pair(float xr, float xc) {
+    const float d = xr - xc;
+    const float bv = d - xr;
+    const float de = (xr - (d - bv)) + (-xc - bv);          // two-sum error of xr + (-xc)
+    const float c = d * d;
+    return DF{c, fmaf(d, d, -c) + 2.f * d * de};
+}
+__device__ __forceinline__ DF cost_times(DF c, float v) {
+    const float p = c.hi * v;
+    return DF{p, fmaf(c.hi, v, -p) + c.lo * v};
+}
+
+// The reduced cost g = c - alpha_r - beta_c of an element as an unevaluated
+// pair (Gh, Gl), from its row piece a and column piece b.  Integer
+// coordinates: Gh = h (x_r - x_c)^2 - alpha_hi - beta_hi is exact on the grid
+// 2^-E, Gl = -(alpha_lo + beta_lo).  Real coordinates (pieces P_r, Q_c as
+// pairs): g = P_r + Q_c - 2 h x_r x_c by two exact two-sums and the product's
+// fma error.
+__device__ __forceinline__ void reduced_cost(const float4& a, const float4& b, float h, int coord_real, float& Gh,
+                                             float& Gl) {
+    const float m2hr = -2.f * h * a.w;                       // exact
+    if (coord_real) {
+        const float t = a.x + b.x;
+        const float tb = t - a.x;
+        const float te = (a.x - (t - tb)) + (b.x - tb);      // two-sum error of P_hi + Q_hi
+        const float ph = m2hr * b.w;
+        const float pe = fmaf(m2hr, b.w, -ph);               // exact error of the product
+        Gh = t + ph;
+        const float sb = Gh - t;
+        const float se = (t - (Gh - sb)) + (ph - sb);        // two-sum error of t + ph
+        Gl = se + ((te + pe) + (a.y + b.y));
+    } else {
+        Gh = fmaf(m2hr, b.w, fmaf(a.w * a.w, h, -a.x) + fmaf(b.w * b.w, h, -b.x));
+        Gl = -(a.y + b.y);
+    }
+}
+
 // Element math of Steps 2-3.  Inputs: anchor u, delta d, cost cq = (r-c)^2
 // (unscaled integer), the slab row/column pieces of A^T y-bar (hi, lo) and of
 // dA = A^T(y-bar - y0).  Outputs: w = g - v/sigma, mg = -g and
@@ -183,10 +223,15 @@ __device__ __forceinline__ P64 make_p64(double sigma, int k, double h, int gadmm
 struct E32 {
     float Gh, Gl, D, s, w, mg, r;
 };
-__device__ __forceinline__ E32 elem32(float u, float d, float cq, const float4& a, const float4& b, const P32& p) {
+__device__ __forceinline__ E32 elem32(float u, float d, float cq, const float4& a, const float4& b, const P32& p,
+                                      int coord_real = 0) {
     E32 e;
-    e.Gh = fmaf(cq, p.h, -a.x) - b.x;       // exact: every term is on the grid 2^-E
-    e.Gl = -(a.y + b.y);
+    if (coord_real) {
+        reduced_cost(a, b, p.h, 1, e.Gh, e.Gl);
+    } else {
+        e.Gh = fmaf(cq, p.h, -a.x) - b.x;   // exact: every term is on the grid 2^-E
+        e.Gl = -(a.y + b.y);
+    }
     e.D = a.z + b.z;                        // A^T (y-bar - y0)
     e.s = u + d;
     e.w = fmaf(-e.s, p.sih, -e.D);          // g - v/sigma
@@ -637,12 +682,22 @@ __device__ __forceinline__ DF piece_dv(const HotInst& I, const PieceK& K, int sl
 // The float4 the sweep reads for a piece: the full piece A^T y-bar = anchor +
 // dv split into a part on the cost grid 2^-E (hi, so that c - hi_r - hi_c is
 // exact in FP32) and an FP32 remainder, then dv itself, then the bin
-// coordinate of the piece's row or column.
-__device__ __forceinline__ float4 piece_pack(const PieceIn& a, DF dv, const PieceK& K) {
+// coordinate of the piece's row or column.  With real-valued coordinates
+// (coord_real) the first two are instead the pair h x^2 - (anchor + dv), the
+// piece's share of the separable cost h (x_r - x_c)^2 = h x_r^2 + h x_c^2 -
+// 2 h x_r x_c less the piece itself (x^2 exact as a pair by fma; h a power of 2).
+__device__ __forceinline__ float4 piece_pack(const PieceIn& a, DF dv, const PieceK& K, int coord_real) {
     const float df = df_f(dv);
+    if (coord_real) {
+        const float x2 = a.xc * a.xc;
+        const DF hx2{x2 * K.igrid, fmaf(a.xc, a.xc, -x2) * K.igrid};
+        const DF P = df_sub(hx2, df_add(DF{a.a0.x, a.a0.y}, dv));
+        return make_float4(P.hi, P.lo, df, a.xc);
+    }
     const float dh = rintf(df * K.grid) * K.igrid;
     return make_float4(a.a0.x + dh, a.a0.y + (df - dh), df, a.xc);
 }
+
 
 // The instance-wide O(m + n) stage of Prop. 3: from T1, T2, P1, P2 (k_vec32)
 // the vectors
@@ -953,7 +1008,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_alpha32(const WorkDev* __restri
             const bool col = idx >= Ls;
             const size_t o = 2 * g_row(I, slab) + idx;
             dab2[o] = df_st(dv);
-            ab32[o] = piece_pack(a, dv, K);
+            ab32[o] = piece_pack(a, dv, K, I.coord_real);
             if (CHECK) {
                 const DF full = df_add(DF{a.a0.x, a.a0.y}, dv);
                 ymax = fmaxf(ymax, fabsf(full.hi));
@@ -1342,11 +1397,14 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkD
         const bool active = ro < P;
         const int c0 = cg * NV;
         const int nval = PAD ? S - c0 : NV;       // columns of this thread's group inside the slab (pad after)
+        const int cr = PAD ? I.coord_real : 0;    // real-valued coordinates (general variant only)
         const float h = p.h;
+        if (!cr) {
 #pragma unroll
-        for (int e = 0; e < NV; ++e) {
-            const float cf = bq[e].w;                          // column coordinate x_c
-            bq[e] = make_float4(fmaf(cf * cf, h, -bq[e].x), bq[e].y, bq[e].z, cf);
+            for (int e = 0; e < NV; ++e) {
+                const float cf = bq[e].w;                      // column coordinate x_c
+                bq[e] = make_float4(fmaf(cf * cf, h, -bq[e].x), bq[e].y, bq[e].z, cf);
+            }
         }
         const float4* sa = s_alpha[ck % kStages];
         float* __restrict__ dout = (float*)((j & 1) ? I.d0 : I.d1) + dc.elem + ((size_t)r0 + ro) * Sp + c0;
@@ -1380,8 +1438,13 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkD
 #pragma unroll
                 for (int e = 0; e < NV; ++e) {
                     const float4 b = bq[e];
-                    const float Gh = fmaf(m2hr, b.w, Ar + b.x);   // h (x_r-x_c)^2 - alpha_hi - beta_hi
-                    const float Gl = -(a.y + b.y);
+                    float Gh, Gl;
+                    if (PAD && cr) {
+                        reduced_cost(a, b, h, 1, Gh, Gl);          // pieces h x^2 - alpha, h x^2 - beta as pairs
+                    } else {
+                        Gh = fmaf(m2hr, b.w, Ar + b.x);            // h (x_r-x_c)^2 - alpha_hi - beta_hi
+                        Gl = -(a.y + b.y);
+                    }
                     const float Dv = a.z + b.z;                  // A^T (y-bar - y0)
                     const float s = uu[e] + dd[e];
                     const float w = fmaf(-s, p.sih, -Dv);        // g - v/sigma
@@ -1400,8 +1463,12 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkD
                             k32[1] = fmaf(mn, mn, k32[1]);
                             k32[2] = fmaf(xb, xb, k32[2]);
                             k32[3] = fmaf(zb, zb, k32[3]);
-                            const float cq = dcol * dcol, pd = cq * dd[e];
-                            cd = df_add(cd, DF{pd, fmaf(cq, dd[e], -pd)});
+                            if (PAD && cr) {
+                                cd = df_add(cd, cost_times(cost_pair(rf, b.w), dd[e]));
+                            } else {
+                                const float cq = dcol * dcol, pd = cq * dd[e];
+                                cd = df_add(cd, DF{pd, fmaf(cq, dd[e], -pd)});
+                            }
                             xacc[e] += xb;
                         }
                     }
@@ -1516,6 +1583,7 @@ __device__ __forceinline__ void restart_tile(const HotInst& I, int slab, int ban
     const double sig_new = I.ctl->sigma;
     const int c0 = cg * NV;
     const int nval = S - c0;                         // columns inside the slab (pad columns after)
+    const int cr = F32 ? I.coord_real : 0;           // real-valued coordinates: the cost term in pairs
     const int xb0 = g_xbase(I, slab);                // bin coordinates of this slab's half
     // sums that feed later iterations: FP64 (FP64 mode) or double-float (FP32 mode)
     double racc[2] = {0.0, 0.0};
@@ -1567,7 +1635,7 @@ __device__ __forceinline__ void restart_tile(const HotInst& I, int slab, int ban
 #pragma unroll
                 for (int e = 0; e < NV; ++e) {
                     const float dc = xrow - xc[e];
-                    const E32 el = elem32(uu[e], dd[e], dc * dc, a, bq[e], p32);
+                    const E32 el = elem32(uu[e], dd[e], dc * dc, a, bq[e], p32, cr);
                     xz32(el, p32, xbv[e], zbv[e]);
                     rv[e] = el.r;
                 }
@@ -1620,9 +1688,13 @@ __device__ __forceinline__ void restart_tile(const HotInst& I, int slab, int ban
                         rsf = df_add(rsf, (float)nu_[e]);
                         fcol[e] = df_add(fcol[e], (float)nu_[e]);
                         // <c, u>: (r-c)^2 u exactly as a pair (the integer cost is exact in FP32)
-                        const float dc = X32[r] - xc[e], cq = dc * dc;
-                        const float p = cq * (float)nu_[e];
-                        fr[0] = df_add(fr[0], DF{p, fmaf(cq, (float)nu_[e], -p)});
+                        if (cr) {
+                            fr[0] = df_add(fr[0], cost_times(cost_pair(X32[r], xc[e]), (float)nu_[e]));
+                        } else {
+                            const float dc = X32[r] - xc[e], cq = dc * dc;
+                            const float p = cq * (float)nu_[e];
+                            fr[0] = df_add(fr[0], DF{p, fmaf(cq, (float)nu_[e], -p)});
+                        }
                     } else {
                         rsd += nu_[e];
                         ccol[e] += nu_[e];
@@ -1691,7 +1763,10 @@ __device__ __forceinline__ void restart_tile(const HotInst& I, int slab, int ban
             const double a0 = I.ab0[o + idx] + (F32 ? df_val(df_ld(I.dab2[o + idx])) : I.dab64[o + idx]);
             I.ab0[o + idx] = a0;
             if (I.ab0_32) {
-                const double hi = rint(a0 * ih) * I.h;           // on the grid 2^-E
+                // integer coordinates: hi on the grid 2^-E (the reduced cost is then
+                // exact in FP32); real ones form it in pairs and take a plain
+                // double-float split, whose lo part keeps 2^-24 of hi, not of 2^-E
+                const double hi = I.coord_real ? (double)(float)a0 : rint(a0 * ih) * I.h;
                 I.ab0_32[o + idx] = make_float2((float)hi, (float)(a0 - hi));
             }
         };
@@ -1784,8 +1859,13 @@ __global__ void __launch_bounds__(kThreads) k_init(HotInst I, double sigma0) {
                     if constexpr (std::is_same<T, float>::value) {
                         rsf = df_add(rsf, (float)uu[e]);
                         fcol[e] = df_add(fcol[e], (float)uu[e]);
-                        const float cq = (float)(dc * dc), p = cq * (float)uu[e];
-                        cuf = df_add(cuf, DF{p, fmaf(cq, (float)uu[e], -p)});   // <c, u>
+                        if (I.coord_real) {                                     // <c, u> with the FP32 positions
+                            const float* X32 = I.X32 + xb0;
+                            if (v) cuf = df_add(cuf, cost_times(cost_pair(X32[r], X32[c0 + e]), (float)uu[e]));
+                        } else {
+                            const float cq = (float)(dc * dc), p = cq * (float)uu[e];
+                            cuf = df_add(cuf, DF{p, fmaf(cq, (float)uu[e], -p)});   // <c, u>
+                        }
                     } else {
                         rs += (double)uu[e];
                         ccol[e] += (double)uu[e];

@@ -2,7 +2,8 @@
 bin (i, j) to (k, l) is (xs_i - xs_k)^2 + (ys_j - ys_l)^2 (eq. 1 with the
 bins' own positions, as colour and point-cloud data have).  Checked against
 the FP64 oracle run on the same coordinates (iterates in FP64 mode, values in
-FP32 mode with integer coordinates) and against the exact LP."""
+FP32 mode with integer and with real-valued coordinates) and against the
+exact LP."""
 import numpy as np
 import pytest
 
@@ -82,10 +83,55 @@ def test_unit_coordinates_equal_the_plain_solve(hot):
     assert a["ot_value"] == b["ot_value"] and a["iters"] == b["iters"]
 
 
-def test_fp32_rejects_non_integer_coordinates(hot):
+@pytest.mark.parametrize("m,n,kind,seed", [(16, 16, "white", 11), (24, 24, "gauss", 12), (13, 19, "shapes", 13)])
+def test_fp32_real_coordinates_match_oracle(hot, m, n, kind, seed):
+    """Real-valued bin positions (sorted U(0, 1), as colour or point-cloud bins
+    have; App. E-G) in FP32 bulk mode: the reduced cost and the objective's
+    parts are formed in pairs.  FP32 mode solves eq. (1) with the positions
+    rounded to FP32, so the FP64 oracle runs on those rounded positions; at
+    the paper's stopping rule: the dual to 1e-6, the primal to 1e-6 of
+    sum |c x-bar|, iterations within a check or two."""
+    from oracle import reduced_model as rm
+    rng = np.random.default_rng(seed)
+    xs, ys = np.sort(rng.uniform(0.0, 1.0, m)), np.sort(rng.uniform(0.0, 1.0, n))
+    mu1, mu2 = syn.make_pair(kind, m, seed, n=n)
+    r32 = lambda v: v.astype(np.float32).astype(np.float64)
+    with hot.Context(precision="fp32") as ctx:
+        r = ctx.solve(mu1, mu2, tol=1e-6, max_iter=100000, xs=xs, ys=ys)
+        x = ctx.flows(r)
+        ctx.release(r)
+    xs, ys = r32(xs), r32(ys)
+    ref = ohot.hot_solve(mu1, mu2, tol=1e-6, max_iter=100000, xs=xs, ys=ys)
+    assert r["status"] == 0 and r["rel_kkt"] <= 1e-6
+    assert abs(r["iters"] - ref.iters) <= max(20, 0.01 * ref.iters), (r["iters"], ref.iters)
+    if r["iters"] != ref.iters:
+        ref = ohot.hot_solve(mu1, mu2, tol=0.0, max_iter=r["iters"], xs=xs, ys=ys)
+    assert abs(r["dual_value"] - ref.dual_value) <= 1e-6 * abs(ref.dual_value)
+    cx = float(np.abs(rm.build_c(m, n, xs, ys) * x).sum())
+    assert abs(r["ot_value"] - ref.ot_value) <= 1e-6 * max(cx, abs(ref.ot_value))
+
+
+def test_fp32_real_coordinates_against_exact_lp(hot):
+    """A tight stopping rule: both objectives at the exact optimum of eq. (1)
+    with real-valued positions, rounded to FP32 as FP32 mode solves it."""
+    S = 8
+    rng = np.random.default_rng(21)
+    xs, ys = np.sort(rng.uniform(0.0, 3.0, S)), np.sort(rng.uniform(0.0, 3.0, S))
+    mu1, mu2 = syn.make_pair("white", S, 21)
+    ex = exact.ot_exact_lp(mu1, mu2, xs.astype(np.float32).astype(np.float64),
+                           ys.astype(np.float32).astype(np.float64))
+    with hot.Context(precision="fp32") as ctx:
+        r = ctx.solve(mu1, mu2, tol=5e-9, max_iter=400000, xs=xs, ys=ys)
+        ctx.release(r)
+    assert r["status"] == 0
+    assert abs(r["dual_value"] - ex) <= 1e-6 * ex
+    assert abs(r["ot_value"] - ex) <= 2e-6 * ex
+
+
+def test_coordinates_must_be_finite(hot):
     S = 8
     mu1, mu2 = syn.make_pair("white", S, 1)
     with hot.Context(precision="fp32") as ctx:
         with pytest.raises(hot.HotError) as e:
-            ctx.solve(mu1, mu2, xs=np.linspace(0, 1, S), ys=np.arange(S, dtype=float))
+            ctx.solve(mu1, mu2, xs=np.array([0.0] * (S - 1) + [np.inf]), ys=np.arange(S, dtype=float))
     assert e.value.status == hot.HOT_EINVAL
