@@ -268,22 +268,22 @@ template <> struct VecT<float> {
     using type = float4;
     static constexpr int N = 4;
     __device__ static void ld(const float* p, float (&x)[4]) {
-        const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+        const float4 t = __ldcs(reinterpret_cast<const float4*>(p));
         x[0] = t.x; x[1] = t.y; x[2] = t.z; x[3] = t.w;
     }
     __device__ static void st(float* p, const float (&x)[4]) {
-        *reinterpret_cast<float4*>(p) = make_float4(x[0], x[1], x[2], x[3]);
+        __stcs(reinterpret_cast<float4*>(p), make_float4(x[0], x[1], x[2], x[3]));
     }
 };
 template <> struct VecT<double> {
     using type = double2;
     static constexpr int N = 2;
     __device__ static void ld(const double* p, double (&x)[2]) {
-        const double2 t = __ldg(reinterpret_cast<const double2*>(p));
+        const double2 t = __ldcs(reinterpret_cast<const double2*>(p));
         x[0] = t.x; x[1] = t.y;
     }
     __device__ static void st(double* p, const double (&x)[2]) {
-        *reinterpret_cast<double2*>(p) = make_double2(x[0], x[1]);
+        __stcs(reinterpret_cast<double2*>(p), make_double2(x[0], x[1]));
     }
 };
 
@@ -293,6 +293,10 @@ template <> struct VecT<double> {
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async16_ef(void* smem, const void* gmem, unsigned long long pol) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "l"(pol) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
@@ -329,12 +333,21 @@ __device__ __forceinline__ bool resolve_tile(const WorkDev* __restrict__ W, int 
     return true;
 }
 
+// Programmatic dependent launch: the kernels of the iteration chain are
+// launched with programmatic stream serialisation, so the launch of a kernel
+// is prepared while its predecessor runs.  Each one first waits for the
+// predecessor grid to complete and its memory to be visible (everything
+// below then sees stream order).  No kernel triggers its successor early:
+// CTAs placed ahead of time and left waiting cost more than they saved.
+__device__ __forceinline__ void pdl_enter() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+
 // ----------------------------------------------------------------- k_vec --
 // T1[j] = sum_k rowsum(f1 slab j)[k] (j < n), T2[k] = sum_j rowsum(f2 slab k)[j]
 // (k < m), P1[k] = sum_j rowsum(f1 slab j)[k], P2[j] = sum_k rowsum(f2 slab k)[j];
 // row sums are those of u + d (the slab sums of u are kept separately).  One
 // warp per output; outputs at vecs[which * L + index], L = max(m, n).
 __global__ void __launch_bounds__(kThreads) k_vec(const WorkDev* __restrict__ W) {
+    pdl_enter();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ninst = W->ninst;
     const int nitems = W->pre_vec[ninst];
@@ -392,6 +405,7 @@ __global__ void __launch_bounds__(kThreads) k_vec(const WorkDev* __restrict__ W)
 // k_alpha (one CTA per slab) then forms the slab's entries with products only
 // (FP64 division is slow on this part; reciprocals are taken once).
 __global__ void __launch_bounds__(kThreads) k_marg(const WorkDev* __restrict__ W) {
+    pdl_enter();
     extern __shared__ double sv[];                   // 7 L: T1 T2 P1 P2 colmu1 rowmu2, then s
     __shared__ double s_red[4 * 32];
     const int ninst = W->ninst;
@@ -473,6 +487,7 @@ __global__ void __launch_bounds__(kThreads) k_marg(const WorkDev* __restrict__ W
 // k_anchor; here only the delta's sums enter.
 template <bool CHECK>
 __global__ void __launch_bounds__(kThreads) k_alpha(const WorkDev* __restrict__ W) {
+    pdl_enter();
     __shared__ double s_red[4 * 32];
     __shared__ float s_max[32];
     __shared__ int s_t[4];
@@ -823,6 +838,7 @@ __device__ void alpha32_stage(const HotInst& I, float2* __restrict__ sq, float2*
 // since there every item would pay the count's atomic and barriers.
 template <bool SINGLE>
 __global__ void __launch_bounds__(kThreads) k_vec32(const WorkDev* __restrict__ W, int j) {
+    pdl_enter();
     constexpr int kW = kThreads / 32;
     constexpr int kRW = kVecRows / kW;               // rows per warp in a P item
     __shared__ float2 s_p[kThreads];
@@ -939,6 +955,7 @@ __global__ void __launch_bounds__(kThreads) k_vec32(const WorkDev* __restrict__ 
 // last k_vec32 item cost every item an atomic and a barrier, which batches of
 // many small instances paid many times over.)
 __global__ void __launch_bounds__(kThreads) k_stage32(const WorkDev* __restrict__ W, int j) {
+    pdl_enter();
     __shared__ float2 s_red[2 * 32];
     const int ninst = W->ninst;
     for (int i = blockIdx.x; i < ninst; i += gridDim.x) {
@@ -963,6 +980,7 @@ __global__ void __launch_bounds__(kThreads) k_stage32(const WorkDev* __restrict_
 // k_check adds them in order).
 template <bool CHECK>
 __global__ void __launch_bounds__(kThreads, 2) k_alpha32(const WorkDev* __restrict__ W, int j) {
+    pdl_enter();
     __shared__ float2 s_red[2 * 32];
     __shared__ float s_max[32];
     const int ninst = W->ninst;
@@ -1080,6 +1098,7 @@ __device__ __forceinline__ void anchor_slab(const HotInst& I, int slab, double s
 }
 
 __global__ void __launch_bounds__(kThreads) k_anchor(const WorkDev* __restrict__ W) {
+    pdl_enter();
     __shared__ int s_t[4];
     const int ninst = W->ninst;
     const int nslab = W->pre_slab[ninst];
@@ -1110,6 +1129,7 @@ __global__ void __launch_bounds__(kThreads) k_anchor_one(HotInst I, double sigma
 // FP64 mode: Steps 2-4 of Algorithm 2 on one tile (TR rows of one slab) per
 // loop trip.
 __global__ void __launch_bounds__(kThreads, 2) k_sweep64(const WorkDev* __restrict__ W, int j, int check) {
+    pdl_enter();
     constexpr int NV = 2;
     constexpr int kRowN = kRowSmemBytes / sizeof(double) + 256;
     __shared__ __align__(16) double s_row[kRowN];
@@ -1284,6 +1304,7 @@ __device__ __forceinline__ TileD tile_desc(const WorkDev* __restrict__ W, int t,
 // variant of its own: the masks cost the unpadded sweep registers).
 template <bool CHECK, bool PAD>
 __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkDev* __restrict__ W, int j) {
+    pdl_enter();
     constexpr int NV = 4;
     constexpr int kW = kThreads / 32;
     constexpr int kRowN = kRowSmemBytes / sizeof(float) + 256;
@@ -1339,14 +1360,16 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkD
         }
     };
     c.ik = 0;
+    unsigned long long pol_ef;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(pol_ef));
     set_tile(blockIdx.x);
     // one commit group per call: the copies of global pass n (ring slot n % kStages)
     auto issue = [&](int n) {
         if (c.it < ntiles) {
             if (c.mine > 0) {
                 float4* su = s_stage + (size_t)(n % kStages) * 2 * kThreads + tid;
-                cp_async16(su, c.u);
-                cp_async16(su + kThreads, c.d);
+                cp_async16_ef(su, c.u, pol_ef);
+                cp_async16_ef(su + kThreads, c.d, pol_ef);
                 --c.mine;
             }
             if (c.acopy) {
@@ -1416,10 +1439,10 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkD
 #pragma unroll
         for (int e = 0; e < NV; ++e) cacc[e] = xacc[e] = 0.f;
         // KKT partials: FP32 chains of at most 64 terms per thread and tile
-        // (a tile has TR * S / 1024 <= 16 passes), summed over the CTA in pairs;
-        // the objective's share <c, d> (k32[4] unused) as exact products in a pair
-        float k32[kNK] = {0.f, 0.f, 0.f, 0.f, 0.f};
-        DF cd{0.f, 0.f};
+        // (a tile has TR * S / 1024 <= 16 passes), summed over the CTA in pairs.
+        // The objective's share <c, d> is not formed here: it only reports the
+        // value, so the pass that ends an instance forms it once (MODE 2)
+        float k32[kNK - 1] = {0.f, 0.f, 0.f, 0.f};
         int rr = ro;                              // this thread's row, relative to r0
 #pragma unroll 1
         for (int q = 0; q < dc.npass; ++q, ++n) {
@@ -1456,25 +1479,18 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkD
                         if (!PAD || e < nval) {
                             const float zb = (w > mg) ? ((Gh + Gl) + w) : 0.f;
                             const float xb = fmaf(p.sf, Dv, s);
-                            const float dcol = rf - b.w;
                             xo[e] = xb;
                             const float mn = fminf(xb, zb);
                             k32[0] = fmaf(r, r, k32[0]);
                             k32[1] = fmaf(mn, mn, k32[1]);
                             k32[2] = fmaf(xb, xb, k32[2]);
                             k32[3] = fmaf(zb, zb, k32[3]);
-                            if (PAD && cr) {
-                                cd = df_add(cd, cost_times(cost_pair(rf, b.w), dd[e]));
-                            } else {
-                                const float cq = dcol * dcol, pd = cq * dd[e];
-                                cd = df_add(cd, DF{pd, fmaf(cq, dd[e], -pd)});
-                            }
                             xacc[e] += xb;
                         }
                     }
                     cacc[e] += out[e];
                 }
-                *reinterpret_cast<float4*>(dout) = make_float4(out[0], out[1], out[2], out[3]);
+                __stcs(reinterpret_cast<float4*>(dout), make_float4(out[0], out[1], out[2], out[3]));
                 *srow = (out[0] + out[1]) + (out[2] + out[3]);
                 if constexpr (CHECK) *sxrow = (xo[0] + xo[1]) + (xo[2] + xo[3]);
             }
@@ -1521,15 +1537,14 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkD
             }
         }
         if constexpr (CHECK) {
-            DF kd[kNK];
+            DF kd[kNK - 1];
 #pragma unroll
             for (int qq = 0; qq < kNK - 1; ++qq) kd[qq] = DF{k32[qq], 0.f};
-            kd[kNK - 1] = cd;
-            block_sum_df<kNK>(kd, s_red);        // its barriers also publish s_rdf
+            block_sum_df<kNK - 1>(kd, s_red);    // its barriers also publish s_rdf
             if (tid == 0) {
                 float2* o = reinterpret_cast<float2*>(I.tile_kkt) + (size_t)dc.tile * kNK;
 #pragma unroll
-                for (int qq = 0; qq < kNK; ++qq) o[qq] = df_st(kd[qq]);
+                for (int qq = 0; qq < kNK - 1; ++qq) o[qq] = df_st(kd[qq]);
             }
         } else {
             __syncthreads();
@@ -1557,7 +1572,9 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkD
 //         u = v0 - sigma_new g-bar = x-bar + sigma_new r (r = z-bar - g-bar);
 //         (x_r, z_r) = (x-bar, z-bar); delta = 0; FP64 slab sums of u;
 //         A^T y0 pieces <- those of y-bar.
-// MODE 2: x-bar of the final check iteration into x_r (the solution).
+// MODE 2: x-bar of the final check iteration into x_r (the solution), and
+//         (FP32 mode) the tile's share of <c, d> of that iteration, which
+//         completes the reported objective (k_block_end).
 // The check iteration (index K-1, odd) read delta buffer d1.
 template <typename T, int MODE>
 __device__ __forceinline__ void restart_tile(const HotInst& I, int slab, int band, double* s_row, double* s_col,
@@ -1708,6 +1725,21 @@ __device__ __forceinline__ void restart_tile(const HotInst& I, int slab, int ban
                 else s_row[(r - r0) * NC + cg] = rsd;
             } else {
                 V::st(xr + (size_t)r * Sp + c0, xbv);
+                if constexpr (F32) {
+                    // <c, d> of the final check iteration: (r-c)^2 d exactly as a pair
+                    // (real-valued coordinates: the cost itself as a pair)
+#pragma unroll
+                    for (int e = 0; e < NV; ++e) {
+                        if (e >= nval) continue;
+                        if (cr) {
+                            fr[0] = df_add(fr[0], cost_times(cost_pair(X32[r], xc[e]), (float)dd[e]));
+                        } else {
+                            const float dc = X32[r] - xc[e], cq = dc * dc;
+                            const float pd = cq * (float)dd[e];
+                            fr[0] = df_add(fr[0], DF{pd, fmaf(cq, (float)dd[e], -pd)});
+                        }
+                    }
+                }
             }
         }
     }
@@ -1728,6 +1760,13 @@ __device__ __forceinline__ void restart_tile(const HotInst& I, int slab, int ban
                 o[0] = racc[0];
                 o[1] = racc[1];
             }
+        }
+    } else if constexpr (MODE == 2) {
+        if constexpr (F32) {
+            DF cd[1] = {fr[0]};                           // <c, d> of this thread's share
+            block_sum_df<1>(cd, reinterpret_cast<float2*>(s_red));
+            if (threadIdx.x == 0)
+                reinterpret_cast<float2*>(I.tile_kkt)[(size_t)g_tile(I, slab, band) * kNK + kNK - 1] = df_st(cd[0]);
         }
     } else if constexpr (MODE == 1) {
         if constexpr (F32) {
@@ -1789,6 +1828,7 @@ __device__ __forceinline__ void restart_tile(const HotInst& I, int slab, int ban
 
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kThreads, 3) k_restart(const WorkDev* __restrict__ W) {
+    pdl_enter();
     __shared__ double s_row[MODE == 1 ? kRowSmemBytes / 8 * 2 : 1];
     __shared__ double s_col[MODE == 1 ? kThreads * 4 : 1];
     __shared__ double s_red[2 * 32];
@@ -1908,6 +1948,7 @@ __global__ void __launch_bounds__(kThreads) k_init(HotInst I, double sigma0) {
 // these small kernels.  FP64 mode keeps FP64 throughout.
 template <bool F32>
 __global__ void __launch_bounds__(kThreads) k_kkt1(const WorkDev* __restrict__ W) {
+    pdl_enter();
     __shared__ double s_red[32];
     __shared__ int s_t[3];
     const int ninst = W->ninst;
@@ -1981,6 +2022,7 @@ __device__ __forceinline__ DF sum_pairs(const float2* __restrict__ p, int count,
 template <bool F32>
 __global__ void __launch_bounds__(kThreads) k_check(const WorkDev* __restrict__ W, int K, double a1, double a2,
                                                     double a3) {
+    pdl_enter();
     __shared__ double s_red[8 * 32];
     const int ninst = W->ninst;
     for (int i = blockIdx.x; i < ninst; i += gridDim.x) {
@@ -1990,9 +2032,10 @@ __global__ void __launch_bounds__(kThreads) k_check(const WorkDev* __restrict__ 
         const int ntile = g_ntiles(I), nslab = g_nslab(I);
         double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         if constexpr (F32) {
-            // pairs: the check sweep's per-tile sums, <c, u> per tile, the
+            // pairs: the check sweep's per-tile KKT sums, <c, u> per tile, the
             // ||A x - b||^2 chunks and k_alpha32's <b, y> and <c, A^T(y-bar - y0)>
-            // per chunk
+            // per chunk (the objective's <c, d> share is added when the
+            // instance ends: only the reported value needs it)
             // (every load of a round is issued before the adds: the sums cost
             // a few round trips, not one per array)
             const float2* tk = reinterpret_cast<const float2*>(I.tile_kkt);
@@ -2006,7 +2049,8 @@ __global__ void __launch_bounds__(kThreads) k_check(const WorkDev* __restrict__ 
                 for (int u = 0; u < 4; ++u) {
                     const int q = q0 + u * blockDim.x;
 #pragma unroll
-                    for (int e = 0; e < kNK; ++e) t[u][e] = q < ntile ? tk[(size_t)q * kNK + e] : make_float2(0.f, 0.f);
+                    for (int e = 0; e < kNK - 1; ++e) t[u][e] = q < ntile ? tk[(size_t)q * kNK + e] : make_float2(0.f, 0.f);
+                    t[u][kNK - 1] = make_float2(0.f, 0.f);
                     t[u][kNK] = q < ntile ? cu[q] : make_float2(0.f, 0.f);
                 }
 #pragma unroll
@@ -2034,7 +2078,8 @@ __global__ void __launch_bounds__(kThreads) k_check(const WorkDev* __restrict__ 
         if (threadIdx.x == 0) {
             // FP32 mode: <c, x-bar> = <c, u> + <c, d> + sigma <c, A^T(y-bar - y0)>
             // from exact per-tile and per-slab parts (the per-element x-bar is
-            // rounded where u + d nearly cancels)
+            // rounded where u + d nearly cancels); <c, d> joins at the end
+            // (restart pass MODE 2, k_block_end)
             const double r2 = v[0], mn2 = v[1], x2 = v[2], z2 = v[3], cx = v[4] + v[7], ax2 = v[5], dob = v[6];
             const double scale = 1.0 / I.h;
             const double rel_dual = sqrt(r2) / (1.0 + I.norm_c);
@@ -2088,6 +2133,7 @@ __global__ void __launch_bounds__(kThreads) k_check(const WorkDev* __restrict__ 
 // Sigma update at a restart: sigma <- sqrt(sigma ||x-bar - x_r|| / ||z-bar - z_r||) on the grid 2^(j/16).
 template <bool F32>
 __global__ void __launch_bounds__(kThreads) k_restart_sigma(const WorkDev* __restrict__ W) {
+    pdl_enter();
     __shared__ double s_red[2 * 32];
     const int ninst = W->ninst;
     for (int i = blockIdx.x; i < ninst; i += gridDim.x) {
@@ -2127,12 +2173,27 @@ __global__ void __launch_bounds__(kThreads) k_restart_sigma(const WorkDev* __res
     }
 }
 
-__global__ void k_block_end(const WorkDev* __restrict__ W) {
+// End of a block: an FP32 instance that finished in it adds the <c, d> share
+// of its final check iteration (per-tile pairs from the restart pass MODE 2,
+// summed in tile order) to its objective; every instance's flags reset.
+// One CTA per instance.
+__global__ void __launch_bounds__(kThreads) k_block_end(const WorkDev* __restrict__ W) {
+    pdl_enter();
+    __shared__ float2 s_red[32];
     const int ninst = W->ninst;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ninst; i += gridDim.x * blockDim.x) {
-        HotCtl* C = W->inst[i].ctl;
-        C->restart_pending = 0;
-        C->just_finished = 0;
+    for (int i = blockIdx.x; i < ninst; i += gridDim.x) {
+        const HotInst& I = W->inst[i];
+        HotCtl* C = I.ctl;
+        if (C->just_finished && !I.fp64) {                // block-uniform
+            DF cd[1] = {sum_pairs(reinterpret_cast<const float2*>(I.tile_kkt) + (kNK - 1), g_ntiles(I), kNK)};
+            block_sum_df<1>(cd, s_red);
+            if (threadIdx.x == 0) C->pobj += df_val(cd[0]);
+        }
+        if (threadIdx.x == 0) {
+            C->restart_pending = 0;
+            C->just_finished = 0;
+        }
+        __syncthreads();
     }
 }
 
@@ -2208,7 +2269,8 @@ cudaError_t kernels_init(int device) {
     return e;
 }
 
-// One launch of the chain (cudaLaunchKernelEx keeps every call site in one form).
+// One launch of the chain (cudaLaunchKernelEx keeps every call site in one form),
+// programmatically dependent on the previous kernel (pdl_enter in every kernel).
 template <typename... KArgs, typename... Args>
 static void launch(const LaunchDims&, void (*k)(KArgs...), int grid, size_t smem, cudaStream_t st, Args... args) {
     cudaLaunchConfig_t cfg = {};
@@ -2216,6 +2278,11 @@ static void launch(const LaunchDims&, void (*k)(KArgs...), int grid, size_t smem
     cfg.blockDim = dim3(kThreads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
     cudaLaunchKernelEx(&cfg, k, args...);
 }
 
