@@ -81,7 +81,7 @@ void tune_pair(int S, PairHost& p) {
 }  // namespace
 
 std::vector<int> tile_candidates(int S, int fp64) {
-    const int cap = fp64 ? 4096 : 16384;
+    const int cap = fp64 ? 4096 : kMaxTileElems;
     const int Sp = (S + 3) & ~3;             // the row pitch of an S x S slab
     std::vector<int> out;
     for (int tr = std::min(S, cap / Sp); tr >= 1 && out.size() < 4; tr /= 2) {

@@ -38,7 +38,7 @@ int tile_rows(int m, int n, int fp64, int grid) {
     // of the grid's CTAs without a tile and a tile keeps at least 4 passes
     // (measured with the autotuner on GB300: TR = 64 at 64^2, 128^2 and 256^2,
     // 32 at 512^2)
-    int tr = std::min(std::min(Ls, 16384 / L), kMaxTR);
+    int tr = std::min(std::min(Ls, kMaxTileElems / L), kMaxTR);
     auto tiles = [&](int t) { return (long long)n * ((m + t - 1) / t) + (long long)m * ((n + t - 1) / t); };
     if (grid > 0)
         while (tiles(tr) < (long long)grid && (long long)(tr / 2) * L >= 4096) tr /= 2;
@@ -132,7 +132,7 @@ int inst_create(const PairHost& p, int fp64, const hot_config& cfg, double tol, 
     I->fp64 = fp64;
     I->TR = tr_override > 0 ? tr_override : tile_rows(m, n, fp64, sweep_grid(fp64));
     const int NV = fp64 ? 2 : 4;
-    if (I->TR > (fp64 ? L : kMaxTR) || (size_t)I->TR * Lp > (size_t)(fp64 ? 4096 : 16384) ||
+    if (I->TR > (fp64 ? L : kMaxTR) || (size_t)I->TR * Lp > (size_t)(fp64 ? 4096 : kMaxTileElems) ||
         kThreads / (Lp / NV) < 1) {
         set_error("invalid tile rows for this grid");
         return HOT_EINVAL;

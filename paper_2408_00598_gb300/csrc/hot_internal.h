@@ -39,6 +39,7 @@ constexpr int kMaxS = 1024;
 constexpr int kAPT = 4;                // k_alpha32: pieces per thread and chunk
 constexpr int kAlphaChunk = kThreads * kAPT;
 constexpr int kMaxTR = 128;            // FP32 tiles: TR * max(m, n) <= kRowSmemBytes / 4
+constexpr int kMaxTileElems = 16384;   // FP32 tiles: TR * (longer row pitch) <= this
 
 enum : int {
     ST_RUNNING = 0,
@@ -69,7 +70,8 @@ struct HotCtl {
     int just_finished;     // set at the check that ends the solve
     int cancel;            // host asks the instance to stop at the next check
     unsigned int ymax_bits;// max |alpha|, |beta| (float bits, scaled units)
-    int pad;
+    int dzero;             // FP32: a restart left the delta zero (not stored); the
+                           // next block's first sweep reads no d (cleared at the check)
 };
 
 // Element constants of one iteration in FP32 mode (formed once per instance

@@ -1264,11 +1264,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep64(const WorkDev* __restri
 // coordinates travel in the w component of the alpha/beta pieces (k_alpha32),
 // so the sweep reads no coordinate array.  A tile's offsets in the per-slab
 // arrays are resolved once, by the issue side, into its descriptor.
+// Zeros in place of a tile's delta: a tile spans TR * pitch <= kMaxTileElems
+// floats (checked when the instance is created); zero-initialised at module load.
+__device__ __align__(16) float g_zero_tile[kMaxTileElems];
+
 struct TileD {
     int inst, slab, band, S, NC, P, r0, r1, npass;   // NC: column groups of the row pitch (S rounded up to 4)
     int row;          // g_row: first row entry of the slab
     int tile;         // g_tile: index of the tile within its instance
     int colp;         // g_colp: first column-partial entry of (slab, band)
+    int dz;           // the delta read is zero (first iteration after an FP32 restart): no loads
     long long elem;   // g_elem: first flow variable of the slab
 };
 
@@ -1276,7 +1281,7 @@ struct TileD {
 // or t past the end.  PAD = false: every side of the batch is a multiple of 4,
 // so the pitch is the side.
 template <bool PAD>
-__device__ __forceinline__ TileD tile_desc(const WorkDev* __restrict__ W, int t, int ntiles) {
+__device__ __forceinline__ TileD tile_desc(const WorkDev* __restrict__ W, int t, int ntiles, bool first) {
     TileD d{};
     if (t >= ntiles) return d;
     const int i = find_inst(W->pre_tile, W->ninst, t);
@@ -1296,13 +1301,17 @@ __device__ __forceinline__ TileD tile_desc(const WorkDev* __restrict__ W, int t,
                  : (d.slab < I.n ? (long long)d.slab * I.m * I.m
                                  : (long long)I.n * I.m * I.m + (long long)(d.slab - I.n) * I.n * I.n);
     if (I.ctl->status == ST_RUNNING) d.npass = (d.r1 - d.r0 + d.P - 1) / d.P;
+    if (first) d.dz = I.ctl->dzero;
     return d;
 }
 
 // PAD: some slab side of the batch is not a multiple of 4, so a thread's
 // last column group may reach into the pad columns, which are masked (a
 // variant of its own: the masks cost the unpadded sweep registers).
-template <bool CHECK, bool PAD>
+// FIRST (the first iteration of a block, never a check): a tile whose delta
+// is known to be zero copies it from the zero tile (a variant of its own, so
+// the other iterations' sweep carries none of it).
+template <bool CHECK, bool PAD, bool FIRST = false>
 __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkDev* __restrict__ W, int j) {
     pdl_enter();
     constexpr int NV = 4;
@@ -1336,10 +1345,10 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkD
         bool acopy;                // the next pass is the tile's first and this thread copies an alpha piece
     } c;
     auto set_tile = [&](int t) {
-        TileD d = tile_desc<PAD>(W, t, ntiles);
+        TileD d = tile_desc<PAD>(W, t, ntiles, FIRST);
         while (t < ntiles && d.npass == 0) {
             t += G;
-            d = tile_desc<PAD>(W, t, ntiles);
+            d = tile_desc<PAD>(W, t, ntiles, FIRST);
         }
         c.it = t;
         if (t < ntiles) {
@@ -1348,7 +1357,10 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkD
             const int sp = PAD ? (d.S + 3) & ~3 : d.S;   // row pitch (without padded slabs, the side)
             const size_t base = (size_t)d.elem + ((size_t)d.r0 + ro) * sp + (size_t)cg * NV;
             c.u = (const float*)I.u + base;
-            c.d = (const float*)((j & 1) ? I.d1 : I.d0) + base;
+            // a delta known to be zero (first iteration after an FP32 restart,
+            // which stores none) is copied from a zero tile: L2 hits, no HBM read
+            c.d = (FIRST && d.dz) ? g_zero_tile + ((size_t)ro * sp + (size_t)cg * NV)
+                                  : (const float*)((j & 1) ? I.d1 : I.d0) + base;
             const int nr = d.r1 - d.r0;
             c.a = I.ab32 + 2 * (size_t)d.row + d.r0 + tid;
             c.step = d.P * sp;
@@ -1720,7 +1732,7 @@ __device__ __forceinline__ void restart_tile(const HotInst& I, int slab, int ban
                 V::st(u + (size_t)r * Sp + c0, nu_);
                 V::st(xr + (size_t)r * Sp + c0, xbv);
                 V::st(zr + (size_t)r * Sp + c0, zbv);
-                V::st(d0 + (size_t)r * Sp + c0, zero);
+                if constexpr (!F32) V::st(d0 + (size_t)r * Sp + c0, zero);   // FP32: dzero instead
                 if constexpr (F32) reinterpret_cast<float2*>(s_row)[(r - r0) * NC + cg] = df_st(rsf);
                 else s_row[(r - r0) * NC + cg] = rsd;
             } else {
@@ -2093,6 +2105,7 @@ __global__ void __launch_bounds__(kThreads) k_check(const WorkDev* __restrict__ 
             C->rel_primal = rel_primal;
             C->rel_kkt = rel;
             C->pobj = cx;                 // sum (r-c)^2 x-bar: unscaled <c, x-bar>
+            C->dzero = 0;                 // this block's first sweep has read it
             C->dobj = dob * scale;
             const long long total = C->total + K;
             const int kcheck = C->k + K - 1;
@@ -2168,6 +2181,7 @@ __global__ void __launch_bounds__(kThreads) k_restart_sigma(const WorkDev* __res
             C->r0 = -1.0;
             C->rprev = -1.0;
             C->restarts += 1;
+            if constexpr (F32) C->dzero = 1;   // MODE 1 stores no zero delta; the next first sweep reads none
         }
         __syncthreads();
     }
@@ -2265,6 +2279,10 @@ cudaError_t kernels_init(int device) {
         e = cudaFuncSetAttribute(k_sweep32<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSweepSmem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_sweep32<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSweepSmemChk);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_sweep32<false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSweepSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_sweep32<false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSweepSmem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_marg, cudaFuncAttributeMaxDynamicSharedMemorySize, 7 * kMaxS * 8);
     return e;
 }
@@ -2308,6 +2326,8 @@ void launch_sweep(const WorkDev* w, const LaunchDims& ld, int fp64, int j, bool 
         launch(ld, k_sweep64, check ? ld.grid_tile_chk : ld.grid_tile, 0, st, w, j, check ? 1 : 0);
     else if (check)
         launch(ld, pad ? k_sweep32<true, true> : k_sweep32<true, false>, ld.grid_tile_chk, kSweepSmemChk, st, w, j);
+    else if (j == 0)
+        launch(ld, pad ? k_sweep32<false, true, true> : k_sweep32<false, false, true>, ld.grid_tile, kSweepSmem, st, w, j);
     else
         launch(ld, pad ? k_sweep32<false, true> : k_sweep32<false, false>, ld.grid_tile, kSweepSmem, st, w, j);
 }
