@@ -56,7 +56,7 @@ extern "C" {
 #define HOT_NOT_CONVERGED   2   /* iteration cap reached; result still filled */
 #define HOT_EINVAL        (-1)  /* invalid argument or histogram              */
 #define HOT_ENOMEM        (-2)  /* device memory (or budget) exhausted        */
-#define HOT_NUMERIC       (-3)  /* NaN/Inf met in the FP64 reductions         */
+#define HOT_NUMERIC       (-3)  /* NaN/Inf met in the KKT reductions          */
 #define HOT_TIMEOUT       (-4)  /* a bounded wait ran out                      */
 #define HOT_ECUDA         (-5)  /* CUDA runtime error                          */
 #define HOT_ENOTFOUND     (-6)  /* unknown ticket or solution id               */

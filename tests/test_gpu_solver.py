@@ -232,6 +232,23 @@ def test_invalid_inputs_are_rejected(lib, ctx32):
         ctx32.solve(good1, good2, tol=-1.0)
 
 
+def test_numeric_status_from_an_overflowing_sigma0(lib):
+    """HOT_NUMERIC (NaN/Inf in the KKT reductions) reached from the host: a
+    sigma0 of 1e300 overflows the FP32 anchor u = -sigma0 c to -Inf, so the
+    first check's sums are NaN.  The result reports the status, the call
+    itself succeeds and the context keeps working."""
+    mu1, mu2 = syn.make_pair("white", 16, 3)
+    with lib.Context(precision="fp32", sigma0=1e300) as ctx:
+        r = ctx.solve(mu1, mu2, tol=1e-6, max_iter=1000)
+        ctx.release(r)
+        assert r["status"] == lib.HOT_NUMERIC
+        assert r["iters"] == 10                       # stopped at the first check
+    with lib.Context(precision="fp32") as ctx:
+        r = ctx.solve(mu1, mu2, tol=1e-6)
+        ctx.release(r)
+        assert r["status"] == lib.HOT_OK
+
+
 def test_device_inputs_match_host_inputs(lib, ctx32):
     import torch
     mu1, mu2 = syn.make_pair("cauchy", 32, 5)
