@@ -508,8 +508,10 @@ int Batch::set_instances(const std::vector<Inst*>& v, cudaStream_t st) {
     int* pa = h_pre + 4 * (cap + 1);
     pt[0] = ps[0] = pv[0] = pk[0] = pa[0] = 0;
     int running = 0;
+    size_t swept = 0;                 // bytes one sweep streams: u, d read, d written
     for (int i = 0; i < n; ++i) {
         h_inst[i] = v[i]->desc;
+        swept += 3 * (v[i]->big_bytes / 5);
         const int m = v[i]->m, nn = v[i]->n;
         pt[i + 1] = pt[i] + nn * v[i]->nb1 + m * v[i]->nb2;
         ps[i + 1] = ps[i] + m + nn;
@@ -518,7 +520,13 @@ int Batch::set_instances(const std::vector<Inst*>& v, cudaStream_t st) {
         pa[i + 1] = pa[i] + v[i]->desc.n_achunk;
         if (v[i]->ctl_host.status == ST_RUNNING) ++running;
     }
+    // a state larger than L2: alternate the sweep's tile order, so that each
+    // sweep starts on the tiles the previous one touched last (still in L2);
+    // a state that fits gains nothing from it
+    int l2 = 0;
+    if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, device) != cudaSuccess) l2 = 0;
     h_work->ninst = n;
+    h_work->alternate = (l2 > 0 && swept > (size_t)l2) ? 1 : 0;
     h_work->inst = d_inst;
     h_work->pre_tile = d_pre;
     h_work->pre_slab = d_pre + (cap + 1);

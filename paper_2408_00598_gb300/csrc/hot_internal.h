@@ -218,7 +218,7 @@ __host__ __device__ inline int g_L(const HotInst& I) { return I.m > I.n ? I.m : 
 // instances of the number of work items each kernel family handles.
 struct WorkDev {
     int ninst;
-    int pad;
+    int alternate;         // the sweeps' state exceeds L2: odd iterations take the tiles in reverse
     HotInst* inst;         // [ninst]
     int* pre_tile;         // sweep / restart tiles: n nb1 + m nb2 per instance
     int* pre_slab;         // k_alpha: m + n slabs per instance

@@ -1344,11 +1344,15 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 2 : 3) k_sweep32(const WorkD
         int left, it, ik;          // passes left, tile, tiles started
         bool acopy;                // the next pass is the tile's first and this thread copies an alpha piece
     } c;
+    // a state larger than L2: odd iterations take the tiles in reverse order,
+    // so a sweep starts on the tiles whose state the previous sweep touched
+    // last (still in L2)
+    const bool rev = (j & 1) && W->alternate;
     auto set_tile = [&](int t) {
-        TileD d = tile_desc<PAD>(W, t, ntiles, FIRST);
+        TileD d = tile_desc<PAD>(W, rev && t < ntiles ? ntiles - 1 - t : t, ntiles, FIRST);
         while (t < ntiles && d.npass == 0) {
             t += G;
-            d = tile_desc<PAD>(W, t, ntiles, FIRST);
+            d = tile_desc<PAD>(W, rev && t < ntiles ? ntiles - 1 - t : t, ntiles, FIRST);
         }
         c.it = t;
         if (t < ntiles) {
