@@ -369,6 +369,25 @@ def test_batch_equals_single_solves(lib, ctx32):
         assert rb["ot_value"] == rs["ot_value"] and rb["iters"] == rs["iters"]
 
 
+def test_results_do_not_depend_on_the_sweeps_tile_order(lib, ctx32):
+    """A batch whose state exceeds L2 walks the sweep's tiles in reverse on
+    odd iterations; every sum is formed per tile or per slab in a fixed order,
+    so each instance's results are bit-identical either way.  A 128 x 128
+    pair alone (its state fits in L2: one order) against the same pair batched
+    with the 256 x 256 bench pair (together above L2: alternating order)."""
+    small = syn.make_pair("gauss", 128, 7)
+    big = syn.make_pair("white", 256, 1000)
+    alone = []
+    for a, b in (small, big):
+        r = ctx32.solve(a, b, tol=1e-6)
+        ctx32.release(r)
+        alone.append(r)
+    out = ctx32.solve_batch([small[0], big[0]], [small[1], big[1]], tol=1e-6)
+    for rb, rs in zip(out, alone):
+        assert rb["status"] == 0 and rb["iters"] == rs["iters"] and rb["restarts"] == rs["restarts"]
+        assert rb["ot_value"] == rs["ot_value"] and rb["dual_value"] == rs["dual_value"]
+
+
 # ------------------------------------------------------- live sweep timing --
 
 def test_live_sweep_timing_leaves_the_solve_unchanged(lib):
