@@ -177,6 +177,15 @@ def kernels_sha():
     return h.hexdigest()
 
 
+def recorded_traffic(S, precision):
+    """The recorded ncu DRAM traffic of one sweep launch, or None where it was
+    not taken (another size or precision) or the kernel source has changed
+    since."""
+    if SWEEP_TRAFFIC["kernels_sha256"] == kernels_sha() and S == 256 and precision == "fp32":
+        return SWEEP_TRAFFIC["bytes_per_launch"]
+    return None
+
+
 def measured_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -344,9 +353,7 @@ def bench_solve(args, dist):
         achieved = kt["sweep_bytes"] / sweep_s / 1e9
         timing = "CUDA event pairs around every sweep of a separate profiled solve (no graph)"
     peak, peak_kind = measured_peak()
-    traffic = None
-    if SWEEP_TRAFFIC["kernels_sha256"] == kernels_sha() and S == 256 and args.precision == "fp32":
-        traffic = SWEEP_TRAFFIC["bytes_per_launch"]
+    traffic = recorded_traffic(S, args.precision)
     total_ms = kt["sweep_ms"] + kt["sweep_check_ms"] + kt["solve_ms"] + kt["block_end_ms"]
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
